@@ -1,0 +1,381 @@
+"""Pins of the oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: the anchors are values the
+paper prints, hand-derived worked examples, closed forms, exact enumeration
+on tiny filters, invariants the method guarantees, and an independent
+re-derivation of each greedy step with Python integers.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from oracle.oracle import OracleFilter, bits_of_bitmap, COST_MIX, COST_LA, COST_EXP, GOLDEN_RATIO
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([f.strip() for f in line.split("|")])
+    return rows
+
+
+# ---------------------------------------------------------------- generators
+
+def test_splitmix64_check_vector():
+    want = [int(r[0]) for r in _rows("splitmix64_seed1234567.txt")]
+    state = 1234567
+    got = []
+    for _ in want:
+        state, out = oracle.splitmix64_next(state)
+        got.append(out)
+    assert got == want
+    assert [int(v) for v in workloads.splitmix64(1234567, len(want))] == want
+
+
+# ---------------------------------------------------------------- hash (Section 3.4)
+
+def test_hash_worked_examples():
+    rows = _rows("hash_worked_examples.txt")
+    assert len(rows) >= 10
+    for a, x, b, want, _why in rows:
+        assert oracle.hash_lin(int(a), int(x), int(b)) == int(want), (a, x, b)
+
+
+@pytest.mark.parametrize("b", [512, 1 << 21, 1000003, 6150, 2])
+def test_hash_range_and_uniformity(b):
+    """Values stay in [b) and are uniform over random keys (chi-square)."""
+    keys = workloads.uniform_keys(77, 60000)
+    a = 0x9E3779B97F4A7C15 | 1
+    vals = np.array([oracle.hash_lin(a, int(x), b) for x in keys], dtype=np.uint64)
+    assert int(vals.max()) < b
+    bins = min(b, 64)
+    # fold onto `bins` classes by value range (uniform over [b) stays uniform)
+    cls = (vals.astype(np.float64) * bins / b).astype(np.int64)
+    cnt = np.bincount(cls, minlength=bins)
+    exp = len(keys) / bins
+    chi2 = float(np.sum((cnt - exp) ** 2 / exp))
+    # chi-square with bins-1 dof: mean bins-1, sd sqrt(2(bins-1)); allow 6 sd
+    assert chi2 < (bins - 1) + 6 * math.sqrt(2 * (bins - 1)) + 1, chi2
+
+
+def test_multipliers_odd_coprime_deterministic():
+    for M in [1, 7, 6150, 1 << 15, 32768 * 3]:
+        ab, af = oracle.derive_multipliers(12345, M, 14, 3)
+        ab2, af2 = oracle.derive_multipliers(12345, M, 14, 3)
+        assert np.array_equal(ab, ab2) and np.array_equal(af, af2)
+        for a in ab:
+            assert math.gcd(int(a), M) == 1 and int(a) & 1
+        for a in af:
+            assert math.gcd(int(a), 512) == 1
+        assert len(set(int(v) for v in af)) == 14
+    # the stream order: c block multipliers first, then k bit multipliers
+    ab3, af3 = oracle.derive_multipliers(12345, 1 << 15, 14, 3)
+    outs = workloads.splitmix64(12345, 17)
+    assert [int(v) for v in ab3] == [int(v) | 1 for v in outs[:3]]
+    assert [int(v) for v in af3] == [int(v) | 1 for v in outs[3:17]]
+
+
+def test_birthday_rate_of_bit_hashes():
+    """Fig. 3B: P(|F(x)| < k) for k = 10 matches the birthday formula."""
+    k = 10
+    _, a_bit = oracle.derive_multipliers(99, 1, k, 1)
+    keys = workloads.uniform_keys(5, 40000)
+    short = sum(1 for x in keys if len(oracle.bit_positions(a_bit, int(x))) < k)
+    p = cf.birthday_collision(k)
+    sd = math.sqrt(len(keys) * p * (1 - p))
+    assert abs(short - len(keys) * p) < 4.5 * sd, (short, len(keys) * p)
+
+
+# ---------------------------------------------------------------- cost functions
+
+def test_cost_printed_facts():
+    k = 14
+    beta = GOLDEN_RATIO
+    for a in range(0, k + 1):
+        # Appendix A: at load 1/4 (j = 128) cost^EXP equals beta plus a/k
+        assert oracle.cost(COST_EXP, beta, k, 128, a) == pytest.approx(beta + a / k, rel=1e-15)
+        # Appendix A: with sigma = 1, reaching load 1/2 (j = 256) makes the FPR term exactly k
+        assert oracle.cost(COST_MIX, 1.0, k, 256, a) == pytest.approx(k + a, rel=1e-15)
+    # Eq. 6: cost^LA_mu(j, a) = cost^MIX_1(j + mu k, a); mu = 3.5 gives an integer shift of 49
+    for j in [0, 17, 100, 200, 300, 400, 463]:
+        for a in [0, 1, 7, 14]:
+            assert oracle.cost(COST_LA, 3.5, k, j, a) == pytest.approx(
+                oracle.cost(COST_MIX, 1.0, k, j + 49, a), rel=1e-14)
+    # Eq. 5 at j = 0 is a alone; Eq. 4 at j = 0 is 1 + a/k
+    assert oracle.cost(COST_MIX, 50.0, k, 0, 3) == 3.0
+    assert oracle.cost(COST_EXP, beta, k, 0, 7) == pytest.approx(1.5, rel=1e-15)
+    # MIX at sigma: first term scales linearly in sigma
+    assert oracle.cost(COST_MIX, 50.0, k, 300, 0) == pytest.approx(
+        50.0 * oracle.cost(COST_MIX, 1.0, k, 300, 0), rel=1e-14)
+
+
+def test_cost_monotone():
+    """All three costs grow with the final load j and with the new bits a."""
+    for kind, par in [(COST_MIX, 50.0), (COST_LA, 3.5), (COST_EXP, GOLDEN_RATIO)]:
+        k = 12
+        prev = None
+        for j in range(0, 513):
+            v = oracle.cost(kind, par, k, j, 3)
+            if prev is not None:
+                assert v >= prev
+            prev = v
+        for a in range(0, k):
+            assert oracle.cost(kind, par, k, 200, a + 1) > oracle.cost(kind, par, k, 200, a)
+
+
+# ---------------------------------------------------------------- printed closed forms
+
+def _printed():
+    return {(r[0], r[1]): r for r in _rows("paper_printed_values.txt")}
+
+
+def test_bloom_overload_printed():
+    assert cf.bloom_overload_fpr(1.1, 10) / 2.0 ** -10 == pytest.approx(1.912, abs=0.001)
+    assert _printed()[("bloom_overload_fpr", "gamma=1.1 k=10")][2] == "1.912*2^-10"
+
+
+def test_bloom_overhead_printed():
+    assert cf.bloom_bits(1.0, 1) == pytest.approx(1.443, abs=0.0005)
+    # at load 1/2 the standard Bloom FPR is exactly 2^-k
+    assert cf.bloom_fpr(1000.0, cf.bloom_bits(1000.0, 10), 10) == pytest.approx(2.0 ** -10, rel=1e-12)
+
+
+@pytest.mark.parametrize("c,k,want", [(2, 7, 232), (3, 7, 219), (2, 14, 244), (3, 14, 237)])
+def test_load_bound_printed(c, k, want):
+    assert abs(cf.load_bound(c, k) - want) < 0.5
+    # and the defining property: (j/512)^k = 2^-k / c at the bound
+    j = cf.load_bound(c, k)
+    assert (j / 512.0) ** k == pytest.approx(2.0 ** -k / c, rel=1e-12)
+
+
+def test_birthday_printed():
+    p = cf.birthday_collision(10)
+    assert 0.08 < p < 0.10  # "almost 10%"
+    # brute force over all 8^3 triples in a range of 8: 1 - 8*7*6/512
+    assert cf.birthday_collision(3, 8) == pytest.approx(1 - 8 * 7 * 6 / 512.0, rel=1e-15)
+
+
+# ---------------------------------------------------------------- the filter itself
+
+def _filter(M, k, c, kind=COST_EXP, par=GOLDEN_RATIO, seed=3, B=1):
+    return OracleFilter(M, k, c, kind, par, seed=seed, batch=B)
+
+
+@pytest.mark.parametrize("c,kind,par,B", [
+    (1, COST_EXP, GOLDEN_RATIO, 1), (2, COST_MIX, 50.0, 1), (3, COST_LA, 3.5, 1),
+    (2, COST_EXP, GOLDEN_RATIO, 97), (3, COST_MIX, 2.5, 4096), (2, COST_LA, 3.5, 100000)])
+def test_no_false_negatives(c, kind, par, B):
+    """Section 1: a key that was inserted always queries True."""
+    f = _filter(64, 9, c, kind, par, B=B)
+    keys = workloads.uniform_keys(11, 6000)
+    f.insert(keys)
+    bm = f.query(keys)
+    assert bits_of_bitmap(bm, len(keys)).all()
+    assert f.inserted + f.skipped == len(keys)
+
+
+def _textbook_blocked_bloom(M, k, a_block1, a_bit, keys):
+    """Blocked Bloom filter (Section 2.2) with Python integers as blocks:
+    set the bits f_1(x)..f_k(x) in block h_1(x)."""
+    blocks = [0] * M
+    for x in keys:
+        b = oracle.hash_lin(a_block1, int(x), M)
+        for a in a_bit:
+            blocks[b] |= 1 << oracle.hash_lin(int(a), int(x), 512)
+    return blocks
+
+
+def _words_to_blocks(words, M):
+    blocks = []
+    for b in range(M):
+        v = 0
+        for w in range(8):
+            v |= int(words[8 * b + w]) << (64 * w)
+        blocks.append(v)
+    return blocks
+
+
+def test_one_choice_is_blocked_bloom():
+    """Section 3.4: one choice without cost evaluation is a Blocked Bloom
+    filter; the words depend neither on B nor on the cost."""
+    M, k = 37, 6
+    keys = workloads.uniform_keys(21, 3000)
+    ref = None
+    for kind, par, B in [(COST_EXP, GOLDEN_RATIO, 1), (COST_MIX, 50.0, 7), (COST_LA, 3.5, 3000)]:
+        f = _filter(M, k, 1, kind, par, seed=8, B=B)
+        f.insert(keys)
+        if ref is None:
+            ref = f.words.copy()
+            tb = _textbook_blocked_bloom(M, k, int(f.a_block[0]), f.a_bit[:k], keys)
+            assert _words_to_blocks(f.words, M) == tb
+        assert np.array_equal(f.words, ref)
+
+
+def test_whole_batch_against_empty_filter_takes_first_choice():
+    """With B >= n every key sees the empty filter: all candidate costs tie
+    and the lowest index wins, so the result is the Blocked Bloom filter on h_1."""
+    for c in (2, 3):
+        f = _filter(50, 8, c, COST_MIX, 50.0, seed=4, B=10 ** 6)
+        keys = workloads.uniform_keys(31, 2000)
+        ch = f.insert(keys, return_choices=True)
+        assert (ch == 0).all()
+        tb = _textbook_blocked_bloom(50, 8, int(f.a_block[0]), f.a_bit[:8], keys)
+        assert _words_to_blocks(f.words, 50) == tb
+
+
+def test_order_invariance_inside_a_batch():
+    keys = workloads.uniform_keys(41, 4096)
+    rng = np.random.default_rng(0)
+    a = _filter(16, 7, 3, COST_LA, 3.5, B=1024)
+    a.insert(keys)
+    b = _filter(16, 7, 3, COST_LA, 3.5, B=1024)
+    perm = np.concatenate([s + rng.permutation(1024) for s in range(0, 4096, 1024)])
+    b.insert(keys[perm])
+    assert np.array_equal(a.words, b.words)
+
+
+@pytest.mark.parametrize("M,k,c,kind,par", [
+    (1, 2, 2, COST_MIX, 50.0), (2, 3, 2, COST_EXP, GOLDEN_RATIO), (4, 2, 3, COST_LA, 3.5),
+    (8, 3, 3, COST_MIX, 2.5), (4, 3, 2, COST_EXP, GOLDEN_RATIO)])
+def test_greedy_steps_by_brute_force(M, k, c, kind, par):
+    """Replays every sequential insertion with Python integers as blocks:
+    each step must skip exactly when a candidate already holds F(x), and
+    otherwise pick the first candidate of least cost (Section 3.2)."""
+    f = _filter(M, k, c, kind, par, seed=M * 10 + k, B=1)
+    keys = workloads.uniform_keys(M + 100 * k, 300)
+    ch = f.insert(keys, return_choices=True)
+    blocks = [0] * M
+    for t, x in enumerate(keys):
+        F = set(int(p) for p in oracle.bit_positions(f.a_bit[:k], int(x)))
+        cands = [oracle.hash_lin(int(f.a_block[i]), int(x), M) for i in range(c)]
+        Ls = [bin(blocks[b]).count("1") for b in cands]
+        As = [sum(1 for p in F if not (blocks[b] >> p) & 1) for b in cands]
+        if min(As) == 0:
+            assert ch[t] == -1, t
+            continue
+        if kind == COST_MIX:
+            costs = [par * k * ((L + a) / 256.0) ** k + a for L, a in zip(Ls, As)]
+        elif kind == COST_LA:
+            costs = [k * ((L + a + par * k) / 256.0) ** k + a for L, a in zip(Ls, As)]
+        else:
+            costs = [par ** ((L + a) / 128.0) + a / k for L, a in zip(Ls, As)]
+        best = min(range(c), key=lambda i: (costs[i], i))
+        assert ch[t] == best, (t, costs, ch[t])
+        for p in F:
+            blocks[cands[best]] |= 1 << p
+    assert _words_to_blocks(f.words, M) == blocks
+
+
+def _exact_fpr_by_enumeration(blocks, M, c, k):
+    """P(query hits) for a key whose c block addresses and k bit addresses
+    are independent and uniform: enumerate every block tuple, and for each
+    take the union over candidates by inclusion-exclusion over subsets
+    (|intersection|/512)^k. For k = 2 also enumerate all 512^2 bit pairs."""
+    import itertools
+    tot = 0.0
+    for tup in itertools.product(range(M), repeat=c):
+        p = 0.0
+        for r in range(1, c + 1):
+            for sub in itertools.combinations(tup, r):
+                inter = (1 << 512) - 1
+                for b in sub:
+                    inter &= blocks[b]
+                p += (-1) ** (r + 1) * (bin(inter).count("1") / 512.0) ** k
+        tot += p
+    return tot / M ** c
+
+
+def test_exact_fpr_tiny_filter_vs_measured():
+    M, k, c = 2, 2, 2
+    f = _filter(M, k, c, COST_EXP, GOLDEN_RATIO, seed=5, B=1)
+    keys = workloads.uniform_keys(61, 220)
+    f.insert(keys)
+    blocks = _words_to_blocks(f.words, M)
+    p_ie = _exact_fpr_by_enumeration(blocks, M, c, k)
+    # direct enumeration of all (b1, b2, p1, p2) outcomes
+    bits = np.array([[(blocks[b] >> p) & 1 for p in range(512)] for b in range(M)], dtype=bool)
+    cont = bits[:, :, None] & bits[:, None, :]          # block holds both positions
+    p_enum = float(np.mean(cont[:, None, :, :] | cont[None, :, :, :]))
+    assert p_enum == pytest.approx(p_ie, rel=1e-12)
+    neg = workloads.disjoint_keys(62, 400000, keys)
+    W = int(bits_of_bitmap(f.query(neg), len(neg)).sum())
+    sd = math.sqrt(len(neg) * p_ie * (1 - p_ie))
+    assert abs(W - len(neg) * p_ie) < 4.5 * sd, (W, len(neg) * p_ie)
+
+
+def test_one_choice_fpr_given_state_and_formula():
+    """One choice: measured W/N equals mean_b (L_b/512)^k within binomial
+    noise, and is near the Putze et al. blocked-Bloom formula."""
+    M, k = 1024, 8
+    n = int(M * 512 * math.log(2) / k)
+    f = _filter(M, k, 1, seed=6)
+    keys = workloads.uniform_keys(71, n)
+    f.insert(keys)
+    hist, total = f.histogram()
+    assert int(hist.sum()) == M and total == sum(bin(b).count("1") for b in _words_to_blocks(f.words, M))
+    q = cf.fpr_given_state(hist, k, 1)
+    neg = workloads.disjoint_keys(72, 600000, keys)
+    W = int(bits_of_bitmap(f.query(neg), len(neg)).sum())
+    sd = math.sqrt(len(neg) * q * (1 - q))
+    assert abs(W - len(neg) * q) < 4.5 * sd
+    assert q == pytest.approx(cf.blocked_bloom_fpr(n, M, k), rel=0.06)
+    # Section 2.2: the blocked filter is worse than a standard Bloom filter of the same size
+    assert q > cf.bloom_fpr(n, M * 512, k)
+
+
+def test_load_histograms_ordered_by_choices():
+    """Appendix C (Fig. 8): three choices give a lower and tighter load
+    distribution than two, and two than one, at equal n, M and k."""
+    M, k = 1024, 14
+    n = int(M * 512 * math.log(2) / k)
+    keys = workloads.uniform_keys(81, n)
+    stats = []
+    for c in (1, 2, 3):
+        f = _filter(M, k, c, COST_EXP, GOLDEN_RATIO, seed=9)
+        f.insert(keys)
+        hist, _ = f.histogram()
+        L = np.arange(513)
+        mean = float(np.sum(hist * L) / M)
+        sd = math.sqrt(float(np.sum(hist * (L - mean) ** 2) / M))
+        stats.append((mean, sd))
+    assert stats[2][0] < stats[1][0] < stats[0][0]
+    assert stats[2][1] < stats[1][1] < stats[0][1]
+
+
+def test_duplicates_and_skip_counts():
+    f = _filter(32, 10, 2, COST_MIX, 50.0, B=1)
+    keys = workloads.uniform_keys(91, 100)
+    f.insert(keys)
+    assert f.inserted + f.skipped == 100
+    before = f.words.copy()
+    f.insert(keys)                # every key is now contained: all skipped
+    assert f.skipped >= 100 and np.array_equal(before, f.words)
+    g = _filter(32, 10, 2, COST_MIX, 50.0, B=64)
+    g.insert(np.concatenate([keys[:10], keys[:10]]))  # same batch: same choice, idempotent
+    h = _filter(32, 10, 2, COST_MIX, 50.0, B=64)
+    h.insert(keys[:10])
+    assert np.array_equal(g.words, h.words) and g.inserted == 20
+
+
+def test_query_bitmap_layout():
+    f = _filter(8, 4, 2, COST_MIX, 50.0, B=1)
+    keys = workloads.uniform_keys(101, 40)
+    f.insert(keys[::2])
+    bm = f.query(keys[:70])
+    assert len(bm) == 1
+    hits = bits_of_bitmap(bm, 40)
+    assert hits[::2].all()
+    assert (int(bm[0]) >> 40) == 0       # bits past n are zero
+    for t in range(40):
+        assert hits[t] == ((int(bm[0]) >> t) & 1 == 1)
+    assert len(f.query(keys[:0])) == 0

@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the filter method: it only makes keys.
+Both the oracle-side tests and the GPU path draw their inputs from here, so
+that the two sides see identical keys.
+
+* uniform 64-bit keys: successive splitmix64 outputs (Steele, Lea and Flood,
+  OOPSLA 2014) of a seed, standing in for the paper's random 64-bit integers
+  (Section 4.1, Section 4.2);
+* DNA: a uniform random genome over A/C/G/T, 2 bits per base, and its
+  canonical 31-mers encoded as 64-bit integers, standing in for the genomes
+  of Section 4.3 (which are not available offline).
+"""
+import math
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, start: int = 0) -> np.ndarray:
+    """Outputs start..start+n-1 of splitmix64 seeded with `seed` (uint64)."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(start + 1, start + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform_keys(seed: int, n: int) -> np.ndarray:
+    """n uniform 64-bit keys: the first n splitmix64 outputs of `seed`."""
+    return splitmix64(seed, n)
+
+
+def disjoint_keys(seed: int, n: int, exclude: np.ndarray) -> np.ndarray:
+    """n uniform 64-bit keys from `seed` that do not occur in `exclude`,
+    in stream order (rejection against a sorted copy of `exclude`)."""
+    ex = np.sort(np.asarray(exclude, dtype=np.uint64))
+    out = []
+    have = 0
+    start = 0
+    while have < n:
+        want = (n - have) + (n - have) // 64 + 16
+        cand = splitmix64(seed, want, start)
+        start += want
+        if len(ex):
+            pos = np.searchsorted(ex, cand)
+            pos[pos == len(ex)] = 0
+            cand = cand[ex[pos] != cand]
+        out.append(cand[: n - have])
+        have += len(out[-1])
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.uint64)
+
+
+def random_genome(seed: int, nbases: int) -> np.ndarray:
+    """Uniform random DNA, one base per uint8 in {0,1,2,3} = A,C,G,T.
+    Base 32w+i is bits 2i..2i+1 of splitmix64 output w (low bits first)."""
+    nwords = (nbases + 31) // 32
+    w = splitmix64(seed, nwords)
+    shifts = (2 * np.arange(32, dtype=np.uint64))
+    bases = ((w[:, None] >> shifts[None, :]) & np.uint64(3)).astype(np.uint8)
+    return bases.reshape(-1)[:nbases]
+
+
+def _windows(vals: np.ndarray, q: int, first_high: bool) -> np.ndarray:
+    """Pack every length-q window of 2-bit symbols into a uint64 by doubling.
+    first_high: the window's first symbol is most significant; otherwise the
+    first symbol is least significant."""
+    n = len(vals) - q + 1
+    pieces = {1: vals.astype(np.uint64)}
+    L = 1
+    while 2 * L <= q:
+        a = pieces[L]
+        m = len(a) - L
+        if first_high:
+            pieces[2 * L] = (a[:m] << np.uint64(2 * L)) | a[L:L + m]
+        else:
+            pieces[2 * L] = a[:m] | (a[L:L + m] << np.uint64(2 * L))
+        L *= 2
+    acc = None
+    acc_len = 0
+    for L in sorted(pieces, reverse=True):
+        if acc_len + L > q:
+            continue
+        p = pieces[L]
+        if acc is None:
+            acc = p[:n].copy()
+        else:
+            seg = p[acc_len:acc_len + n]
+            if first_high:
+                acc = (acc << np.uint64(2 * L)) | seg
+            else:
+                acc = acc | (seg << np.uint64(2 * acc_len))
+        acc_len += L
+        if acc_len == q:
+            break
+    return acc
+
+
+def canonical_kmers(bases: np.ndarray, q: int = 31) -> np.ndarray:
+    """Canonical q-mers of a base sequence, 2-bit encoded (A=0, C=1, G=2,
+    T=3, first base most significant): min(forward, reverse complement).
+    Duplicates are kept, in sequence order."""
+    if q < 1 or q > 32:
+        raise ValueError("q must be in 1..32")
+    bases = np.asarray(bases, dtype=np.uint8)
+    if len(bases) < q:
+        return np.zeros(0, dtype=np.uint64)
+    fwd = _windows(bases, q, first_high=True)
+    rc = _windows((3 - bases).astype(np.uint8), q, first_high=False)
+    return np.minimum(fwd, rc)
+
+
+def lognormal_counts(seed: int, n_filters: int, median: float = 200000.0,
+                     sigma: float = 1.0, lo: int = 1000, hi: int = 20000000):
+    """Per-filter key counts round(median * exp(sigma Z)), clipped to [lo, hi],
+    Z standard normal by Box-Muller on splitmix64 uniforms."""
+    u = splitmix64(seed, 2 * n_filters)
+    u1 = ((u[0::2] >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
+    u2 = ((u[1::2] >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    n = np.rint(median * np.exp(sigma * z)).astype(np.int64)
+    return np.clip(n, lo, hi)
+
+
+def uniform01(seed: int, n: int) -> np.ndarray:
+    """n doubles in (0, 1) from splitmix64 (53-bit mantissa)."""
+    u = splitmix64(seed, n)
+    return ((u >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
