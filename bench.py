@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of the BlowChoc filter hot path on one GB300 (or N replicas).
+
+Workload (the DNA k-mer configuration): a 50,000,000-base uniform random
+genome (splitmix64 seed 2, 2 bits per base) gives 49,999,970 canonical
+31-mers, inserted with B = 2^20 into a filter of 2^30 bits (M = 2^21 blocks,
+128 MiB), k = 16, three choices, cost^LA with mu = 3.5; the query set is the
+same 31-mers followed by 49,999,970 31-mers of an independent genome (seed 3).
+
+One step = clear the filter, insert all keys, query all query keys, read the
+load statistics: every row of the hot path over one batch of input. The
+metric is keys processed (inserted + queried) per second, in Mkeys/s.
+
+--impl reference runs the CPU oracle (plain single-threaded C) on a bounded
+sample of the same workload, as the reference arm.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+CONFIG = dict(workload="dna_kmer_31_c3_la", genome_bases=50_000_000, q=31, genome_seed=2,
+              other_genome_seed=3, nblocks=1 << 21, filter_bits=1 << 30, k=16, choices=3,
+              cost="LA", mu=3.5, batch=1 << 20, hash_seed=2)
+N_KEYS = CONFIG["genome_bases"] - CONFIG["q"] + 1
+COST_LA = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload():
+    g1 = workloads.random_genome(CONFIG["genome_seed"], CONFIG["genome_bases"])
+    keys = workloads.canonical_kmers(g1, CONFIG["q"])
+    del g1
+    g2 = workloads.random_genome(CONFIG["other_genome_seed"], CONFIG["genome_bases"])
+    other = workloads.canonical_kmers(g2, CONFIG["q"])
+    del g2
+    queries = np.concatenate([keys, other])
+    return keys, queries
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "bc_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def golden_pbar():
+    """Mean 1-based index of the first candidate block holding an inserted
+    31-mer of this workload, as counted by the oracle (tests/golden)."""
+    path = os.path.join(ROOT, "tests", "golden", "dna_kmer_31_c3_la.txt")
+    if os.path.exists(path):
+        with open(path) as fh:
+            for line in fh:
+                if line.startswith("pbar_positive"):
+                    return float(line.split("=")[1].split()[0]), "oracle"
+    return 1.0, "lower bound 1.0 (oracle count not stored)"
+
+
+def cpu_baseline(keys, queries, n_ins, n_q):
+    """The oracle (single-threaded C) on a bounded sample of the workload."""
+    from oracle import OracleFilter
+    o = OracleFilter(CONFIG["nblocks"], CONFIG["k"], CONFIG["choices"], COST_LA, CONFIG["mu"],
+                     seed=CONFIG["hash_seed"], batch=CONFIG["batch"])
+    t0 = time.perf_counter()
+    o.insert(keys[:n_ins])
+    qs = np.concatenate([queries[: n_q // 2], queries[N_KEYS: N_KEYS + n_q // 2]])
+    o.query(qs)
+    dt = time.perf_counter() - t0
+    return {"value": round((n_ins + len(qs)) / dt / 1e6, 4), "unit": "Mkeys/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "first %d inserts (one partial batch, B = 2^20) and %d queries (half "
+                      "members, half other-genome 31-mers) of the same workload, %.1f s"
+                      % (n_ins, len(qs), dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    keys, queries = make_workload()
+    from oracle import OracleFilter
+    n_ins, n_q = 200_000, 400_000
+    times = []
+    for step in range(args.warmup + args.steps):
+        o = OracleFilter(CONFIG["nblocks"], CONFIG["k"], CONFIG["choices"], COST_LA, CONFIG["mu"],
+                         seed=CONFIG["hash_seed"], batch=CONFIG["batch"])
+        qs = np.concatenate([queries[: n_q // 2], queries[N_KEYS: N_KEYS + n_q // 2]])
+        t0 = time.perf_counter()
+        o.insert(keys[:n_ins])
+        o.query(qs)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = (n_ins + n_q) / (ms / 1e3) / 1e6
+    sample = ("per step: %d inserts (B = 2^20, one partial batch) and %d queries (half members, "
+              "half other-genome 31-mers) of the DNA 31-mer workload" % (n_ins, n_q))
+    out = {"impl": "reference", "metric": "insert+query throughput (DNA 31-mers, c=3, k=16, cost^LA)",
+           "value": round(value, 4), "unit": "Mkeys/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": dict(CONFIG, sample=sample),
+           "cpu_baseline": {"value": round(value, 4), "unit": "Mkeys/s", "cores": 1,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "Mkeys/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2501_18977_gb300 as bc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    keys, queries = make_workload()
+    n_ins, n_q = len(keys), len(queries)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dq = torch.from_numpy(queries.view(np.int64)).cuda()
+    nwords = (n_q + 63) // 64
+    bitmap = torch.empty(nwords, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    f = bc.Filter(CONFIG["nblocks"], CONFIG["k"], CONFIG["choices"], bc.COST_LA, CONFIG["mu"],
+                  hash_seed=CONFIG["hash_seed"], batch=CONFIG["batch"], stream=stream)
+
+    ev = []
+
+    def step(record):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        if record:
+            e[0].record(stream)
+        f.clear(stream)
+        f.insert(dk, stream)
+        if record:
+            e[1].record(stream)
+        f.query(dq, bitmap, stream)
+        if record:
+            e[2].record(stream)
+        st = f.stats()
+        if record:
+            e[3].record(stream)
+            ev.append(e)
+        return st
+
+    for _ in range(args.warmup):
+        st = step(False)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = bc.blowchoc_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        st = step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = bc.blowchoc_launch_count() - launches0
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * (n_ins + n_q) / (ms / 1e3) / 1e6
+
+    ins_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    qry_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    sta_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    skip_rate = st.skipped / max(1, st.inserted + st.skipped)
+
+    # roofline of the query kernel (one launch per step) against HBM
+    c = CONFIG["choices"]
+    pbar, pbar_src = golden_pbar()
+    q_bytes = n_ins * (8 + 64 * pbar + 1 / 8) + (n_q - n_ins) * (8 + 64 * c + 1 / 8)
+    i_bytes = n_ins * (8 + 64 * c + 64 * (1 - skip_rate))
+    peak, peak_src = peaks()
+    q_gbs = q_bytes / (qry_ms / 1e3) / 1e9
+    i_gbs = i_bytes / (ins_ms / 1e3) / 1e9
+    hits = None
+
+    e2e = None
+    if not args.no_e2e:
+        h_keys = torch.from_numpy(keys.view(np.int64)).pin_memory()
+        h_q = torch.from_numpy(queries.view(np.int64)).pin_memory()
+        h_bm = torch.empty(nwords, dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            dk.copy_(h_keys, non_blocking=True)
+            dq.copy_(h_q, non_blocking=True)
+            f.clear(stream)
+            f.insert(dk, stream)
+            f.query(dq, bitmap, stream)
+            h_bm.copy_(bitmap, non_blocking=True)
+            f.stats()
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = a.elapsed_time(b) / args.steps
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        hits = int(np.unpackbits(h_bm.numpy().view(np.uint8), bitorder="little")[:n_q].sum())
+        e2e = {"value": round(world * (n_ins + n_q) / (ems / 1e3) / 1e6, 3), "unit": "Mkeys/s",
+               "h2d_bytes_per_step": int(8 * (n_ins + n_q)), "d2h_bytes_per_step": int(8 * nwords),
+               "ms_per_step": round(ems, 3)}
+
+    if rank != 0:
+        f.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(keys, queries, 300_000, 600_000)
+
+    dominant = "query" if qry_ms >= ins_ms else "insert"
+    out = {
+        "metric": "insert+query throughput (DNA 31-mers, c=3, k=16, cost^LA)",
+        "value": round(value, 3), "unit": "Mkeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": dict(CONFIG, n_insert=n_ins, n_query=n_q, parallelism="replicas",
+                       l2="inputs larger than L2 (1.2 GB of keys per step); filter cleared at step start"),
+        "insert_mkeys_s": round(n_ins / (ins_ms / 1e3) / 1e6, 2),
+        "query_mkeys_s": round(n_q / (qry_ms / 1e3) / 1e6, 2),
+        "phase_ms": {"clear+insert": round(ins_ms, 4), "query": round(qry_ms, 4),
+                     "stats": round(sta_ms, 4)},
+        "roofline": {"bound": "hbm", "kernel": "query_kernel" if dominant == "query" else
+                     "insert (choose_kernel + set_kernel)",
+                     "achieved": round(q_gbs if dominant == "query" else i_gbs, 1),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round((q_gbs if dominant == "query" else i_gbs) / peak, 4),
+                     "traffic": None, "peak_source": peak_src, "pbar": pbar, "pbar_source": pbar_src},
+        "roofline_other": {"insert_gbs": round(i_gbs, 1), "insert_frac": round(i_gbs / peak, 4),
+                           "query_gbs": round(q_gbs, 1), "query_frac": round(q_gbs / peak, 4)},
+        "skip_rate": round(skip_rate, 6), "inserted": st.inserted, "skipped": st.skipped,
+        "query_hits": hits, "fpr_est": st.fpr_est,
+        "gpu_launches": int(launches),
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    f.close()
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * blowchoc.h -- C ABI of a GPU (sm_103a) Blocked Bloom filter with choices.
+ *
+ * The data structure is the "BlowChoc" filter of J. E. Schmitz, J. Zentgraf
+ * and S. Rahmann, "Blocked Bloom Filters with Choices" (arXiv 2501.18977):
+ * M blocks of 512 bits; a key x has c candidate blocks h_1(x)..h_c(x) and a
+ * bit set F(x) = {f_1(x)..f_k(x)} inside a block (Section 3.1, Eq. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: BLOWCHOC_OK (0) or a negative BLOWCHOC_E* code. No
+ *    exception crosses the ABI. blowchoc_last_error() describes the last
+ *    failure of the calling thread.
+ *  - Pointers named d_* are DEVICE pointers (global memory of the current
+ *    CUDA device), 8-byte aligned. The caller owns them and keeps them alive
+ *    until the work queued on the given stream has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Insert and query are asynchronous and stream-ordered; the
+ *    caller orders calls on different streams (events) if one must see the
+ *    other's result.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one fails with BLOWCHOC_ECUDA.
+ */
+#ifndef BLOWCHOC_H
+#define BLOWCHOC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLOWCHOC_OK 0
+#define BLOWCHOC_EINVAL (-1)   /* bad argument */
+#define BLOWCHOC_ENOMEM (-2)   /* device allocation failed */
+#define BLOWCHOC_ECUDA (-3)    /* CUDA runtime error (or no device) */
+#define BLOWCHOC_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define BLOWCHOC_EBUDGET (-5)  /* request exceeds a memory budget */
+
+#define BLOWCHOC_BLOCK_BITS 512
+#define BLOWCHOC_MAX_K 32
+#define BLOWCHOC_MAX_CHOICES 3
+
+/* Block-selection costs, with j = set bits of the block after insertion and
+ * a = bits the key would newly set there (Section 3.2, Appendix A):
+ *   MIX (Eq. 5): sigma k (j/256)^k + a        cost_param = sigma >= 0
+ *   LA  (Eq. 6): k ((j + mu k)/256)^k + a     cost_param = mu >= 0
+ *   EXP (Eq. 4): beta^(j/128) + a/k           cost_param = beta > 0
+ * Costs are evaluated once per filter on the host in IEEE double and turned
+ * into an exact integer rank table; ties go to the lowest choice index. */
+typedef enum {
+    BLOWCHOC_COST_MIX = 0,
+    BLOWCHOC_COST_LA = 1,
+    BLOWCHOC_COST_EXP = 2
+} blowchoc_cost;
+
+typedef struct {
+    uint64_t nblocks;   /* M >= 1 blocks of 512 bits (m = 512 M bits), M <= 2^32 */
+    uint32_t k;         /* bit-address hashes, 1..32 */
+    uint32_t choices;   /* c, 1..3 (c = 1 is a Blocked Bloom filter, no cost) */
+    int32_t cost;       /* blowchoc_cost */
+    uint32_t bitsel;    /* 0 = random bit selection (Section 3.3); other values rejected */
+    double cost_param;  /* sigma | mu | beta */
+    uint64_t hash_seed; /* seeds the hash multipliers (see blowchoc_multipliers) */
+    uint64_t batch;     /* B >= 1: batch size of the batch-synchronous insertion */
+} blowchoc_params;
+
+typedef struct blowchoc_filter blowchoc_filter;
+
+typedef struct {
+    uint64_t inserted;  /* keys whose bits were OR-ed into a block */
+    uint64_t skipped;   /* keys already contained in a candidate block (Section 3.2) */
+    uint64_t set_bits;  /* total 1-bits of the filter */
+    uint64_t hist[BLOWCHOC_BLOCK_BITS + 1]; /* hist[L] = blocks with L set bits (Fig. 8) */
+    double fpr_est;     /* 1 - (1 - mean_b (L_b/512)^k)^c, see blowchoc_stats */
+} blowchoc_filter_stats;
+
+/*
+ * blowchoc_create -- allocate a filter of params->nblocks zeroed blocks on the
+ * current device (Section 3.1; the block layout of Section 2.2).
+ *   params  in, host pointer, read during the call only.
+ *   stream  the filter's home stream: zeroing is queued there, and
+ *           blowchoc_stats / blowchoc_destroy order themselves on it.
+ *   out     out, receives the handle; the library owns the device memory
+ *           (filter words, rank table, counters, scratch) until destroy.
+ * Hash multipliers (Section 3.4: "a random large integer" coprime to the
+ * range b) are drawn from splitmix64 seeded with hash_seed, forced odd and
+ * redrawn until coprime: first a_1..a_c for the block hashes (range M), then
+ * a'_1..a'_k for the bit hashes (range 512).
+ * Layout: bit p of block b is bit (p mod 64) of the little-endian 64-bit
+ * word 8b + p/64; blocks are contiguous and 64-byte aligned.
+ * Errors: EINVAL (M = 0 or > 2^32, k not in 1..32, c not in 1..3, bad cost
+ * kind or parameter, bitsel != 0, batch = 0, out NULL), ENOMEM, ECUDA.
+ */
+int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter **out);
+
+/*
+ * blowchoc_insert -- insert d_keys[0..n) (Section 3.2, Fig. 2B), in batches
+ * of B = params.batch keys. Every key of a batch decides against the bits
+ * present when its batch starts: if some candidate block already holds all
+ * of F(x), the key is skipped; otherwise it goes to the candidate of least
+ * cost (lowest index on ties). The batch's bits are OR-ed in after all its
+ * choices. B = 1 is the paper's one-key-at-a-time insertion. The result
+ * depends only on (params, key sequence), never on launch configuration.
+ *   d_keys  device, n uint64 keys (any values; u = 64-bit keys).
+ *   n       may be 0 (no-op).
+ * May grow an internal device scratch buffer (min(B, n) bytes) on first use.
+ * Errors: EINVAL (NULL filter, NULL keys with n > 0), ENOMEM, ECUDA.
+ */
+int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream);
+
+/*
+ * blowchoc_query -- membership of d_keys[0..n) (Section 3.1): key t is
+ * reported present iff all bits of F(x) are set in at least one of its c
+ * candidate blocks. No false negatives for inserted keys.
+ *   d_bitmap  device, out, ceil(n/64) uint64 words: bit (t mod 64) of word
+ *             t/64 (least significant first) is key t; bits past n are 0.
+ * Errors: EINVAL (NULL filter, NULL pointers with n > 0), ECUDA.
+ */
+int blowchoc_query(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n,
+                   uint64_t *d_bitmap, void *stream);
+
+/*
+ * blowchoc_stats -- load statistics (Appendix C, Fig. 8): the histogram of
+ * set bits per block, the total, and the insert/skip counters. Runs on the
+ * filter's home stream and synchronises it before returning (host result).
+ * fpr_est is the false-positive rate implied by the histogram for ideal
+ * hashing, q = mean_b (L_b/512)^k (exact in expectation for c = 1), combined
+ * over c candidates as if independent: 1 - (1 - q)^c.
+ * Errors: EINVAL (NULL pointers), ECUDA, ETIMEOUT (an earlier bounded
+ * device wait of this filter gave up; its result is not trustworthy).
+ */
+int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out);
+
+/*
+ * blowchoc_destroy -- synchronise the home stream and free the filter's
+ * device memory. NULL is accepted (no-op).
+ */
+int blowchoc_destroy(blowchoc_filter *f);
+
+/*
+ * blowchoc_words -- the device address and length (8 M words) of the filter
+ * words. The library keeps ownership; the pointer is valid until destroy.
+ * Reading or writing it must be ordered with the filter's other work.
+ */
+int blowchoc_words(blowchoc_filter *f, uint64_t **d_words, uint64_t *nwords);
+
+/*
+ * blowchoc_multipliers -- the hash multipliers in use (Section 3.4):
+ * a_block[0..c) for h_1..h_c and a_bit[0..k) for f_1..f_k (host arrays of at
+ * least 3 and 32 entries). Errors: EINVAL.
+ */
+int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit);
+
+/*
+ * blowchoc_read_words / blowchoc_write_words -- copy filter words
+ * [first, first + count) to or from HOST memory (checkpoint and restore: a
+ * filter is fully determined by its parameters and its words). Both run on
+ * the home stream and synchronise it before returning. write_words leaves
+ * the insert/skip counters unchanged.
+ * Errors: EINVAL (NULL pointers, range past 8 M words), ECUDA.
+ */
+int blowchoc_read_words(blowchoc_filter *f, uint64_t first, uint64_t count, uint64_t *h_dst);
+int blowchoc_write_words(blowchoc_filter *f, uint64_t first, uint64_t count, const uint64_t *h_src);
+
+/*
+ * blowchoc_clear -- reset the filter to empty (all words and counters
+ * zero), queued on `stream`. Errors: EINVAL, ECUDA.
+ */
+int blowchoc_clear(blowchoc_filter *f, void *stream);
+
+/*
+ * blowchoc_launch_count -- number of kernels this library has launched in
+ * this process so far (all filters, all threads). Diagnostic counter for
+ * measuring how many launches a piece of work takes.
+ */
+uint64_t blowchoc_launch_count(void);
+
+/* Text of the calling thread's last error ("" if none). Never NULL. */
+const char *blowchoc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLOWCHOC_H */

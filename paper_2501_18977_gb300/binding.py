@@ -1,0 +1,234 @@
+"""Python binding of the C ABI in include/blowchoc.h (argument marshalling only).
+
+Functions keep the C names. Device buffers are passed as torch CUDA tensors
+(any 8-byte dtype, contiguous) or as raw integer device addresses; streams as
+torch.cuda.Stream, raw cudaStream_t integers, or None for torch's current
+stream. Every computation runs in the CUDA library; if it is missing, loading
+fails loudly (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libblowchoc.so")
+
+BLOWCHOC_OK = 0
+BLOWCHOC_EINVAL = -1
+BLOWCHOC_ENOMEM = -2
+BLOWCHOC_ECUDA = -3
+BLOWCHOC_ETIMEOUT = -4
+BLOWCHOC_EBUDGET = -5
+
+COST_MIX, COST_LA, COST_EXP = 0, 1, 2
+
+_ERRNAMES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUDGET"}
+
+
+class BlowChocError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("blowchoc error %s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class blowchoc_params(ctypes.Structure):
+    _fields_ = [("nblocks", ctypes.c_uint64), ("k", ctypes.c_uint32),
+                ("choices", ctypes.c_uint32), ("cost", ctypes.c_int32),
+                ("bitsel", ctypes.c_uint32), ("cost_param", ctypes.c_double),
+                ("hash_seed", ctypes.c_uint64), ("batch", ctypes.c_uint64)]
+
+
+class blowchoc_filter_stats(ctypes.Structure):
+    _fields_ = [("inserted", ctypes.c_uint64), ("skipped", ctypes.c_uint64),
+                ("set_bits", ctypes.c_uint64), ("hist", ctypes.c_uint64 * 513),
+                ("fpr_est", ctypes.c_double)]
+
+
+# name -> (argtypes, restype)
+_VP, _U64, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+_SIGS = {
+    "blowchoc_create": ([ctypes.POINTER(blowchoc_params), _VP, ctypes.POINTER(_VP)], _I),
+    "blowchoc_insert": ([_VP, _VP, _U64, _VP], _I),
+    "blowchoc_query": ([_VP, _VP, _U64, _VP, _VP], _I),
+    "blowchoc_stats": ([_VP, ctypes.POINTER(blowchoc_filter_stats)], _I),
+    "blowchoc_destroy": ([_VP], _I),
+    "blowchoc_words": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_U64)], _I),
+    "blowchoc_multipliers": ([_VP, _VP, _VP], _I),
+    "blowchoc_read_words": ([_VP, _U64, _U64, _VP], _I),
+    "blowchoc_write_words": ([_VP, _U64, _U64, _VP], _I),
+    "blowchoc_clear": ([_VP, _VP], _I),
+    "blowchoc_last_error": ([], ctypes.c_char_p),
+    "blowchoc_launch_count": ([], ctypes.c_uint64),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libblowchoc.so (built by the package's build step)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build() "
+                           "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def _check(rc):
+    if rc != BLOWCHOC_OK:
+        raise BlowChocError(rc, load_library().blowchoc_last_error().decode())
+
+
+def _dev_ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if x.element_size() != 8 or not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor of 8-byte elements")
+        return x.data_ptr()
+    raise TypeError("expected a torch CUDA tensor or an integer device address")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def blowchoc_create(params: blowchoc_params, stream=None):
+    h = _VP()
+    _check(load_library().blowchoc_create(ctypes.byref(params), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def blowchoc_insert(f, d_keys, n: int, stream=None):
+    _check(load_library().blowchoc_insert(f, _dev_ptr(d_keys), int(n), _stream(stream)))
+
+
+def blowchoc_query(f, d_keys, n: int, d_bitmap, stream=None):
+    _check(load_library().blowchoc_query(f, _dev_ptr(d_keys), int(n), _dev_ptr(d_bitmap),
+                                         _stream(stream)))
+
+
+def blowchoc_stats(f) -> blowchoc_filter_stats:
+    out = blowchoc_filter_stats()
+    _check(load_library().blowchoc_stats(f, ctypes.byref(out)))
+    return out
+
+
+def blowchoc_destroy(f):
+    _check(load_library().blowchoc_destroy(f))
+
+
+def blowchoc_words(f):
+    p, n = _VP(), _U64()
+    _check(load_library().blowchoc_words(f, ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
+
+
+def blowchoc_multipliers(f):
+    a_block = (ctypes.c_uint64 * 3)()
+    a_bit = (ctypes.c_uint64 * 32)()
+    _check(load_library().blowchoc_multipliers(f, a_block, a_bit))
+    return list(a_block), list(a_bit)
+
+
+def blowchoc_read_words(f, first: int, count: int, h_dst):
+    """h_dst: a writable host buffer (numpy uint64 array) of >= count words."""
+    _check(load_library().blowchoc_read_words(f, int(first), int(count), h_dst.ctypes.data))
+
+
+def blowchoc_write_words(f, first: int, count: int, h_src):
+    _check(load_library().blowchoc_write_words(f, int(first), int(count), h_src.ctypes.data))
+
+
+def blowchoc_clear(f, stream=None):
+    _check(load_library().blowchoc_clear(f, _stream(stream)))
+
+
+def blowchoc_launch_count() -> int:
+    return int(load_library().blowchoc_launch_count())
+
+
+def blowchoc_last_error() -> str:
+    return load_library().blowchoc_last_error().decode()
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder for a zero-copy torch view."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Filter:
+    """Owning handle around blowchoc_create/destroy with tensor conveniences."""
+
+    def __init__(self, nblocks, k, choices, cost=COST_EXP, cost_param=(1 + 5 ** 0.5) / 2,
+                 hash_seed=0, batch=1, stream=None):
+        self.params = blowchoc_params(nblocks=int(nblocks), k=int(k), choices=int(choices),
+                                      cost=int(cost), bitsel=0, cost_param=float(cost_param),
+                                      hash_seed=int(hash_seed), batch=int(batch))
+        self.handle = blowchoc_create(self.params, stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            blowchoc_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def insert(self, keys, stream=None):
+        blowchoc_insert(self.handle, keys, keys.numel(), stream)
+
+    def query(self, keys, bitmap=None, stream=None):
+        import torch
+        n = keys.numel()
+        if bitmap is None:
+            bitmap = torch.empty(max((n + 63) // 64, 1), dtype=torch.int64, device=keys.device)
+        blowchoc_query(self.handle, keys, n, bitmap, stream)
+        return bitmap[: (n + 63) // 64]
+
+    def stats(self):
+        return blowchoc_stats(self.handle)
+
+    def words_view(self):
+        """Zero-copy torch int64 view of the filter words (device)."""
+        import torch
+        p, n = blowchoc_words(self.handle)
+        return torch.as_tensor(_CudaArray(p, n), device="cuda")
+
+    def words_host(self):
+        import numpy as np
+        _, n = blowchoc_words(self.handle)
+        out = np.empty(n, dtype=np.uint64)
+        blowchoc_read_words(self.handle, 0, n, out)
+        return out
+
+    def multipliers(self):
+        return blowchoc_multipliers(self.handle)
+
+    def clear(self, stream=None):
+        blowchoc_clear(self.handle, stream)

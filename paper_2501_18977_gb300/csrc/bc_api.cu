@@ -1,0 +1,346 @@
+// C ABI of the BlowChoc filter library (declared in include/blowchoc.h).
+//
+// Host side: parameter checks, hash-multiplier derivation, the cost rank
+// table, device memory, batch scheduling and kernel dispatch. Every step of
+// the filter's arithmetic on keys runs in the CUDA kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/blowchoc.h"
+#include "bc_launch.h"
+
+struct blowchoc_filter {
+    blowchoc_params p;
+    bc::DevFilter dev;             // words pointer, M, k, hash parameters
+    uint16_t *d_rank = nullptr;    // 513 x (k+1) cost ranks (c > 1)
+    unsigned long long *d_counters = nullptr;  // [0] inserted [1] skipped [2] error [3..515] hist
+    uint8_t *d_sel = nullptr;      // per-key choices of one batch
+    uint64_t sel_cap = 0;
+    cudaStream_t home = nullptr;
+    int device = 0;
+    int sms = 0;
+    int lanes_choose = 4, lanes_set = 8, lanes_query = 4;
+};
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+
+// Every bc::launch_* call launches exactly one kernel.
+inline cudaError_t counted(cudaError_t e) {
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? BLOWCHOC_ENOMEM : BLOWCHOC_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define BC_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+// splitmix64 (Steele, Lea and Flood, OOPSLA 2014): golden-ratio increment
+// followed by the published finaliser.
+uint64_t splitmix64(uint64_t &state) {
+    uint64_t z = (state += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Section 3.4: multipliers are random, odd and coprime to the hash range.
+void derive_multipliers(uint64_t seed, uint64_t M, uint32_t k, uint32_t c, uint64_t *a_block,
+                        uint64_t *a_bit) {
+    uint64_t st = seed;
+    for (uint32_t i = 0; i < c; ++i) {
+        uint64_t a;
+        do a = splitmix64(st) | 1ull;
+        while (gcd64(a, M) != 1);
+        a_block[i] = a;
+    }
+    for (uint32_t i = 0; i < k; ++i) a_bit[i] = splitmix64(st) | 1ull;  // odd => coprime to 512
+}
+
+// Cost of Eq. 4-6 in double; j = L + a.
+double cost_value(int kind, double par, uint32_t k, uint32_t j, uint32_t a) {
+    const double dk = (double)k;
+    if (kind == BLOWCHOC_COST_MIX) return (par * dk) * std::pow((double)j / 256.0, dk) + (double)a;
+    if (kind == BLOWCHOC_COST_LA) return dk * std::pow(((double)j + par * dk) / 256.0, dk) + (double)a;
+    return std::pow(par, (double)j / 128.0) + (double)a / dk;
+}
+
+// Integer rank of every reachable (L, a) cost: equal doubles share a rank,
+// so comparing ranks on the device is comparing the doubles exactly.
+std::vector<uint16_t> rank_table(int kind, double par, uint32_t k) {
+    const uint32_t k1 = k + 1;
+    std::vector<double> cost(513 * k1, INFINITY);
+    std::vector<double> vals;
+    vals.reserve(513 * k1);
+    for (uint32_t L = 0; L <= 512; ++L)
+        for (uint32_t a = 0; a <= k && L + a <= 512; ++a) {
+            cost[L * k1 + a] = cost_value(kind, par, k, L + a, a);
+            vals.push_back(cost[L * k1 + a]);
+        }
+    std::sort(vals.begin(), vals.end());
+    vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+    std::vector<uint16_t> rank(513 * k1, 0xFFFF);
+    for (uint32_t t = 0; t < 513 * k1; ++t)
+        if (std::isfinite(cost[t]))
+            rank[t] = (uint16_t)(std::lower_bound(vals.begin(), vals.end(), cost[t]) - vals.begin());
+    return rank;
+}
+
+int check_params(const blowchoc_params *p) {
+    if (!p) return fail(BLOWCHOC_EINVAL, "params is NULL");
+    if (p->nblocks == 0 || p->nblocks > (1ull << 32))
+        return fail(BLOWCHOC_EINVAL, "nblocks must be in 1..2^32 (got %llu)", (unsigned long long)p->nblocks);
+    if (p->k < 1 || p->k > BLOWCHOC_MAX_K) return fail(BLOWCHOC_EINVAL, "k must be in 1..32 (got %u)", p->k);
+    if (p->choices < 1 || p->choices > BLOWCHOC_MAX_CHOICES)
+        return fail(BLOWCHOC_EINVAL, "choices must be in 1..3 (got %u)", p->choices);
+    if (p->cost < BLOWCHOC_COST_MIX || p->cost > BLOWCHOC_COST_EXP)
+        return fail(BLOWCHOC_EINVAL, "unknown cost kind %d", p->cost);
+    if (!std::isfinite(p->cost_param) || p->cost_param < 0.0 ||
+        (p->cost == BLOWCHOC_COST_EXP && p->cost_param <= 0.0))
+        return fail(BLOWCHOC_EINVAL, "bad cost parameter %g", p->cost_param);
+    if (p->bitsel != 0) return fail(BLOWCHOC_EINVAL, "only random bit selection (bitsel = 0) is built");
+    if (p->batch == 0) return fail(BLOWCHOC_EINVAL, "batch must be >= 1");
+    return BLOWCHOC_OK;
+}
+
+int grid_for(const blowchoc_filter *f, uint64_t work_groups, int threads_per_cta, int ctas_per_sm) {
+    const uint64_t per_cta = (uint64_t)threads_per_cta;
+    uint64_t need = (work_groups + per_cta - 1) / per_cta;
+    const uint64_t cap = (uint64_t)f->sms * (uint64_t)ctas_per_sm;
+    if (need > cap) need = cap;
+    if (need < 1) need = 1;
+    return (int)need;
+}
+
+int ensure_sel(blowchoc_filter *f, uint64_t need) {
+    if (need <= f->sel_cap) return BLOWCHOC_OK;
+    if (f->d_sel) {
+        cudaError_t e = cudaFree(f->d_sel);
+        f->d_sel = nullptr;
+        f->sel_cap = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(sel)");
+    }
+    BC_CUDA(cudaMalloc(&f->d_sel, need), "cudaMalloc(sel)");
+    f->sel_cap = need;
+    return BLOWCHOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *blowchoc_last_error(void) { return g_err.c_str(); }
+
+uint64_t blowchoc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter **out) {
+    if (!out) return fail(BLOWCHOC_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    blowchoc_filter *f = new blowchoc_filter();
+    f->p = *params;
+    f->home = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&f->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device);
+    if (e != cudaSuccess) {
+        delete f;
+        return cuda_fail(e, "no usable CUDA device");
+    }
+    bc::DevFilter &d = f->dev;
+    std::memset(&d, 0, sizeof d);
+    d.M = params->nblocks;
+    d.k = params->k;
+    d.c = params->choices;
+    if ((d.M & (d.M - 1)) == 0) {
+        uint32_t lg = 0;
+        while ((1ull << lg) < d.M) ++lg;
+        d.range_kind = bc::kRangePow2;
+        d.shift = 64 - lg;
+    } else {
+        d.range_kind = (d.M & 1) ? bc::kRangeOdd : bc::kRangeEven;
+        d.shift = 0;
+    }
+    derive_multipliers(params->hash_seed, d.M, d.k, d.c, d.a_block, d.a_bit);
+
+    const size_t wbytes = (size_t)d.M * bc::kBlockWords * sizeof(uint64_t);
+    e = cudaMalloc(&d.words, wbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_counters, 516 * sizeof(unsigned long long));
+    if (e == cudaSuccess && d.c > 1) {
+        std::vector<uint16_t> rank = rank_table(params->cost, params->cost_param, d.k);
+        e = cudaMalloc(&f->d_rank, rank.size() * sizeof(uint16_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(f->d_rank, rank.data(), rank.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.words, 0, wbytes, f->home);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_counters, 0, 516 * sizeof(unsigned long long), f->home);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "blowchoc_create");
+        cudaFree(d.words);
+        cudaFree(f->d_counters);
+        cudaFree(f->d_rank);
+        delete f;
+        return rc;
+    }
+    *out = f;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream) {
+    if (!f) return fail(BLOWCHOC_EINVAL, "filter is NULL");
+    if (n == 0) return BLOWCHOC_OK;
+    if (!d_keys) return fail(BLOWCHOC_EINVAL, "keys is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = (int)f->p.choices;
+    const uint64_t B = f->p.batch;
+    if (B == 1) {
+        BC_CUDA(counted(bc::launch_sequential(C, s, f->dev, d_keys, n, f->d_rank, f->d_counters)),
+                "sequential insert launch");
+        return BLOWCHOC_OK;
+    }
+    if (B <= bc::kSmallBatchMax) {
+        bc::Launch L{1, f->lanes_choose, s};
+        BC_CUDA(counted(bc::launch_small_batch(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_counters)),
+                "small-batch insert launch");
+        return BLOWCHOC_OK;
+    }
+    int rc = ensure_sel(f, std::min(B, n));
+    if (rc) return rc;
+    for (uint64_t s0 = 0; s0 < n; s0 += B) {
+        const uint64_t cnt = std::min(B, n - s0);
+        bc::Launch Lc{grid_for(f, cnt * f->lanes_choose, 256, 8), f->lanes_choose, s};
+        BC_CUDA(counted(bc::launch_choose(C, Lc, f->dev, d_keys + s0, cnt, f->d_rank, f->d_sel, f->d_counters)),
+                "choose launch");
+        bc::Launch Ls{grid_for(f, cnt * f->lanes_set, 256, 8), f->lanes_set, s};
+        BC_CUDA(counted(bc::launch_set(Ls, f->dev, d_keys + s0, cnt, f->d_sel)), "set launch");
+    }
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_query(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, uint64_t *d_bitmap,
+                   void *stream) {
+    if (!f) return fail(BLOWCHOC_EINVAL, "filter is NULL");
+    if (n == 0) return BLOWCHOC_OK;
+    if (!d_keys || !d_bitmap) return fail(BLOWCHOC_EINVAL, "keys or bitmap is NULL");
+    const uint64_t nwords = (n + 63) / 64;
+    bc::Launch L{grid_for(f, nwords * 32, 256, 8), f->lanes_query, (cudaStream_t)stream};
+    BC_CUDA(counted(bc::launch_query((int)f->p.choices, L, f->dev, d_keys, n, d_bitmap)), "query launch");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
+    if (!f || !out) return fail(BLOWCHOC_EINVAL, "filter or out is NULL");
+    unsigned long long *d_hist = f->d_counters + 3;
+    BC_CUDA(cudaMemsetAsync(d_hist, 0, 513 * sizeof(unsigned long long), f->home), "memset hist");
+    bc::Launch L{grid_for(f, (f->dev.M + 7) / 8 * 32, 256, 8), 4, f->home};
+    BC_CUDA(counted(bc::launch_stats(L, f->dev.words, f->dev.M, d_hist)), "stats launch");
+    unsigned long long h[516];
+    BC_CUDA(cudaMemcpyAsync(h, f->d_counters, sizeof h, cudaMemcpyDeviceToHost, f->home), "stats copy");
+    BC_CUDA(cudaStreamSynchronize(f->home), "stats sync");
+    std::memset(out, 0, sizeof *out);
+    out->inserted = h[0];
+    out->skipped = h[1];
+    double q = 0.0;
+    for (int L = 0; L <= 512; ++L) {
+        out->hist[L] = h[3 + L];
+        out->set_bits += (uint64_t)L * h[3 + L];
+        q += (double)h[3 + L] * std::pow((double)L / 512.0, (double)f->p.k);
+    }
+    q /= (double)f->dev.M;
+    out->fpr_est = 1.0 - std::pow(1.0 - q, (double)f->p.choices);
+    if (h[2]) return fail(BLOWCHOC_ETIMEOUT, "a bounded device wait of this filter gave up");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_destroy(blowchoc_filter *f) {
+    if (!f) return BLOWCHOC_OK;
+    cudaError_t e = cudaStreamSynchronize(f->home);
+    cudaFree(f->dev.words);
+    cudaFree(f->d_counters);
+    cudaFree(f->d_rank);
+    cudaFree(f->d_sel);
+    delete f;
+    if (e != cudaSuccess) return cuda_fail(e, "blowchoc_destroy");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_words(blowchoc_filter *f, uint64_t **d_words, uint64_t *nwords) {
+    if (!f || !d_words || !nwords) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    *d_words = f->dev.words;
+    *nwords = f->dev.M * bc::kBlockWords;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit) {
+    if (!f || !a_block || !a_bit) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    for (int i = 0; i < 3; ++i) a_block[i] = i < (int)f->dev.c ? f->dev.a_block[i] : 0;
+    for (int i = 0; i < 32; ++i) a_bit[i] = i < (int)f->dev.k ? f->dev.a_bit[i] : 0;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_read_words(blowchoc_filter *f, uint64_t first, uint64_t count, uint64_t *h_dst) {
+    if (!f || (!h_dst && count)) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    const uint64_t nw = f->dev.M * bc::kBlockWords;
+    if (first > nw || count > nw - first) return fail(BLOWCHOC_EINVAL, "word range past the filter");
+    if (count == 0) return BLOWCHOC_OK;
+    BC_CUDA(cudaMemcpyAsync(h_dst, f->dev.words + first, count * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            f->home), "read words");
+    BC_CUDA(cudaStreamSynchronize(f->home), "read words sync");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_write_words(blowchoc_filter *f, uint64_t first, uint64_t count, const uint64_t *h_src) {
+    if (!f || (!h_src && count)) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    const uint64_t nw = f->dev.M * bc::kBlockWords;
+    if (first > nw || count > nw - first) return fail(BLOWCHOC_EINVAL, "word range past the filter");
+    if (count == 0) return BLOWCHOC_OK;
+    BC_CUDA(cudaMemcpyAsync(f->dev.words + first, h_src, count * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                            f->home), "write words");
+    BC_CUDA(cudaStreamSynchronize(f->home), "write words sync");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_clear(blowchoc_filter *f, void *stream) {
+    if (!f) return fail(BLOWCHOC_EINVAL, "filter is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    BC_CUDA(cudaMemsetAsync(f->dev.words, 0, f->dev.M * bc::kBlockWords * sizeof(uint64_t), s), "clear words");
+    BC_CUDA(cudaMemsetAsync(f->d_counters, 0, 3 * sizeof(unsigned long long), s), "clear counters");
+    return BLOWCHOC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// Device-side building blocks of the BlowChoc filter kernels (sm_103a).
+//
+// A key is handled by a group of LANES consecutive lanes of a warp; lane q of
+// the group owns W = 8 / LANES consecutive 64-bit words of every 512-bit block
+// (words q*W .. q*W+W-1). One group therefore moves a whole 64-byte block with
+// one W*8-byte vector access per lane, and a warp instruction touches
+// 32 / LANES blocks, each as one contiguous 64-byte segment.
+#pragma once
+
+#include <cstdint>
+
+namespace bc {
+
+constexpr int kBlockWords = 8;  // 512 bits
+constexpr uint32_t kSkip = 0xFFu;
+
+// Hash range kinds of the linear hash (Section 3.4).
+enum : uint32_t { kRangePow2 = 0, kRangeEven = 1, kRangeOdd = 2 };
+
+// Everything a kernel needs to address one filter. Passed by value as a
+// kernel parameter, so per-thread indexing of the multipliers reads the
+// constant bank with a uniform address.
+struct DevFilter {
+    uint64_t *words;       // 8 * M words
+    uint64_t M;            // blocks
+    uint32_t k;            // bit hashes
+    uint32_t range_kind;   // kRange* for M
+    uint32_t shift;        // pow2 M: 64 - log2(M); 64 when M == 1
+    uint32_t c;            // choices (for dispatch checks)
+    uint64_t a_block[3];   // h_1..h_c multipliers
+    uint64_t a_bit[32];    // f_1..f_k multipliers
+};
+
+// h_i(x): linear hash into [M] (Section 3.4) with u = 64.
+__device__ __forceinline__ uint64_t block_addr(const DevFilter &f, uint64_t a, uint64_t x) {
+    uint64_t y = a * x;
+    if (f.range_kind == kRangePow2) return f.shift >= 64 ? 0ull : (y >> f.shift);
+    if (f.range_kind == kRangeEven) y ^= (y >> 32);
+    return y % f.M;
+}
+
+__device__ __forceinline__ uint64_t block_mult(const DevFilter &f, uint32_t i) {
+    return i == 0 ? f.a_block[0] : (i == 1 ? f.a_block[1] : f.a_block[2]);
+}
+
+// The group's share of the key's 512-bit mask: m[j] = word q*W + j of the
+// bit set F(x), with f_i(x) = top 9 bits of a'_i x (range 512, Section 3.4).
+template <int W>
+__device__ __forceinline__ void key_mask(const DevFilter &f, uint64_t x, int q, uint64_t (&m)[W]) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) m[j] = 0;
+    const uint32_t first = (uint32_t)q * W;
+    for (uint32_t i = 0; i < f.k; ++i) {
+        uint32_t p = (uint32_t)((f.a_bit[i] * x) >> 55);
+        uint32_t w = p >> 6;
+        uint64_t bit = 1ull << (p & 63);
+#pragma unroll
+        for (int j = 0; j < W; ++j) m[j] |= (w == first + (uint32_t)j) ? bit : 0ull;
+    }
+}
+
+// Vector loads of W words. NC: read-only path (filter not written during the
+// kernel). CG: L2-coherent path for kernels that read words other lanes or
+// CTAs may have OR-ed in earlier in the same launch.
+enum LoadPath { kLoadNC = 0, kLoadCG = 1 };
+
+template <int W, int PATH>
+__device__ __forceinline__ void load_words(const uint64_t *p, uint64_t (&v)[W]) {
+    if constexpr (W == 1) {
+        if constexpr (PATH == kLoadNC) v[0] = __ldg(reinterpret_cast<const unsigned long long *>(p));
+        else v[0] = __ldcg(reinterpret_cast<const unsigned long long *>(p));
+    } else if constexpr (W == 2) {
+        ulonglong2 t;
+        if constexpr (PATH == kLoadNC) t = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+        else t = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else if constexpr (W == 4) {
+        if constexpr (PATH == kLoadNC)
+            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
+        else
+            asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
+    } else {
+        static_assert(W == 8, "W must be 1, 2, 4 or 8");
+        if constexpr (PATH == kLoadNC) {
+            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
+            asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[4]), "=l"(v[5]), "=l"(v[6]), "=l"(v[7]) : "l"(p + 4));
+        } else {
+            asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
+            asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(v[4]), "=l"(v[5]), "=l"(v[6]), "=l"(v[7]) : "l"(p + 4));
+        }
+    }
+}
+
+// Streaming read of a key (read once: evict-first in L2, no L1 allocation).
+__device__ __forceinline__ uint64_t load_key(const uint64_t *p) {
+    return __ldcs(reinterpret_cast<const unsigned long long *>(p));
+}
+
+// Sum of v over the LANES lanes of this lane's group (butterfly).
+template <int LANES>
+__device__ __forceinline__ uint32_t group_sum(uint32_t v) {
+#pragma unroll
+    for (int s = LANES / 2; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s, LANES);
+    return v;
+}
+
+// Per-candidate terms of the cost: L = popcount(block) and
+// a = popcount(F(x) & ~block), packed as L | a << 16 and summed over the group.
+template <int W>
+__device__ __forceinline__ uint32_t load_and_new(const uint64_t (&blk)[W], const uint64_t (&m)[W]) {
+    uint32_t L = 0, a = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        L += __popcll(blk[j]);
+        a += __popcll(m[j] & ~blk[j]);
+    }
+    return L | (a << 16);
+}
+
+// Choice among C candidates from their (L, a) terms: kSkip if one of them
+// already holds F(x) (a == 0); otherwise the index of least rank[L][a],
+// lowest index on ties (Section 3.2). rank has (k+1) entries per load L.
+template <int C>
+__device__ __forceinline__ uint32_t choose_from_terms(const uint32_t (&la)[C], const uint16_t *rank,
+                                                      uint32_t k1) {
+    bool skip = false;
+#pragma unroll
+    for (int i = 0; i < C; ++i) skip |= ((la[i] >> 16) == 0);
+    if (skip) return kSkip;
+    if constexpr (C == 1) {
+        return 0;
+    } else {
+        uint32_t best = 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            uint32_t L = la[i] & 0xFFFFu, a = la[i] >> 16;
+            uint32_t key = ((uint32_t)rank[L * k1 + a] << 2) | (uint32_t)i;
+            best = key < best ? key : best;
+        }
+        return best & 3u;
+    }
+}
+
+}  // namespace bc

@@ -1,0 +1,298 @@
+// Insertion kernels of the BlowChoc filter (Section 3.2, Fig. 2B).
+//
+// Batch rule: the keys of one batch all decide against the filter as it is
+// when the batch starts, and the batch's bits are OR-ed in afterwards. The
+// result is therefore independent of the order of keys inside a batch and of
+// the launch configuration; B = 1 is the paper's one-key-at-a-time insertion.
+#include "bc_launch.h"
+
+namespace bc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Copies the rank table into shared memory (only needed with choices).
+template <int C>
+__device__ __forceinline__ const uint16_t *stage_rank(const uint16_t *rank_g, uint16_t *s_rank,
+                                                      uint32_t k1) {
+    if constexpr (C == 1) {
+        return rank_g;
+    } else {
+        for (uint32_t t = threadIdx.x; t < 513u * k1; t += blockDim.x) s_rank[t] = rank_g[t];
+        __syncthreads();
+        return s_rank;
+    }
+}
+
+// Decision of one key by its group: loads the C candidate blocks (the group's
+// W-word slice each), computes L and a for each and returns the choice.
+template <int C, int LANES, int PATH>
+__device__ __forceinline__ uint32_t choose_one(const DevFilter &f, uint64_t x, bool valid, int q,
+                                               const uint16_t *rank) {
+    constexpr int W = kBlockWords / LANES;
+    uint64_t m[W];
+    key_mask<W>(f, x, q, m);
+    uint64_t blk[C][W];
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const uint64_t b = block_addr(f, f.a_block[i], x);
+        if (valid) {
+            load_words<W, PATH>(f.words + b * kBlockWords + (uint64_t)q * W, blk[i]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) blk[i][j] = ~0ull;
+        }
+    }
+    uint32_t la[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) la[i] = group_sum<LANES>(load_and_new<W>(blk[i], m));
+    return choose_from_terms<C>(la, rank, f.k + 1);
+}
+
+// OR of the key's bits into block b: lane q of the group owns W words.
+template <int LANES>
+__device__ __forceinline__ void set_one(const DevFilter &f, uint64_t x, uint64_t b, int q) {
+    constexpr int W = kBlockWords / LANES;
+    uint64_t m[W];
+    key_mask<W>(f, x, q, m);
+    unsigned long long *dst =
+        reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + (uint64_t)q * W);
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if (m[j]) atomicOr(dst + j, (unsigned long long)m[j]);
+}
+
+// Sums two per-thread counters over the CTA and adds them to counters[0..1].
+__device__ __forceinline__ void flush_counts(uint32_t ins, uint32_t skp, unsigned long long *counters) {
+    __shared__ unsigned long long s_cnt[2];
+    if (threadIdx.x == 0) { s_cnt[0] = 0; s_cnt[1] = 0; }
+    __syncthreads();
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        ins += __shfl_xor_sync(kFull, ins, s);
+        skp += __shfl_xor_sync(kFull, skp, s);
+    }
+    if ((threadIdx.x & 31) == 0 && (ins | skp)) {
+        atomicAdd(&s_cnt[0], (unsigned long long)ins);
+        atomicAdd(&s_cnt[1], (unsigned long long)skp);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (s_cnt[0] | s_cnt[1])) {
+        atomicAdd(&counters[0], s_cnt[0]);
+        atomicAdd(&counters[1], s_cnt[1]);
+    }
+}
+
+// Phase 1 of a batch: every key's choice against the unchanged filter.
+template <int C, int LANES>
+__global__ void __launch_bounds__(256) choose_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                     uint64_t n, const uint16_t *__restrict__ rank_g,
+                                                     uint8_t *__restrict__ sel,
+                                                     unsigned long long *counters) {
+    extern __shared__ uint16_t s_rank[];
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    constexpr int G = 32 / LANES;
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t ins = 0, skp = 0;
+    for (uint64_t base = warp * G; base < n; base += nwarps * G) {
+        const uint64_t i = base + g;
+        const bool valid = i < n;
+        const uint64_t x = valid ? load_key(keys + i) : 0ull;
+        const uint32_t s = choose_one<C, LANES, kLoadNC>(f, x, valid, q, rank);
+        if (valid && q == 0) {
+            sel[i] = (uint8_t)s;
+            if (s == kSkip) ++skp; else ++ins;
+        }
+    }
+    flush_counts(ins, skp, counters);
+}
+
+// Phase 2 of a batch: OR every non-skipped key into its chosen block.
+template <int LANES>
+__global__ void __launch_bounds__(256) set_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                  uint64_t n, const uint8_t *__restrict__ sel) {
+    const int q = threadIdx.x % LANES;
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+    const uint64_t ngroups = ((uint64_t)gridDim.x * blockDim.x) / LANES;
+    for (uint64_t i = gid; i < n; i += ngroups) {
+        const uint32_t s = sel[i];
+        if (s == kSkip) continue;
+        const uint64_t x = load_key(keys + i);
+        set_one<LANES>(f, x, block_addr(f, block_mult(f, s), x), q);
+    }
+}
+
+// B = 1 in one warp. Lane 8i + j handles word j of candidate i (i < C); keys
+// are prefetched 32 at a time and broadcast. A key's update is visible to the
+// next key's loads through __syncwarp (the warp is the only writer).
+template <int C>
+__global__ void __launch_bounds__(32) sequential_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                        uint64_t n, const uint16_t *__restrict__ rank_g,
+                                                        unsigned long long *counters) {
+    extern __shared__ uint16_t s_rank[];
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    const int lane = threadIdx.x;
+    const int i = lane >> 3, j = lane & 7;
+    const bool active = i < C;
+    uint64_t ins = 0, skp = 0;
+    for (uint64_t base = 0; base < n; base += 32) {
+        const uint64_t mine = base + lane < n ? load_key(keys + base + lane) : 0ull;
+        const int cnt = (int)((n - base) < 32 ? (n - base) : 32);
+        for (int t = 0; t < cnt; ++t) {
+            const uint64_t x = __shfl_sync(kFull, mine, t);
+            uint64_t m[1];
+            key_mask<1>(f, x, j, m);
+            const uint64_t b = active ? block_addr(f, block_mult(f, (uint32_t)i), x) : 0ull;
+            unsigned long long *wp = reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + j);
+            const uint64_t w = active ? __ldcg(wp) : ~0ull;
+            const uint32_t v = group_sum<8>((uint32_t)__popcll(w) | ((uint32_t)__popcll(m[0] & ~w) << 16));
+            uint32_t la[C];
+#pragma unroll
+            for (int ii = 0; ii < C; ++ii) la[ii] = __shfl_sync(kFull, v, 8 * ii);
+            const uint32_t s = choose_from_terms<C>(la, rank, f.k + 1);
+            if (s == kSkip) {
+                ++skp;
+            } else {
+                ++ins;
+                if (active && (uint32_t)i == s && (m[0] & ~w)) *wp = w | m[0];
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[0], (unsigned long long)ins);
+        atomicAdd(&counters[1], (unsigned long long)skp);
+    }
+}
+
+// 1 < B <= kSmallBatchMax: one CTA, CTA barriers between the two phases of
+// every batch; choices live in shared memory. Block loads take the L2 path
+// because earlier batches of this launch have written the filter.
+template <int C, int LANES>
+__global__ void __launch_bounds__(1024) small_batch_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                           uint64_t n, uint64_t B,
+                                                           const uint16_t *__restrict__ rank_g,
+                                                           unsigned long long *counters) {
+    extern __shared__ uint16_t s_dyn[];
+    uint8_t *sel = reinterpret_cast<uint8_t *>(s_dyn);
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(sel + kSmallBatchMax);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    constexpr int G = 32 / LANES;
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t gid = threadIdx.x / LANES, ngroups = blockDim.x / LANES;
+    uint32_t ins = 0, skp = 0;
+    for (uint64_t s0 = 0; s0 < n; s0 += B) {
+        const uint32_t cnt = (uint32_t)((n - s0) < B ? (n - s0) : B);
+        for (uint32_t base = warp * G; base < cnt; base += nwarps * G) {
+            const uint32_t i = base + g;
+            const bool valid = i < cnt;
+            const uint64_t x = valid ? load_key(keys + s0 + i) : 0ull;
+            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank);
+            if (valid && q == 0) {
+                sel[i] = (uint8_t)s;
+                if (s == kSkip) ++skp; else ++ins;
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = gid; i < cnt; i += ngroups) {
+            const uint32_t s = sel[i];
+            if (s == kSkip) continue;
+            const uint64_t x = load_key(keys + s0 + i);
+            set_one<LANES>(f, x, block_addr(f, block_mult(f, s), x), q);
+        }
+        __syncthreads();
+    }
+    flush_counts(ins, skp, counters);
+}
+
+inline size_t rank_bytes(int C, uint32_t k) { return C > 1 ? 513u * (k + 1) * sizeof(uint16_t) : 0; }
+
+template <int C>
+cudaError_t choose_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                            const uint16_t *rank, uint8_t *sel, unsigned long long *counters) {
+    const size_t sm = rank_bytes(C, f.k);
+    switch (L.lanes) {
+        case 2: choose_kernel<C, 2><<<L.grid, 256, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 4: choose_kernel<C, 4><<<L.grid, 256, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 8: choose_kernel<C, 8><<<L.grid, 256, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t small_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                           uint64_t B, const uint16_t *rank, unsigned long long *counters) {
+    const size_t sm = kSmallBatchMax + rank_bytes(C, f.k);
+    cudaError_t e = cudaSuccess;
+    switch (L.lanes) {
+        case 2:
+            e = cudaFuncSetAttribute(small_batch_kernel<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) small_batch_kernel<C, 2><<<1, 1024, sm, L.stream>>>(f, keys, n, B, rank, counters);
+            break;
+        case 4:
+            e = cudaFuncSetAttribute(small_batch_kernel<C, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) small_batch_kernel<C, 4><<<1, 1024, sm, L.stream>>>(f, keys, n, B, rank, counters);
+            break;
+        case 8:
+            e = cudaFuncSetAttribute(small_batch_kernel<C, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) small_batch_kernel<C, 8><<<1, 1024, sm, L.stream>>>(f, keys, n, B, rank, counters);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_choose(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                          uint64_t n, const uint16_t *rank, uint8_t *sel,
+                          unsigned long long *counters) {
+    switch (C) {
+        case 1: return choose_dispatch<1>(L, f, keys, n, rank, sel, counters);
+        case 2: return choose_dispatch<2>(L, f, keys, n, rank, sel, counters);
+        case 3: return choose_dispatch<3>(L, f, keys, n, rank, sel, counters);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_set(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                       const uint8_t *sel) {
+    switch (L.lanes) {
+        case 1: set_kernel<1><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
+        case 2: set_kernel<2><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
+        case 4: set_kernel<4><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
+        case 8: set_kernel<8><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys,
+                              uint64_t n, const uint16_t *rank, unsigned long long *counters) {
+    const size_t sm = rank_bytes(C, f.k);
+    switch (C) {
+        case 1: sequential_kernel<1><<<1, 32, sm, s>>>(f, keys, n, rank, counters); break;
+        case 2: sequential_kernel<2><<<1, 32, sm, s>>>(f, keys, n, rank, counters); break;
+        case 3: sequential_kernel<3><<<1, 32, sm, s>>>(f, keys, n, rank, counters); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small_batch(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                               uint64_t n, uint64_t B, const uint16_t *rank,
+                               unsigned long long *counters) {
+    if (B > kSmallBatchMax) return cudaErrorInvalidValue;
+    switch (C) {
+        case 1: return small_dispatch<1>(L, f, keys, n, B, rank, counters);
+        case 2: return small_dispatch<2>(L, f, keys, n, B, rank, counters);
+        case 3: return small_dispatch<3>(L, f, keys, n, B, rank, counters);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bc

@@ -1,0 +1,46 @@
+// Host-side launchers of the BlowChoc kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bc_device.cuh"
+
+namespace bc {
+
+// Largest batch the single-CTA batch kernel holds in shared memory.
+constexpr uint64_t kSmallBatchMax = 16384;
+
+struct Launch {
+    int grid;          // CTAs
+    int lanes;         // lanes per key (1, 2, 4, 8)
+    cudaStream_t stream;
+};
+
+// Insertion, batch-synchronous (Section 3.2 with the batch rule of the
+// library): phase 1 writes each key's choice (or kSkip) to sel[0..n),
+// phase 2 OR-s the keys' bits into the chosen blocks.
+cudaError_t launch_choose(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                          uint64_t n, const uint16_t *rank, uint8_t *sel,
+                          unsigned long long *counters);
+cudaError_t launch_set(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                       const uint8_t *sel);
+
+// B = 1: one warp inserts the keys strictly one after another.
+cudaError_t launch_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys,
+                              uint64_t n, const uint16_t *rank, unsigned long long *counters);
+
+// 1 < B <= kSmallBatchMax: one CTA runs all batches with CTA barriers.
+cudaError_t launch_small_batch(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                               uint64_t n, uint64_t B, const uint16_t *rank,
+                               unsigned long long *counters);
+
+// Membership query into an LSB-first bitmap of ceil(n/64) words.
+cudaError_t launch_query(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                         uint64_t n, uint64_t *bitmap);
+
+// Load histogram: hist[L] += blocks with L set bits (hist has 513 entries).
+cudaError_t launch_stats(const Launch &L, const uint64_t *words, uint64_t M,
+                         unsigned long long *hist);
+
+}  // namespace bc

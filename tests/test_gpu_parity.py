@@ -1,0 +1,133 @@
+"""Parity of the CUDA path with the oracle, element by element.
+
+Filter words, query bitmaps, insert/skip counters and load histograms must be
+bit-identical to the oracle's on the same seeded keys, for every batch size,
+choice count, cost and hash range kind, including ragged tails and empty
+inputs. All calls go through the C ABI.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import COST_MIX, COST_LA, COST_EXP
+from oracle.oracle import GOLDEN_RATIO, bits_of_bitmap
+from tests.gpu_helpers import gpu_run, oracle_run, to_dev
+
+pytestmark = pytest.mark.gpu
+
+PHI = GOLDEN_RATIO
+
+# (M, k, c, cost, param, B, n): covers c = 1..3, all costs, pow2 / odd / even
+# ranges, M = 1, k = 1 and 32, sequential, single-CTA and multi-launch batches
+CASES = [
+    (256, 14, 2, COST_MIX, 50.0, 1, 20000),
+    (256, 14, 2, COST_MIX, 50.0, 64, 20000),
+    (256, 14, 2, COST_MIX, 50.0, 16384, 40000),
+    (256, 14, 2, COST_MIX, 50.0, 16385, 40000),
+    (256, 14, 2, COST_MIX, 50.0, 65536, 70001),
+    (1024, 16, 3, COST_LA, 3.5, 1, 30000),
+    (1024, 16, 3, COST_LA, 3.5, 1000, 30000),
+    (1024, 16, 3, COST_LA, 3.5, 20000, 50000),
+    (999, 11, 2, COST_EXP, PHI, 1, 20000),
+    (999, 11, 2, COST_EXP, PHI, 777, 20000),
+    (999, 11, 2, COST_EXP, PHI, 30000, 70000),
+    (1000, 12, 3, COST_EXP, PHI, 30000, 70000),
+    (1000, 12, 3, COST_MIX, 2.5, 5, 10000),
+    (77, 7, 1, COST_EXP, PHI, 1, 10000),
+    (4096, 7, 1, COST_MIX, 50.0, 50000, 90000),
+    (1, 3, 2, COST_MIX, 50.0, 1, 500),
+    (1, 3, 3, COST_LA, 3.5, 100, 500),
+    (2, 1, 2, COST_EXP, PHI, 17, 3000),
+    (64, 32, 3, COST_MIX, 50.0, 1, 5000),
+    (64, 32, 3, COST_EXP, PHI, 40000, 60000),
+    (6150, 10, 2, COST_LA, 3.5, 1 << 20, 100000),
+]
+
+
+@pytest.mark.parametrize("M,k,c,kind,par,B,n", CASES)
+def test_parity_small(M, k, c, kind, par, B, n):
+    seed = 1000 + M + k
+    keys = workloads.uniform_keys(M * 7 + k, n)
+    neg = workloads.disjoint_keys(M * 7 + k + 1, n // 2 + 13, keys)
+    queries = np.concatenate([keys[: n // 2 + 7], neg])
+    words, bm, st = gpu_run(M, k, c, kind, par, seed, B, keys, queries)
+    o, obm, hist, total = oracle_run(M, k, c, kind, par, seed, B, keys, queries)
+    assert np.array_equal(words, o.words)
+    assert np.array_equal(bm, obm)
+    assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
+    assert list(st.hist) == [int(v) for v in hist] and st.set_bits == total
+    assert bits_of_bitmap(bm, n // 2 + 7).all()
+
+
+def test_multipliers_match_the_oracle_derivation():
+    import paper_2501_18977_gb300 as bc
+    from oracle import derive_multipliers
+    for M, k, c in [(1 << 21, 16, 3), (6150, 11, 2), (999, 32, 3), (1, 1, 1)]:
+        f = bc.Filter(M, k, c, bc.COST_EXP, PHI, hash_seed=31337, batch=1)
+        ab, af = f.multipliers()
+        f.close()
+        oab, oaf = derive_multipliers(31337, M, k, c)
+        assert ab[:c] == [int(v) for v in oab] and af[:k] == [int(v) for v in oaf]
+
+
+def test_insert_split_into_calls_at_batch_edges():
+    """Insert calls that start at batch boundaries compose: two calls equal one."""
+    M, k, c, B = 512, 12, 2, 4096
+    keys = workloads.uniform_keys(5, 40000)
+    w1, _, s1 = gpu_run(M, k, c, COST_MIX, 50.0, 9, B, keys, keys[:0])
+    w2, _, s2 = gpu_run(M, k, c, COST_MIX, 50.0, 9, B, keys, keys[:0], chunks=[4096 * 3, 4096 * 7])
+    assert np.array_equal(w1, w2) and s1.inserted == s2.inserted
+
+
+def test_empty_and_ragged():
+    import torch
+    import paper_2501_18977_gb300 as bc
+    f = bc.Filter(128, 9, 2, bc.COST_LA, 3.5, hash_seed=3, batch=100)
+    try:
+        empty = torch.zeros(0, dtype=torch.int64, device="cuda")
+        f.insert(empty)
+        assert f.query(empty).numel() == 0
+        assert not f.words_host().any()
+        keys = workloads.uniform_keys(8, 1000)
+        f.insert(to_dev(keys))
+        for n in [1, 63, 64, 65, 127, 999, 1000]:
+            bm = torch.full(((n + 63) // 64,), -1, dtype=torch.int64, device="cuda")
+            f.query(to_dev(keys[:n]), bitmap=bm)
+            h = bm.cpu().numpy().view(np.uint64)
+            assert bits_of_bitmap(h, n).all()
+            tail = n % 64
+            if tail:
+                assert int(h[-1]) >> tail == 0
+    finally:
+        f.close()
+
+
+def test_stats_fpr_estimate_matches_measured():
+    """fpr_est of a one-choice filter predicts the measured W/N (binomial)."""
+    M, k = 4096, 8
+    n = int(M * 512 * math.log(2) / k)
+    keys = workloads.uniform_keys(17, n)
+    neg = workloads.disjoint_keys(18, 1 << 21, keys)
+    words, bm, st = gpu_run(M, k, 1, COST_EXP, PHI, 2, 1 << 16, keys, neg)
+    W = int(bits_of_bitmap(bm, len(neg)).sum())
+    q = st.fpr_est
+    sd = math.sqrt(len(neg) * q * (1 - q))
+    assert abs(W - len(neg) * q) < 4.5 * sd
+
+
+def test_config_small_uniform_full():
+    """1M uniform keys into 2^24 bits, k = 14, two choices, cost^MIX sigma = 50,
+    B = 65536 and B = 1; queries: the 1M keys plus 1M disjoint keys."""
+    M, k, c = 32768, 14, 2
+    keys = workloads.uniform_keys(1, 1000000)
+    neg = workloads.disjoint_keys(1001, 1000000, keys)
+    queries = np.concatenate([keys, neg])
+    for B in (65536, 1):
+        words, bm, st = gpu_run(M, k, c, COST_MIX, 50.0, 1, B, keys, queries)
+        o, obm, hist, total = oracle_run(M, k, c, COST_MIX, 50.0, 1, B, keys, queries)
+        assert np.array_equal(words, o.words), B
+        assert np.array_equal(bm, obm), B
+        assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
+        assert bits_of_bitmap(bm, len(keys)).all()
