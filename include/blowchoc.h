@@ -109,6 +109,34 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
 int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream);
 
 /*
+ * blowchoc_insert_noalloc -- blowchoc_insert that allocates no device memory.
+ * The paper has no counterpart: this is a library service for callers that
+ * cannot let a library call cudaMalloc, such as applications whose device
+ * memory is entirely handed out by their own allocator or fixed budget, and
+ * latency-critical loops (a request-serving loop, host code between CUDA
+ * graph replays) where an allocation may synchronise the device.
+ * Same arguments, semantics and results as blowchoc_insert (bit-identical
+ * filter words and counters). Batches of more than 16384 keys keep their
+ * per-key choices in one fixed array inside the library's device image
+ * (4 MiB, held by every GPU that loads the library until the process exits)
+ * instead of a buffer the filter allocates; smaller batches and B = 1 need no
+ * scratch at all.
+ *  - Limit: min(B, n) <= 4,194,304 keys when B > 16384; larger batches are
+ *    rejected with EINVAL and a message naming the limit.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture. Call with the filter's device current.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - All calls on a device share the one array: two of these calls whose
+ *    work overlaps on the GPU (different streams, no ordering between them)
+ *    race and give wrong results. Every choice byte of a batch is written
+ *    before it is read, so nothing needs clearing between calls.
+ * Errors: EINVAL (NULL filter, NULL keys with n > 0, batch over the limit,
+ * wrong current device), ECUDA.
+ */
+int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream);
+
+/*
  * blowchoc_query -- membership of d_keys[0..n) (Section 3.1): key t is
  * reported present iff all bits of F(x) are set in at least one of its c
  * candidate blocks. No false negatives for inserted keys.

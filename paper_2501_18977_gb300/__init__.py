@@ -7,7 +7,8 @@ Python binding of that ABI and its build step.
 from .binding import (  # noqa: F401
     BLOWCHOC_OK, BLOWCHOC_EINVAL, BLOWCHOC_ENOMEM, BLOWCHOC_ECUDA, BLOWCHOC_ETIMEOUT,
     BLOWCHOC_EBUDGET, COST_MIX, COST_LA, COST_EXP, BlowChocError, Filter,
-    blowchoc_params, blowchoc_filter_stats, blowchoc_create, blowchoc_insert, blowchoc_query,
+    blowchoc_params, blowchoc_filter_stats, blowchoc_create, blowchoc_insert,
+    blowchoc_insert_noalloc, blowchoc_query,
     blowchoc_stats, blowchoc_destroy, blowchoc_words, blowchoc_multipliers,
     blowchoc_read_words, blowchoc_write_words, blowchoc_clear, blowchoc_last_error, blowchoc_launch_count,
     load_library, exported_symbols, LIB_PATH)

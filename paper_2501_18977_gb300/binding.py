@@ -47,6 +47,7 @@ _VP, _U64, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
 _SIGS = {
     "blowchoc_create": ([ctypes.POINTER(blowchoc_params), _VP, ctypes.POINTER(_VP)], _I),
     "blowchoc_insert": ([_VP, _VP, _U64, _VP], _I),
+    "blowchoc_insert_noalloc": ([_VP, _VP, _U64, _VP], _I),
     "blowchoc_query": ([_VP, _VP, _U64, _VP, _VP], _I),
     "blowchoc_stats": ([_VP, ctypes.POINTER(blowchoc_filter_stats)], _I),
     "blowchoc_destroy": ([_VP], _I),
@@ -120,6 +121,10 @@ def blowchoc_create(params: blowchoc_params, stream=None):
 
 def blowchoc_insert(f, d_keys, n: int, stream=None):
     _check(load_library().blowchoc_insert(f, _dev_ptr(d_keys), int(n), _stream(stream)))
+
+
+def blowchoc_insert_noalloc(f, d_keys, n: int, stream=None):
+    _check(load_library().blowchoc_insert_noalloc(f, _dev_ptr(d_keys), int(n), _stream(stream)))
 
 
 def blowchoc_query(f, d_keys, n: int, d_bitmap, stream=None):

@@ -13,20 +13,9 @@
 #include <vector>
 
 #include "../../include/blowchoc.h"
+#include "bc_filter.h"
 #include "bc_launch.h"
 
-struct blowchoc_filter {
-    blowchoc_params p;
-    bc::DevFilter dev;             // words pointer, M, k, hash parameters
-    uint16_t *d_rank = nullptr;    // 513 x (k+1) cost ranks (c > 1)
-    unsigned long long *d_counters = nullptr;  // [0] inserted [1] skipped [2] error [3..515] hist
-    uint8_t *d_sel = nullptr;      // per-key choices of one batch
-    uint64_t sel_cap = 0;
-    cudaStream_t home = nullptr;
-    int device = 0;
-    int sms = 0;
-    int lanes_choose = 4, lanes_set = 8, lanes_query = 4;
-};
 
 namespace {
 
@@ -167,6 +156,17 @@ extern "C" {
 const char *blowchoc_last_error(void) { return g_err.c_str(); }
 
 uint64_t blowchoc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"
+
+void bc_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int bc_set_error(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
+extern "C" {
 
 int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter **out) {
     if (!out) return fail(BLOWCHOC_EINVAL, "out is NULL");

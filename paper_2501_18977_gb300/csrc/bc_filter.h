@@ -1,0 +1,27 @@
+// The filter handle behind the C ABI (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/blowchoc.h"
+#include "bc_device.cuh"
+
+struct blowchoc_filter {
+    blowchoc_params p;
+    bc::DevFilter dev;             // words pointer, M, k, hash parameters
+    uint16_t *d_rank = nullptr;    // 513 x (k+1) cost ranks (c > 1)
+    unsigned long long *d_counters = nullptr;  // [0] inserted [1] skipped [2] error [3..515] hist
+    uint8_t *d_sel = nullptr;      // per-key choices of one batch
+    uint64_t sel_cap = 0;
+    cudaStream_t home = nullptr;
+    int device = 0;
+    int sms = 0;
+    int lanes_choose = 4, lanes_set = 8, lanes_query = 4;
+};
+
+// Adds one to the library's launch counter (blowchoc_launch_count).
+void bc_note_launch();
+
+// Records msg as the calling thread's last error (blowchoc_last_error); returns code.
+int bc_set_error(int code, const char *msg);
