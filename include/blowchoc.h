@@ -203,6 +203,47 @@ int blowchoc_clear(blowchoc_filter *f, void *stream);
  */
 uint64_t blowchoc_launch_count(void);
 
+/*
+ * Launch configuration of a filter's kernels. It never changes any result
+ * (words, bitmaps, counters are identical for every valid setting); it only
+ * changes speed. Defaults are set at create.
+ *   lanes_choose, lanes_set, lanes_query: lanes of a warp that share one key
+ *       (1, 2, 4 or 8); each lane owns 8/lanes words of every 512-bit block.
+ *   query_early: 1 = load candidate i+1 only if the key was not found in
+ *       candidates 1..i (fewer block reads for members); 0 = load all first.
+ *   ctas_per_sm: grid size of the grid-wide kernels, in CTAs per SM (1..16;
+ *       the persistent insert caps it at what is co-resident).
+ *   persistent: 1 = an insert of batches above 16384 keys runs as one
+ *       cooperative launch with grid barriers between phases (each barrier
+ *       wait is bounded; on expiry the filter's error word is set and
+ *       blowchoc_stats returns ETIMEOUT); 0 = two launches per batch.
+ *       lanes_choose then applies to both phases.
+ */
+typedef struct {
+    uint32_t lanes_choose;
+    uint32_t lanes_set;
+    uint32_t lanes_query;
+    uint32_t query_early;
+    uint32_t ctas_per_sm;
+    uint32_t persistent;
+} blowchoc_tuning;
+
+/* Read / replace a filter's launch configuration. set_tuning checks every
+ * field and changes nothing on error. Errors: EINVAL. */
+int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out);
+int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t);
+
+/*
+ * blowchoc_gather_probe -- measurement aid, not part of the filter: reads
+ * nreads pseudo-random whole 64-byte blocks of d_words[0 .. 8 nblocks) (the
+ * access pattern of insert and query) with `lanes` lanes per block (1, 2, 4
+ * or 8) on SMs x ctas_per_sm CTAs, and writes one folded word per warp to
+ * d_sink (at least SMs x ctas_per_sm x 8 words). Timed by the caller, it
+ * gives the random-sector ceiling of the device. Errors: EINVAL, ECUDA.
+ */
+int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, uint64_t nreads, uint64_t seed,
+                          uint32_t lanes, uint32_t ctas_per_sm, uint64_t *d_sink, void *stream);
+
 /* Text of the calling thread's last error ("" if none). Never NULL. */
 const char *blowchoc_last_error(void);
 

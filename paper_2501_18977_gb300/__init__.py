@@ -11,4 +11,5 @@ from .binding import (  # noqa: F401
     blowchoc_insert_noalloc, blowchoc_query,
     blowchoc_stats, blowchoc_destroy, blowchoc_words, blowchoc_multipliers,
     blowchoc_read_words, blowchoc_write_words, blowchoc_clear, blowchoc_last_error, blowchoc_launch_count,
+    blowchoc_tuning, blowchoc_get_tuning, blowchoc_set_tuning, blowchoc_gather_probe,
     load_library, exported_symbols, LIB_PATH)

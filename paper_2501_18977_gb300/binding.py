@@ -42,6 +42,12 @@ class blowchoc_filter_stats(ctypes.Structure):
                 ("fpr_est", ctypes.c_double)]
 
 
+class blowchoc_tuning(ctypes.Structure):
+    _fields_ = [("lanes_choose", ctypes.c_uint32), ("lanes_set", ctypes.c_uint32),
+                ("lanes_query", ctypes.c_uint32), ("query_early", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32)]
+
+
 # name -> (argtypes, restype)
 _VP, _U64, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
 _SIGS = {
@@ -58,6 +64,9 @@ _SIGS = {
     "blowchoc_clear": ([_VP, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
+    "blowchoc_gather_probe": ([_VP, _U64, _U64, _U64, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP], _I),
+    "blowchoc_get_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
+    "blowchoc_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
 }
 
 _lib = None
@@ -168,6 +177,23 @@ def blowchoc_clear(f, stream=None):
     _check(load_library().blowchoc_clear(f, _stream(stream)))
 
 
+def blowchoc_get_tuning(f) -> blowchoc_tuning:
+    out = blowchoc_tuning()
+    _check(load_library().blowchoc_get_tuning(f, ctypes.byref(out)))
+    return out
+
+
+def blowchoc_set_tuning(f, t: blowchoc_tuning):
+    _check(load_library().blowchoc_set_tuning(f, ctypes.byref(t)))
+
+
+def blowchoc_gather_probe(d_words, nblocks: int, nreads: int, seed: int, lanes: int,
+                          ctas_per_sm: int, d_sink, stream=None):
+    _check(load_library().blowchoc_gather_probe(_dev_ptr(d_words), int(nblocks), int(nreads),
+                                                int(seed), int(lanes), int(ctas_per_sm),
+                                                _dev_ptr(d_sink), _stream(stream)))
+
+
 def blowchoc_launch_count() -> int:
     return int(load_library().blowchoc_launch_count())
 
@@ -237,3 +263,12 @@ class Filter:
 
     def clear(self, stream=None):
         blowchoc_clear(self.handle, stream)
+
+    def tuning(self):
+        return blowchoc_get_tuning(self.handle)
+
+    def set_tuning(self, **kw):
+        t = blowchoc_get_tuning(self.handle)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        blowchoc_set_tuning(self.handle, t)

@@ -20,6 +20,7 @@
 namespace {
 
 thread_local std::string g_err;
+constexpr size_t kCounterWords = 520;  // see blowchoc_filter::d_counters
 std::atomic<uint64_t> g_launches{0};
 
 // Every bc::launch_* call launches exactly one kernel.
@@ -200,7 +201,7 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
 
     const size_t wbytes = (size_t)d.M * bc::kBlockWords * sizeof(uint64_t);
     e = cudaMalloc(&d.words, wbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_counters, 516 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_counters, kCounterWords * sizeof(unsigned long long));
     if (e == cudaSuccess && d.c > 1) {
         std::vector<uint16_t> rank = rank_table(params->cost, params->cost_param, d.k);
         e = cudaMalloc(&f->d_rank, rank.size() * sizeof(uint16_t));
@@ -208,7 +209,7 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
             e = cudaMemcpy(f->d_rank, rank.data(), rank.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d.words, 0, wbytes, f->home);
-    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_counters, 0, 516 * sizeof(unsigned long long), f->home);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_counters, 0, kCounterWords * sizeof(unsigned long long), f->home);
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "blowchoc_create");
         cudaFree(d.words);
@@ -241,12 +242,20 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
     }
     int rc = ensure_sel(f, std::min(B, n));
     if (rc) return rc;
+    if (f->persistent) {
+        bc::Launch L{f->sms * f->ctas_per_sm, f->lanes_choose, s};
+        unsigned int *bar = reinterpret_cast<unsigned int *>(f->d_counters + 516);
+        BC_CUDA(counted(bc::launch_persistent_insert(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_sel,
+                                                     f->d_counters, bar, f->sms)),
+                "persistent insert launch");
+        return BLOWCHOC_OK;
+    }
     for (uint64_t s0 = 0; s0 < n; s0 += B) {
         const uint64_t cnt = std::min(B, n - s0);
-        bc::Launch Lc{grid_for(f, cnt * f->lanes_choose, 256, 8), f->lanes_choose, s};
+        bc::Launch Lc{grid_for(f, cnt * f->lanes_choose, 256, f->ctas_per_sm), f->lanes_choose, s};
         BC_CUDA(counted(bc::launch_choose(C, Lc, f->dev, d_keys + s0, cnt, f->d_rank, f->d_sel, f->d_counters)),
                 "choose launch");
-        bc::Launch Ls{grid_for(f, cnt * f->lanes_set, 256, 8), f->lanes_set, s};
+        bc::Launch Ls{grid_for(f, cnt * f->lanes_set, 256, f->ctas_per_sm), f->lanes_set, s};
         BC_CUDA(counted(bc::launch_set(Ls, f->dev, d_keys + s0, cnt, f->d_sel)), "set launch");
     }
     return BLOWCHOC_OK;
@@ -258,7 +267,7 @@ int blowchoc_query(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, uint6
     if (n == 0) return BLOWCHOC_OK;
     if (!d_keys || !d_bitmap) return fail(BLOWCHOC_EINVAL, "keys or bitmap is NULL");
     const uint64_t nwords = (n + 63) / 64;
-    bc::Launch L{grid_for(f, nwords * 32, 256, 8), f->lanes_query, (cudaStream_t)stream};
+    bc::Launch L{grid_for(f, nwords * 32, 256, f->ctas_per_sm), f->lanes_query, (cudaStream_t)stream, f->query_early};
     BC_CUDA(counted(bc::launch_query((int)f->p.choices, L, f->dev, d_keys, n, d_bitmap)), "query launch");
     return BLOWCHOC_OK;
 }
@@ -332,6 +341,34 @@ int blowchoc_write_words(blowchoc_filter *f, uint64_t first, uint64_t count, con
     BC_CUDA(cudaMemcpyAsync(f->dev.words + first, h_src, count * sizeof(uint64_t), cudaMemcpyHostToDevice,
                             f->home), "write words");
     BC_CUDA(cudaStreamSynchronize(f->home), "write words sync");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
+    if (!f || !out) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    out->lanes_choose = (uint32_t)f->lanes_choose;
+    out->lanes_set = (uint32_t)f->lanes_set;
+    out->lanes_query = (uint32_t)f->lanes_query;
+    out->query_early = (uint32_t)f->query_early;
+    out->ctas_per_sm = (uint32_t)f->ctas_per_sm;
+    out->persistent = (uint32_t)f->persistent;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
+    if (!f || !t) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    auto lanes_ok = [](uint32_t l) { return l == 1 || l == 2 || l == 4 || l == 8; };
+    if (!lanes_ok(t->lanes_choose) || !lanes_ok(t->lanes_set) || !lanes_ok(t->lanes_query))
+        return fail(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
+    if (t->query_early > 1) return fail(BLOWCHOC_EINVAL, "query_early must be 0 or 1");
+    if (t->ctas_per_sm < 1 || t->ctas_per_sm > 16) return fail(BLOWCHOC_EINVAL, "ctas_per_sm must be in 1..16");
+    if (t->persistent > 1) return fail(BLOWCHOC_EINVAL, "persistent must be 0 or 1");
+    f->lanes_choose = (int)t->lanes_choose;
+    f->lanes_set = (int)t->lanes_set;
+    f->lanes_query = (int)t->lanes_query;
+    f->query_early = (int)t->query_early;
+    f->ctas_per_sm = (int)t->ctas_per_sm;
+    f->persistent = (int)t->persistent;
     return BLOWCHOC_OK;
 }
 

@@ -59,6 +59,41 @@ __device__ __forceinline__ void key_mask(const DevFilter &f, uint64_t x, int q, 
     }
 }
 
+// Bit multipliers staged in shared memory once per CTA, so that lanes can
+// read a'_i with a lane-dependent i.
+__device__ __forceinline__ void stage_bit_mults(const DevFilter &f, uint64_t *s_amul) {
+    for (uint32_t t = threadIdx.x; t < f.k; t += blockDim.x) s_amul[t] = f.a_bit[t];
+}
+
+// u32 stride between the shared-memory mask regions of consecutive groups:
+// 64 bytes, padded to 72 for one lane per key so that the lanes' 64-bit
+// accesses spread over all banks.
+template <int LANES>
+constexpr int region_u32() { return LANES == 1 ? 18 : 16; }
+
+// The group's share of the key's 512-bit mask, built once per group: lane q
+// hashes only the bit addresses i = q, q + LANES, ... (each f_i(x) is the top
+// 9 bits of a'_i x, Section 3.4) and ORs them into the group's 64-byte
+// shared-memory region with 32-bit atomics; after a warp barrier each lane
+// reads its W words. `region` is this group's 16 x u32 (8-byte aligned).
+// Every lane of the warp must call this (it contains warp barriers).
+template <int LANES>
+__device__ __forceinline__ void key_mask_shared(const uint64_t *s_amul, uint32_t k, uint64_t x, int q,
+                                                uint32_t *region, uint64_t (&m)[kBlockWords / LANES]) {
+    constexpr int W = kBlockWords / LANES;
+    uint64_t *r64 = reinterpret_cast<uint64_t *>(region);
+#pragma unroll
+    for (int j = 0; j < W; ++j) r64[q * W + j] = 0;
+    __syncwarp();
+    for (uint32_t i = (uint32_t)q; i < k; i += LANES) {
+        const uint32_t p = (uint32_t)((s_amul[i] * x) >> 55);
+        atomicOr(region + (p >> 5), 1u << (p & 31));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < W; ++j) m[j] = r64[q * W + j];
+}
+
 // Vector loads of W words. NC: read-only path (filter not written during the
 // kernel). CG: L2-coherent path for kernels that read words other lanes or
 // CTAs may have OR-ed in earlier in the same launch.

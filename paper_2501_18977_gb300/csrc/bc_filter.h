@@ -12,12 +12,16 @@ struct blowchoc_filter {
     bc::DevFilter dev;             // words pointer, M, k, hash parameters
     uint16_t *d_rank = nullptr;    // 513 x (k+1) cost ranks (c > 1)
     unsigned long long *d_counters = nullptr;  // [0] inserted [1] skipped [2] error [3..515] hist
+                                               // [516] grid-barrier arrivals (u32)
     uint8_t *d_sel = nullptr;      // per-key choices of one batch
     uint64_t sel_cap = 0;
     cudaStream_t home = nullptr;
     int device = 0;
     int sms = 0;
-    int lanes_choose = 4, lanes_set = 8, lanes_query = 4;
+    int lanes_choose = 2, lanes_set = 4, lanes_query = 1;
+    int query_early = 1;
+    int ctas_per_sm = 8;
+    int persistent = 1;            // insert: one cooperative launch for all batches
 };
 
 // Adds one to the library's launch counter (blowchoc_launch_count).

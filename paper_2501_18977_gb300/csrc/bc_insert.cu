@@ -24,14 +24,14 @@ __device__ __forceinline__ const uint16_t *stage_rank(const uint16_t *rank_g, ui
     }
 }
 
-// Decision of one key by its group: loads the C candidate blocks (the group's
-// W-word slice each), computes L and a for each and returns the choice.
+// Decision of one key by its group, given the group's share m of the key's
+// mask: loads the C candidate blocks (the lane's W-word slice of each),
+// computes L and a for each and returns the choice.
 template <int C, int LANES, int PATH>
 __device__ __forceinline__ uint32_t choose_one(const DevFilter &f, uint64_t x, bool valid, int q,
-                                               const uint16_t *rank) {
+                                               const uint16_t *rank,
+                                               const uint64_t (&m)[kBlockWords / LANES]) {
     constexpr int W = kBlockWords / LANES;
-    uint64_t m[W];
-    key_mask<W>(f, x, q, m);
     uint64_t blk[C][W];
 #pragma unroll
     for (int i = 0; i < C; ++i) {
@@ -51,10 +51,9 @@ __device__ __forceinline__ uint32_t choose_one(const DevFilter &f, uint64_t x, b
 
 // OR of the key's bits into block b: lane q of the group owns W words.
 template <int LANES>
-__device__ __forceinline__ void set_one(const DevFilter &f, uint64_t x, uint64_t b, int q) {
+__device__ __forceinline__ void set_one(const DevFilter &f, uint64_t b, int q,
+                                        const uint64_t (&m)[kBlockWords / LANES]) {
     constexpr int W = kBlockWords / LANES;
-    uint64_t m[W];
-    key_mask<W>(f, x, q, m);
     unsigned long long *dst =
         reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + (uint64_t)q * W);
 #pragma unroll
@@ -83,16 +82,24 @@ __device__ __forceinline__ void flush_counts(uint32_t ins, uint32_t skp, unsigne
     }
 }
 
+constexpr int kThreads = 256;  // CTA size of the grid-wide insert kernels
+
 // Phase 1 of a batch: every key's choice against the unchanged filter.
 template <int C, int LANES>
-__global__ void __launch_bounds__(256) choose_kernel(DevFilter f, const uint64_t *__restrict__ keys,
-                                                     uint64_t n, const uint16_t *__restrict__ rank_g,
-                                                     uint8_t *__restrict__ sel,
-                                                     unsigned long long *counters) {
-    extern __shared__ uint16_t s_rank[];
-    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+__global__ void __launch_bounds__(kThreads) choose_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                          uint64_t n, const uint16_t *__restrict__ rank_g,
+                                                          uint8_t *__restrict__ sel,
+                                                          unsigned long long *counters) {
     constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    extern __shared__ uint16_t s_rank[];
+    __shared__ uint64_t s_amul[32];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    stage_bit_mults(f, s_amul);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t ins = 0, skp = 0;
@@ -100,7 +107,9 @@ __global__ void __launch_bounds__(256) choose_kernel(DevFilter f, const uint64_t
         const uint64_t i = base + g;
         const bool valid = i < n;
         const uint64_t x = valid ? load_key(keys + i) : 0ull;
-        const uint32_t s = choose_one<C, LANES, kLoadNC>(f, x, valid, q, rank);
+        uint64_t m[W];
+        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+        const uint32_t s = choose_one<C, LANES, kLoadNC>(f, x, valid, q, rank, m);
         if (valid && q == 0) {
             sel[i] = (uint8_t)s;
             if (s == kSkip) ++skp; else ++ins;
@@ -111,16 +120,25 @@ __global__ void __launch_bounds__(256) choose_kernel(DevFilter f, const uint64_t
 
 // Phase 2 of a batch: OR every non-skipped key into its chosen block.
 template <int LANES>
-__global__ void __launch_bounds__(256) set_kernel(DevFilter f, const uint64_t *__restrict__ keys,
-                                                  uint64_t n, const uint8_t *__restrict__ sel) {
-    const int q = threadIdx.x % LANES;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
-    const uint64_t ngroups = ((uint64_t)gridDim.x * blockDim.x) / LANES;
-    for (uint64_t i = gid; i < n; i += ngroups) {
-        const uint32_t s = sel[i];
-        if (s == kSkip) continue;
-        const uint64_t x = load_key(keys + i);
-        set_one<LANES>(f, x, block_addr(f, block_mult(f, s), x), q);
+__global__ void __launch_bounds__(kThreads) set_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                       uint64_t n, const uint8_t *__restrict__ sel) {
+    constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    __shared__ uint64_t s_amul[32];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    stage_bit_mults(f, s_amul);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * G; base < n; base += nwarps * G) {
+        const uint64_t i = base + g;
+        const uint32_t s = i < n ? (uint32_t)sel[i] : kSkip;
+        const uint64_t x = s != kSkip ? load_key(keys + i) : 0ull;
+        uint64_t m[W];
+        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+        if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
     }
 }
 
@@ -167,22 +185,32 @@ __global__ void __launch_bounds__(32) sequential_kernel(DevFilter f, const uint6
     }
 }
 
-// 1 < B <= kSmallBatchMax: one CTA, CTA barriers between the two phases of
-// every batch; choices live in shared memory. Block loads take the L2 path
-// because earlier batches of this launch have written the filter.
+// 1 < B <= kSmallBatchMax: one CTA of kSmallThreads, CTA barriers between the
+// two phases of every batch; choices live in shared memory. Block loads take
+// the L2 path because earlier batches of this launch have written the filter.
+constexpr int kSmallThreads = 1024;
+
+template <int LANES>
+constexpr size_t small_mask_bytes() { return (kSmallThreads / 32) * (32 / LANES) * region_u32<LANES>() * 4; }
+
 template <int C, int LANES>
-__global__ void __launch_bounds__(1024) small_batch_kernel(DevFilter f, const uint64_t *__restrict__ keys,
-                                                           uint64_t n, uint64_t B,
-                                                           const uint16_t *__restrict__ rank_g,
-                                                           unsigned long long *counters) {
-    extern __shared__ uint16_t s_dyn[];
-    uint8_t *sel = reinterpret_cast<uint8_t *>(s_dyn);
-    uint16_t *s_rank = reinterpret_cast<uint16_t *>(sel + kSmallBatchMax);
-    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+__global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+                                                                    uint64_t n, uint64_t B,
+                                                                    const uint16_t *__restrict__ rank_g,
+                                                                    unsigned long long *counters) {
     constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    __shared__ uint64_t s_amul[32];
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_dyn);
+    uint8_t *sel = s_dyn + small_mask_bytes<LANES>();
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(sel + kSmallBatchMax);
+    stage_bit_mults(f, s_amul);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t gid = threadIdx.x / LANES, ngroups = blockDim.x / LANES;
     uint32_t ins = 0, skp = 0;
     for (uint64_t s0 = 0; s0 < n; s0 += B) {
         const uint32_t cnt = (uint32_t)((n - s0) < B ? (n - s0) : B);
@@ -190,20 +218,120 @@ __global__ void __launch_bounds__(1024) small_batch_kernel(DevFilter f, const ui
             const uint32_t i = base + g;
             const bool valid = i < cnt;
             const uint64_t x = valid ? load_key(keys + s0 + i) : 0ull;
-            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank);
+            uint64_t m[W];
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank, m);
             if (valid && q == 0) {
                 sel[i] = (uint8_t)s;
                 if (s == kSkip) ++skp; else ++ins;
             }
         }
         __syncthreads();
-        for (uint32_t i = gid; i < cnt; i += ngroups) {
-            const uint32_t s = sel[i];
-            if (s == kSkip) continue;
-            const uint64_t x = load_key(keys + s0 + i);
-            set_one<LANES>(f, x, block_addr(f, block_mult(f, s), x), q);
+        for (uint32_t base = warp * G; base < cnt; base += nwarps * G) {
+            const uint32_t i = base + g;
+            const uint32_t s = i < cnt ? (uint32_t)sel[i] : kSkip;
+            const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
+            uint64_t m[W];
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
         }
         __syncthreads();
+    }
+    flush_counts(ins, skp, counters);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent insertion: one cooperative launch runs every batch. Between the
+// choose phase and the set phase of a batch, and between batches, the whole
+// grid meets at a barrier, which gives exactly the batch rule above.
+
+// Clock cycles a CTA waits at a grid barrier before it gives up (about 2 s).
+constexpr long long kBarrierCycles = 4000000000ll;
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a co-resident grid. *bar counts arrivals over the
+// whole launch (zeroed before it); the barrier completes when it reaches
+// `target`. A wait past kBarrierCycles, or an error word already set by
+// another CTA, sets *err and returns false; the caller then leaves.
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int target,
+                                             unsigned long long *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const long long t0 = clock64();
+        while (ld_acquire(bar) < target) {
+            if (*reinterpret_cast<volatile unsigned long long *>(err) != 0ull ||
+                clock64() - t0 > kBarrierCycles) {
+                atomicExch(err, 1ull);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int C, int LANES>
+__global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
+    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
+    const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters,
+    unsigned int *bar) {
+    constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    extern __shared__ uint16_t s_rank[];
+    __shared__ uint64_t s_amul[32];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    stage_bit_mults(f, s_amul);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    if constexpr (C == 1) __syncthreads();
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long *err = counters + 2;
+    unsigned int target = 0;
+    uint32_t ins = 0, skp = 0;
+    for (uint64_t s0 = 0; s0 < n; s0 += B) {
+        const uint64_t cnt = (n - s0) < B ? (n - s0) : B;
+        for (uint64_t base = warp * G; base < cnt; base += nwarps * G) {
+            const uint64_t i = base + g;
+            const bool valid = i < cnt;
+            const uint64_t x = valid ? load_key(keys + s0 + i) : 0ull;
+            uint64_t m[W];
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank, m);
+            if (valid && q == 0) {
+                sel[i] = (uint8_t)s;
+                if (s == kSkip) ++skp; else ++ins;
+            }
+        }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, err)) return;
+        for (uint64_t base = warp * G; base < cnt; base += nwarps * G) {
+            const uint64_t i = base + g;
+            // written by other CTAs in this launch: read through L2
+            const uint32_t s = i < cnt ? (uint32_t)__ldcg(sel + i) : kSkip;
+            const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
+            uint64_t m[W];
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
+        }
+        if (s0 + B < n) {
+            target += gridDim.x;
+            if (!grid_barrier(bar, target, err)) return;
+        }
     }
     flush_counts(ins, skp, counters);
 }
@@ -215,38 +343,83 @@ cudaError_t choose_dispatch(const Launch &L, const DevFilter &f, const uint64_t 
                             const uint16_t *rank, uint8_t *sel, unsigned long long *counters) {
     const size_t sm = rank_bytes(C, f.k);
     switch (L.lanes) {
-        case 2: choose_kernel<C, 2><<<L.grid, 256, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
-        case 4: choose_kernel<C, 4><<<L.grid, 256, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
-        case 8: choose_kernel<C, 8><<<L.grid, 256, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 1: choose_kernel<C, 1><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 2: choose_kernel<C, 2><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 4: choose_kernel<C, 4><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 8: choose_kernel<C, 8><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+template <int C, int LANES>
+cudaError_t small_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n, uint64_t B,
+                         const uint16_t *rank, unsigned long long *counters) {
+    const size_t sm = small_mask_bytes<LANES>() + kSmallBatchMax + rank_bytes(C, f.k);
+    cudaError_t e = cudaFuncSetAttribute(small_batch_kernel<C, LANES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    small_batch_kernel<C, LANES><<<1, kSmallThreads, sm, L.stream>>>(f, keys, n, B, rank, counters);
     return cudaGetLastError();
 }
 
 template <int C>
 cudaError_t small_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                            uint64_t B, const uint16_t *rank, unsigned long long *counters) {
-    const size_t sm = kSmallBatchMax + rank_bytes(C, f.k);
-    cudaError_t e = cudaSuccess;
     switch (L.lanes) {
-        case 2:
-            e = cudaFuncSetAttribute(small_batch_kernel<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) small_batch_kernel<C, 2><<<1, 1024, sm, L.stream>>>(f, keys, n, B, rank, counters);
-            break;
-        case 4:
-            e = cudaFuncSetAttribute(small_batch_kernel<C, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) small_batch_kernel<C, 4><<<1, 1024, sm, L.stream>>>(f, keys, n, B, rank, counters);
-            break;
-        case 8:
-            e = cudaFuncSetAttribute(small_batch_kernel<C, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) small_batch_kernel<C, 8><<<1, 1024, sm, L.stream>>>(f, keys, n, B, rank, counters);
-            break;
+        case 1:  // one lane per key needs more registers than a 1024-thread CTA allows
+        case 2: return small_launch<C, 2>(L, f, keys, n, B, rank, counters);
+        case 4: return small_launch<C, 4>(L, f, keys, n, B, rank, counters);
+        case 8: return small_launch<C, 8>(L, f, keys, n, B, rank, counters);
         default: return cudaErrorInvalidValue;
     }
-    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int C, int LANES>
+cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                              uint64_t B, const uint16_t *rank, uint8_t *sel,
+                              unsigned long long *counters, unsigned int *bar, int sms) {
+    const size_t sm = rank_bytes(C, f.k);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, persistent_insert_kernel<C, LANES>, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int want = L.grid > 0 ? L.grid : 1;
+    const int grid = want < per_sm * sms ? want : per_sm * sms;
+    e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), L.stream);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&f, (void *)&keys, (void *)&n, (void *)&B, (void *)&rank,
+                    (void *)&sel, (void *)&counters, (void *)&bar};
+    return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES>, dim3(grid),
+                                       dim3(kThreads), args, sm, L.stream);
+}
+
+template <int C>
+cudaError_t persistent_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                uint64_t B, const uint16_t *rank, uint8_t *sel,
+                                unsigned long long *counters, unsigned int *bar, int sms) {
+    switch (L.lanes) {
+        case 1: return persistent_launch<C, 1>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 2: return persistent_launch<C, 2>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 4: return persistent_launch<C, 4>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 8: return persistent_launch<C, 8>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
+
+cudaError_t launch_persistent_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                                     uint64_t n, uint64_t B, const uint16_t *rank, uint8_t *sel,
+                                     unsigned long long *counters, unsigned int *bar, int sms) {
+    switch (C) {
+        case 1: return persistent_dispatch<1>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 2: return persistent_dispatch<2>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 3: return persistent_dispatch<3>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_choose(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                           uint64_t n, const uint16_t *rank, uint8_t *sel,
@@ -262,10 +435,10 @@ cudaError_t launch_choose(int C, const Launch &L, const DevFilter &f, const uint
 cudaError_t launch_set(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                        const uint8_t *sel) {
     switch (L.lanes) {
-        case 1: set_kernel<1><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
-        case 2: set_kernel<2><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
-        case 4: set_kernel<4><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
-        case 8: set_kernel<8><<<L.grid, 256, 0, L.stream>>>(f, keys, n, sel); break;
+        case 1: set_kernel<1><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, sel); break;
+        case 2: set_kernel<2><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, sel); break;
+        case 4: set_kernel<4><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, sel); break;
+        case 8: set_kernel<8><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, sel); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

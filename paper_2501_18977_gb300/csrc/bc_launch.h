@@ -13,8 +13,9 @@ constexpr uint64_t kSmallBatchMax = 16384;
 
 struct Launch {
     int grid;          // CTAs
-    int lanes;         // lanes per key (1, 2, 4, 8)
+    int lanes;         // lanes per key (2, 4, 8)
     cudaStream_t stream;
+    int early = 0;     // query: load later candidates only while not yet found
 };
 
 // Insertion, batch-synchronous (Section 3.2 with the batch rule of the
@@ -25,6 +26,14 @@ cudaError_t launch_choose(int C, const Launch &L, const DevFilter &f, const uint
                           unsigned long long *counters);
 cudaError_t launch_set(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                        const uint8_t *sel);
+
+// All batches of one insert in a single cooperative launch (grid barriers
+// between phases; every CTA co-resident). L.grid is the wanted grid, capped
+// at what fits on `sms` SMs. sel holds min(B, n) choices; bar is a zeroed
+// arrival counter; a barrier wait that times out sets counters[2].
+cudaError_t launch_persistent_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
+                                     uint64_t n, uint64_t B, const uint16_t *rank, uint8_t *sel,
+                                     unsigned long long *counters, unsigned int *bar, int sms);
 
 // B = 1: one warp inserts the keys strictly one after another.
 cudaError_t launch_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys,

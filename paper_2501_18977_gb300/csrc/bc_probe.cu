@@ -1,0 +1,68 @@
+// Random 64-byte gather probe: the ceiling that random block reads (the
+// access pattern of insert and query) reach on this device, measured beside
+// the streaming copy bandwidth.
+#include "bc_filter.h"
+#include "bc_launch.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Each group of LANES lanes reads `per_group` pseudo-random whole blocks
+// (block index from a multiplicative hash of a counter, so addresses are
+// spread uniformly) and folds them into one word per warp.
+template <int LANES>
+__global__ void __launch_bounds__(kThreads) gather_probe_kernel(const uint64_t *__restrict__ words,
+                                                                uint64_t mask_or_m, int pow2,
+                                                                uint64_t nreads, uint64_t seed,
+                                                                uint64_t *__restrict__ sink) {
+    constexpr int W = bc::kBlockWords / LANES;
+    const int lane = threadIdx.x & 31, q = lane % LANES;
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
+    const uint64_t ngroups = ((uint64_t)gridDim.x * blockDim.x) / LANES;
+    uint64_t acc = 0;
+    const uint64_t trips = (nreads + ngroups - 1) / ngroups;
+    for (uint64_t t = 0; t < trips; ++t) {
+        const uint64_t r = t * ngroups + gid;
+        const bool valid = r < nreads;
+        const uint64_t h = (r + seed) * 0x9E3779B97F4A7C15ull;
+        const uint64_t b = pow2 ? ((h >> 20) & mask_or_m) : ((h >> 20) % mask_or_m);
+        uint64_t v[W];
+        if (valid) {
+            bc::load_words<W, bc::kLoadNC>(words + b * bc::kBlockWords + (uint64_t)q * W, v);
+#pragma unroll
+            for (int j = 0; j < W; ++j) acc ^= v[j];
+        }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, s);
+    if (lane == 0) sink[((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
+}
+
+}  // namespace
+
+extern "C" int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, uint64_t nreads,
+                                     uint64_t seed, uint32_t lanes, uint32_t ctas_per_sm,
+                                     uint64_t *d_sink, void *stream) {
+    if (!d_words || !d_sink || nblocks == 0) return bc_set_error(BLOWCHOC_EINVAL, "bad probe arguments");
+    if (ctas_per_sm < 1 || ctas_per_sm > 16) return bc_set_error(BLOWCHOC_EINVAL, "ctas_per_sm must be in 1..16");
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bc_set_error(BLOWCHOC_ECUDA, "no usable CUDA device");
+    const int grid = sms * (int)ctas_per_sm;
+    const int pow2 = (nblocks & (nblocks - 1)) == 0;
+    const uint64_t mm = pow2 ? nblocks - 1 : nblocks;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (lanes) {
+        case 1: gather_probe_kernel<1><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 2: gather_probe_kernel<2><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 4: gather_probe_kernel<4><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 8: gather_probe_kernel<8><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
+        default: return bc_set_error(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bc_set_error(BLOWCHOC_ECUDA, cudaGetErrorString(e));
+    bc_note_launch();
+    return BLOWCHOC_OK;
+}

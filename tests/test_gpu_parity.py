@@ -131,3 +131,48 @@ def test_config_small_uniform_full():
         assert np.array_equal(bm, obm), B
         assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
         assert bits_of_bitmap(bm, len(keys)).all()
+
+
+@pytest.mark.parametrize("tune", [
+    dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=0, ctas_per_sm=1, persistent=0),
+    dict(lanes_choose=8, lanes_set=4, lanes_query=8, query_early=1, ctas_per_sm=3, persistent=0),
+    dict(lanes_choose=4, lanes_set=8, lanes_query=4, query_early=0, ctas_per_sm=16, persistent=0),
+    dict(lanes_choose=1, lanes_set=1, lanes_query=1, query_early=1, ctas_per_sm=2, persistent=0),
+    dict(lanes_choose=1, lanes_set=2, lanes_query=1, query_early=0, ctas_per_sm=8, persistent=1),
+    dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=1, ctas_per_sm=1, persistent=1),
+    dict(lanes_choose=8, lanes_set=2, lanes_query=4, query_early=1, ctas_per_sm=16, persistent=1),
+])
+def test_results_independent_of_launch_configuration(tune):
+    """Every launch configuration gives the oracle's words and bitmap."""
+    import paper_2501_18977_gb300 as bc
+    M, k, c, B = 4096, 16, 3, 50000
+    keys = workloads.uniform_keys(123, 200000)
+    neg = workloads.disjoint_keys(124, 100000, keys)
+    queries = np.concatenate([keys[:100000], neg])
+    f = bc.Filter(M, k, c, bc.COST_LA, 3.5, hash_seed=7, batch=B)
+    try:
+        f.set_tuning(**tune)
+        t = f.tuning()
+        assert all(getattr(t, kk) == vv for kk, vv in tune.items())
+        f.insert(to_dev(keys))
+        bm = f.query(to_dev(queries)).cpu().numpy().view(np.uint64)
+        words = f.words_host()
+    finally:
+        f.close()
+    o, obm, _, _ = oracle_run(M, k, c, COST_LA, 3.5, 7, B, keys, queries)
+    assert np.array_equal(words, o.words)
+    assert np.array_equal(bm, obm)
+
+
+def test_set_tuning_rejects_bad_values():
+    import paper_2501_18977_gb300 as bc
+    f = bc.Filter(64, 8, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=1)
+    try:
+        before = (f.tuning().lanes_query, f.tuning().ctas_per_sm)
+        for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=2),
+                    dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2)]:
+            with pytest.raises(bc.BlowChocError):
+                f.set_tuning(**bad)
+        assert (f.tuning().lanes_query, f.tuning().ctas_per_sm) == before
+    finally:
+        f.close()
