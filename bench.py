@@ -13,6 +13,9 @@ metric is keys processed (inserted + queried) per second, in Mkeys/s.
 
 --impl reference runs the CPU oracle (plain single-threaded C) on a bounded
 sample of the same workload, as the reference arm.
+
+Other measurements (--workload): `gather` sweeps the random 64-byte gather
+ceiling of the device over footprints from 2 MiB to 4 GiB.
 """
 import argparse
 import json
@@ -41,11 +44,12 @@ COST_LA = 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["dna", "gather"], default="dna")
     return ap.parse_args()
 
 
@@ -83,7 +87,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -126,6 +130,73 @@ def peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def csrc_sha256():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2501_18977_gb300", "csrc", "*"))):
+        if p.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(p).encode())
+            with open(p, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None if the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("csrc_sha256") != csrc_sha256() or kernel not in d.get("kernels", {}):
+        return None
+    return d["kernels"][kernel]["dram_bytes_per_launch"]
+
+
+def gather_ceiling(bc, torch, nblocks, words=None, nreads=50_000_000, lanes=2, cps=16):
+    """Random whole-block read rate (GB/s of 64-byte blocks) over `nblocks`
+    blocks, best of 3, with the library's gather probe."""
+    own = words is None
+    if own:
+        words = torch.ones(nblocks * 8, dtype=torch.int64, device="cuda")
+    sink = torch.empty(4096 * 16, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    best = None
+    for r in range(4):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        bc.blowchoc_gather_probe(words, nblocks, nreads, r, lanes, cps, sink, s)
+        b.record(s)
+        torch.cuda.synchronize()
+        if r:
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+    if own:
+        del words
+    return nreads * 64 / (best / 1e3) / 1e9
+
+
+def run_gather(args):
+    import torch
+    import paper_2501_18977_gb300 as bc
+    out = []
+    for mib in [2, 64, 128, 512, 4096]:
+        nb = mib * (1 << 20) // 64
+        best = (0.0, None)
+        for lanes in (1, 2, 4, 8):
+            for cps in (4, 8, 16):
+                g = gather_ceiling(bc, torch, nb, nreads=100_000_000, lanes=lanes, cps=cps)
+                if g > best[0]:
+                    best = (g, (lanes, cps))
+        out.append({"footprint_mib": mib, "gbs": round(best[0], 1), "lanes": best[1][0],
+                    "ctas_per_sm": best[1][1]})
+    print(json.dumps({"workload": "gather_ceiling", "unit": "GB/s of whole 64-byte blocks",
+                      "reads": 100_000_000, "results": out}))
 
 
 def golden_pbar():
@@ -195,6 +266,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "gather":
+        run_gather(args)
         return
     import torch
     import torch.distributed as dist
@@ -325,7 +399,12 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(keys, queries, 300_000, 600_000)
 
-    dominant = "query" if qry_ms >= ins_ms else "insert"
+    dominant = "query_kernel" if qry_ms >= ins_ms else "persistent_insert_kernel"
+    dom_ms = qry_ms if dominant == "query_kernel" else ins_ms
+    dom_gbs = q_gbs if dominant == "query_kernel" else i_gbs
+    traffic = ncu_traffic(dominant)
+    ceil_filter = gather_ceiling(bc, torch, CONFIG["nblocks"])
+    ceil_hbm = gather_ceiling(bc, torch, 1 << 26)
     out = {
         "metric": "insert+query throughput (DNA 31-mers, c=3, k=16, cost^LA)",
         "value": round(value, 3), "unit": "Mkeys/s", "n_gpus": world, "steps": args.steps,
@@ -337,12 +416,14 @@ def main():
         "query_mkeys_s": round(n_q / (qry_ms / 1e3) / 1e6, 2),
         "phase_ms": {"clear+insert": round(ins_ms, 4), "query": round(qry_ms, 4),
                      "stats": round(sta_ms, 4)},
-        "roofline": {"bound": "hbm", "kernel": "query_kernel" if dominant == "query" else
-                     "insert (choose_kernel + set_kernel)",
-                     "achieved": round(q_gbs if dominant == "query" else i_gbs, 1),
-                     "peak": peak, "unit": "GB/s",
-                     "frac": round((q_gbs if dominant == "query" else i_gbs) / peak, 4),
-                     "traffic": None, "peak_source": peak_src, "pbar": pbar, "pbar_source": pbar_src},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(dom_gbs, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(dom_gbs / peak, 4),
+                     "traffic": (round(traffic / 1e9, 4) if traffic else None),
+                     "traffic_unit": "GB per launch (ncu dram read+write)",
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+                     "launch_ms": round(dom_ms, 4), "pbar": pbar, "pbar_source": pbar_src,
+                     "gather_ceiling_gbs": {"filter_footprint_128MiB": round(ceil_filter, 1),
+                                            "hbm_4GiB": round(ceil_hbm, 1)}},
         "roofline_other": {"insert_gbs": round(i_gbs, 1), "insert_frac": round(i_gbs / peak, 4),
                            "query_gbs": round(q_gbs, 1), "query_frac": round(q_gbs / peak, 4)},
         "skip_rate": round(skip_rate, 6), "inserted": st.inserted, "skipped": st.skipped,
