@@ -15,7 +15,10 @@ metric is keys processed (inserted + queried) per second, in Mkeys/s.
 sample of the same workload, as the reference arm.
 
 Other measurements (--workload): `gather` sweeps the random 64-byte gather
-ceiling of the device over footprints from 2 MiB to 4 GiB.
+ceiling of the device over footprints from 2 MiB to 4 GiB; `many` runs 256
+independent filters of lognormal sizes (k = 11, c = 2, cost^EXP) as plain
+per-filter calls, as one launch per phase over a work list, and as a replayed
+CUDA graph, and checks that all three give the same words and bitmaps.
 """
 import argparse
 import json
@@ -49,7 +52,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["dna", "gather"], default="dna")
+    ap.add_argument("--workload", choices=["dna", "gather", "many"], default="dna")
     return ap.parse_args()
 
 
@@ -199,6 +202,97 @@ def run_gather(args):
                       "reads": 100_000_000, "results": out}))
 
 
+def run_many(args):
+    """256 filters (lognormal key counts, median 200,000; 16 bits per key; k = 11,
+    c = 2, cost^EXP beta = golden ratio; B_f = 2^floor(log2(M_f / 2))): all
+    inserts, then all queries (half members), three ways."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    cfg = workloads.many_filter_config()
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    filters, dks, dqs, bms = [], [], [], []
+    for it in cfg:
+        keys, queries = workloads.many_filter_keys(it)
+        filters.append(bc.Filter(it["M"], 11, 2, bc.COST_EXP, phi, hash_seed=it["key_seed"],
+                                 batch=it["B"]))
+        dks.append(torch.from_numpy(keys.view(np.int64)).cuda())
+        dqs.append(torch.from_numpy(queries.view(np.int64)).cuda())
+        bms.append(torch.zeros(max(1, (len(queries) + 63) // 64), dtype=torch.int64, device="cuda"))
+    n_ins = sum(it["n"] for it in cfg)
+    n_q = sum(d.numel() for d in dqs)
+    s = torch.cuda.current_stream()
+    ins = [(f, d, d.numel(), None) for f, d in zip(filters, dks)]
+    qry = [(f, d, d.numel(), b) for f, d, b in zip(filters, dqs, bms)]
+    batch = bc.Batch()
+    best = batch.autotune(ins, qry)
+
+    def clear_all():
+        for f in filters:
+            f.clear(s)
+
+    def plain():
+        for f, d in zip(filters, dks):
+            f.insert(d, s)
+        for f, d, b in zip(filters, dqs, bms):
+            f.query(d, b, s)
+
+    def batched():
+        batch.insert_many(ins, s)
+        batch.query_many(qry, s)
+
+    batch.record(ins, qry)
+
+    def graph():
+        batch.replay(s)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            clear_all()
+            fn()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(reps):
+            clear_all()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        return total / reps
+
+    results, digests = {}, {}
+    for name, fn in (("plain", plain), ("batched", batched), ("graph", graph)):
+        launches0 = bc.blowchoc_launch_count()
+        ms = timed(fn, args.steps)
+        launches = (bc.blowchoc_launch_count() - launches0) // (args.steps + 2)
+        words = [f.words_host() for f in filters]
+        bits = [b.cpu().numpy().copy() for b in bms]
+        digests[name] = (words, bits)
+        results[name] = {"ms": round(ms, 4), "mkeys_s": round((n_ins + n_q) / (ms / 1e3) / 1e6, 2),
+                         "launches": int(launches)}
+    same = all(all(np.array_equal(a, b) for a, b in zip(digests[n][0], digests["plain"][0])) and
+               all(np.array_equal(a, b) for a, b in zip(digests[n][1], digests["plain"][1]))
+               for n in ("batched", "graph"))
+    st = [f.stats() for f in filters]
+    out = {"workload": "many_filters_256", "metric": "insert+query throughput, 256 filters",
+           "unit": "Mkeys/s", "n_insert": n_ins, "n_query": n_q,
+           "filters": len(cfg), "filter_mib": round(sum(it["M"] for it in cfg) * 64 / 2**20, 1),
+           "results": results,
+           "batched_vs_plain": round(results["plain"]["ms"] / results["batched"]["ms"], 3),
+           "graph_vs_plain": round(results["plain"]["ms"] / results["graph"]["ms"], 3),
+           "identical_words_and_bitmaps": bool(same),
+           "inserted": int(sum(x.inserted for x in st)), "skipped": int(sum(x.skipped for x in st)),
+           "autotuned": {"lanes_choose": best.lanes_choose, "lanes_query": best.lanes_query,
+                         "query_early": best.query_early, "ctas_per_sm": best.ctas_per_sm},
+           "steps": args.steps, "timing": "CUDA events per repetition, filters cleared before each"}
+    batch.close()
+    for f in filters:
+        f.close()
+    print(json.dumps(out))
+
+
 def golden_pbar():
     """Mean 1-based index of the first candidate block holding an inserted
     31-mer of this workload, as counted by the oracle (tests/golden)."""
@@ -269,6 +363,9 @@ def main():
         return
     if args.workload == "gather":
         run_gather(args)
+        return
+    if args.workload == "many":
+        run_many(args)
         return
     import torch
     import torch.distributed as dist

@@ -204,6 +204,63 @@ int blowchoc_clear(blowchoc_filter *f, void *stream);
 uint64_t blowchoc_launch_count(void);
 
 /*
+ * ---- Many filters in one launch -------------------------------------------
+ * A batch object runs the inserts (or queries) of many independent filters
+ * in one launch over a device work list, instead of one launch per filter.
+ * Each filter keeps its own parameters (M, k, hash multipliers, cost, B); the
+ * results are exactly those of blowchoc_insert / blowchoc_query called on
+ * each filter in turn. Not in the paper: a library service for workloads of
+ * many uneven filters.
+ */
+typedef struct blowchoc_batch blowchoc_batch;
+
+/* One filter's share of a many-filter call. d_bitmap is used by query only
+ * (ceil(n/64) words, same layout as blowchoc_query). */
+typedef struct {
+    blowchoc_filter *filter;
+    const uint64_t *d_keys;
+    uint64_t n;
+    uint64_t *d_bitmap;
+} blowchoc_work;
+
+/* Create / destroy a batch object on the current device. It owns the device
+ * work list, the per-filter choice scratch and a recorded graph (if any).
+ * Errors: EINVAL, ENOMEM, ECUDA. destroy accepts NULL. */
+int blowchoc_batch_create(blowchoc_batch **out);
+int blowchoc_batch_destroy(blowchoc_batch *b);
+
+/*
+ * blowchoc_insert_many -- insert items[i].d_keys into items[i].filter for
+ * every i, with each filter's own batch rule (B of that filter): round r
+ * runs the r-th batch of every filter that has one; a grid barrier separates
+ * the choose and set phases and the rounds. One cooperative launch per
+ * distinct choice count c among the items (filters with B = 1, or with
+ * B <= 16384 and more than 4096 batches, run through the single-filter
+ * kernels on the same stream instead). A filter may appear at most once
+ * per call. Stream-ordered; the batch object must not be reused for another
+ * call until this one's host-side setup has returned (it does not wait for
+ * the GPU). Errors: EINVAL (NULL pointers, count 0, repeated filter,
+ * filters on another device), ENOMEM, ECUDA.
+ */
+int blowchoc_insert_many(blowchoc_batch *b, const blowchoc_work *items, uint32_t count, void *stream);
+
+/* blowchoc_query_many -- blowchoc_query for every item, one launch per
+ * distinct c. Errors as insert_many. */
+int blowchoc_query_many(blowchoc_batch *b, const blowchoc_work *items, uint32_t count, void *stream);
+
+/*
+ * blowchoc_batch_record -- record insert_many(ins) followed by
+ * query_many(qry) (either list may be empty) as a CUDA graph held by the
+ * batch object; blowchoc_batch_replay launches it on `stream`. The recorded
+ * pointers and sizes are fixed at record time: replay repeats exactly that
+ * work (on the filters' current contents). Recording again replaces the
+ * graph. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int blowchoc_batch_record(blowchoc_batch *b, const blowchoc_work *ins, uint32_t n_ins,
+                          const blowchoc_work *qry, uint32_t n_qry);
+int blowchoc_batch_replay(blowchoc_batch *b, void *stream);
+
+/*
  * Launch configuration of a filter's kernels. It never changes any result
  * (words, bitmaps, counters are identical for every valid setting); it only
  * changes speed. Defaults are set at create.
@@ -232,6 +289,23 @@ typedef struct {
  * field and changes nothing on error. Errors: EINVAL. */
 int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out);
 int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t);
+
+/* The same for a batch object's many-filter kernels (lanes_choose applies to
+ * both insert phases; lanes_query, query_early, ctas_per_sm as above). */
+int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out);
+int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t);
+
+/*
+ * blowchoc_batch_autotune -- time insert_many + query_many of `ins` / `qry`
+ * on scratch copies of the filters (same parameters, empty; the callers'
+ * filters are not touched) for a set of launch configurations, keep the
+ * fastest on the batch object and return it in *best (may be NULL). Results
+ * never depend on the choice. Synchronises `stream`. Errors: EINVAL, ENOMEM,
+ * ECUDA.
+ */
+int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_t n_ins,
+                            const blowchoc_work *qry, uint32_t n_qry, void *stream,
+                            blowchoc_tuning *best);
 
 /*
  * blowchoc_gather_probe -- measurement aid, not part of the filter: reads

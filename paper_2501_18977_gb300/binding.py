@@ -48,6 +48,11 @@ class blowchoc_tuning(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32)]
 
 
+class blowchoc_work(ctypes.Structure):
+    _fields_ = [("filter", ctypes.c_void_p), ("d_keys", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("d_bitmap", ctypes.c_void_p)]
+
+
 # name -> (argtypes, restype)
 _VP, _U64, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
 _SIGS = {
@@ -64,6 +69,18 @@ _SIGS = {
     "blowchoc_clear": ([_VP, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
+    "blowchoc_batch_create": ([ctypes.POINTER(_VP)], _I),
+    "blowchoc_batch_destroy": ([_VP], _I),
+    "blowchoc_insert_many": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32, _VP], _I),
+    "blowchoc_query_many": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32, _VP], _I),
+    "blowchoc_batch_record": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32,
+                               ctypes.POINTER(blowchoc_work), ctypes.c_uint32], _I),
+    "blowchoc_batch_replay": ([_VP, _VP], _I),
+    "blowchoc_batch_get_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
+    "blowchoc_batch_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
+    "blowchoc_batch_autotune": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32,
+                                 ctypes.POINTER(blowchoc_work), ctypes.c_uint32, _VP,
+                                 ctypes.POINTER(blowchoc_tuning)], _I),
     "blowchoc_gather_probe": ([_VP, _U64, _U64, _U64, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP], _I),
     "blowchoc_get_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
     "blowchoc_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
@@ -192,6 +209,109 @@ def blowchoc_gather_probe(d_words, nblocks: int, nreads: int, seed: int, lanes: 
     _check(load_library().blowchoc_gather_probe(_dev_ptr(d_words), int(nblocks), int(nreads),
                                                 int(seed), int(lanes), int(ctas_per_sm),
                                                 _dev_ptr(d_sink), _stream(stream)))
+
+
+def _works(items):
+    """items: list of (filter handle or Filter, keys tensor/ptr, n, bitmap or None)."""
+    arr = (blowchoc_work * max(len(items), 1))()
+    for i, (f, keys, n, bm) in enumerate(items):
+        h = f.handle if hasattr(f, "handle") else f
+        arr[i].filter = h.value if hasattr(h, "value") else h
+        arr[i].d_keys = _dev_ptr(keys) if n else None
+        arr[i].n = int(n)
+        arr[i].d_bitmap = _dev_ptr(bm) if bm is not None else None
+    return arr, len(items)
+
+
+def blowchoc_batch_create():
+    h = _VP()
+    _check(load_library().blowchoc_batch_create(ctypes.byref(h)))
+    return h
+
+
+def blowchoc_batch_destroy(b):
+    _check(load_library().blowchoc_batch_destroy(b))
+
+
+def blowchoc_insert_many(b, items, stream=None):
+    arr, n = _works(items)
+    _check(load_library().blowchoc_insert_many(b, arr, n, _stream(stream)))
+
+
+def blowchoc_query_many(b, items, stream=None):
+    arr, n = _works(items)
+    _check(load_library().blowchoc_query_many(b, arr, n, _stream(stream)))
+
+
+def blowchoc_batch_record(b, ins, qry):
+    a1, n1 = _works(ins)
+    a2, n2 = _works(qry)
+    _check(load_library().blowchoc_batch_record(b, a1, n1, a2, n2))
+
+
+def blowchoc_batch_replay(b, stream=None):
+    _check(load_library().blowchoc_batch_replay(b, _stream(stream)))
+
+
+def blowchoc_batch_get_tuning(b) -> blowchoc_tuning:
+    out = blowchoc_tuning()
+    _check(load_library().blowchoc_batch_get_tuning(b, ctypes.byref(out)))
+    return out
+
+
+def blowchoc_batch_set_tuning(b, t: blowchoc_tuning):
+    _check(load_library().blowchoc_batch_set_tuning(b, ctypes.byref(t)))
+
+
+def blowchoc_batch_autotune(b, ins, qry, stream=None) -> blowchoc_tuning:
+    a1, n1 = _works(ins)
+    a2, n2 = _works(qry)
+    out = blowchoc_tuning()
+    _check(load_library().blowchoc_batch_autotune(b, a1, n1, a2, n2, _stream(stream),
+                                                  ctypes.byref(out)))
+    return out
+
+
+class Batch:
+    """Owning handle of a many-filter batch object."""
+
+    def __init__(self):
+        self.handle = blowchoc_batch_create()
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            blowchoc_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def insert_many(self, items, stream=None):
+        blowchoc_insert_many(self.handle, items, stream)
+
+    def query_many(self, items, stream=None):
+        blowchoc_query_many(self.handle, items, stream)
+
+    def record(self, ins, qry):
+        blowchoc_batch_record(self.handle, ins, qry)
+
+    def replay(self, stream=None):
+        blowchoc_batch_replay(self.handle, stream)
+
+    def tuning(self):
+        return blowchoc_batch_get_tuning(self.handle)
+
+    def set_tuning(self, **kw):
+        t = blowchoc_batch_get_tuning(self.handle)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        blowchoc_batch_set_tuning(self.handle, t)
+
+    def autotune(self, ins, qry, stream=None):
+        return blowchoc_batch_autotune(self.handle, ins, qry, stream)
 
 
 def blowchoc_launch_count() -> int:

@@ -5,82 +5,10 @@
 // result is therefore independent of the order of keys inside a batch and of
 // the launch configuration; B = 1 is the paper's one-key-at-a-time insertion.
 #include "bc_launch.h"
+#include "bc_phases.cuh"
 
 namespace bc {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// Copies the rank table into shared memory (only needed with choices).
-template <int C>
-__device__ __forceinline__ const uint16_t *stage_rank(const uint16_t *rank_g, uint16_t *s_rank,
-                                                      uint32_t k1) {
-    if constexpr (C == 1) {
-        return rank_g;
-    } else {
-        for (uint32_t t = threadIdx.x; t < 513u * k1; t += blockDim.x) s_rank[t] = rank_g[t];
-        __syncthreads();
-        return s_rank;
-    }
-}
-
-// Decision of one key by its group, given the group's share m of the key's
-// mask: loads the C candidate blocks (the lane's W-word slice of each),
-// computes L and a for each and returns the choice.
-template <int C, int LANES, int PATH>
-__device__ __forceinline__ uint32_t choose_one(const DevFilter &f, uint64_t x, bool valid, int q,
-                                               const uint16_t *rank,
-                                               const uint64_t (&m)[kBlockWords / LANES]) {
-    constexpr int W = kBlockWords / LANES;
-    uint64_t blk[C][W];
-#pragma unroll
-    for (int i = 0; i < C; ++i) {
-        const uint64_t b = block_addr(f, f.a_block[i], x);
-        if (valid) {
-            load_words<W, PATH>(f.words + b * kBlockWords + (uint64_t)q * W, blk[i]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < W; ++j) blk[i][j] = ~0ull;
-        }
-    }
-    uint32_t la[C];
-#pragma unroll
-    for (int i = 0; i < C; ++i) la[i] = group_sum<LANES>(load_and_new<W>(blk[i], m));
-    return choose_from_terms<C>(la, rank, f.k + 1);
-}
-
-// OR of the key's bits into block b: lane q of the group owns W words.
-template <int LANES>
-__device__ __forceinline__ void set_one(const DevFilter &f, uint64_t b, int q,
-                                        const uint64_t (&m)[kBlockWords / LANES]) {
-    constexpr int W = kBlockWords / LANES;
-    unsigned long long *dst =
-        reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + (uint64_t)q * W);
-#pragma unroll
-    for (int j = 0; j < W; ++j)
-        if (m[j]) atomicOr(dst + j, (unsigned long long)m[j]);
-}
-
-// Sums two per-thread counters over the CTA and adds them to counters[0..1].
-__device__ __forceinline__ void flush_counts(uint32_t ins, uint32_t skp, unsigned long long *counters) {
-    __shared__ unsigned long long s_cnt[2];
-    if (threadIdx.x == 0) { s_cnt[0] = 0; s_cnt[1] = 0; }
-    __syncthreads();
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        ins += __shfl_xor_sync(kFull, ins, s);
-        skp += __shfl_xor_sync(kFull, skp, s);
-    }
-    if ((threadIdx.x & 31) == 0 && (ins | skp)) {
-        atomicAdd(&s_cnt[0], (unsigned long long)ins);
-        atomicAdd(&s_cnt[1], (unsigned long long)skp);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && (s_cnt[0] | s_cnt[1])) {
-        atomicAdd(&counters[0], s_cnt[0]);
-        atomicAdd(&counters[1], s_cnt[1]);
-    }
-}
 
 constexpr int kThreads = 256;  // CTA size of the grid-wide insert kernels
 
@@ -244,44 +172,6 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
 // Persistent insertion: one cooperative launch runs every batch. Between the
 // choose phase and the set phase of a batch, and between batches, the whole
 // grid meets at a barrier, which gives exactly the batch rule above.
-
-// Clock cycles a CTA waits at a grid barrier before it gives up (about 2 s).
-constexpr long long kBarrierCycles = 4000000000ll;
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid-wide barrier of a co-resident grid. *bar counts arrivals over the
-// whole launch (zeroed before it); the barrier completes when it reaches
-// `target`. A wait past kBarrierCycles, or an error word already set by
-// another CTA, sets *err and returns false; the caller then leaves.
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int target,
-                                             unsigned long long *err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        __threadfence();
-        atomicAdd(bar, 1u);
-        const long long t0 = clock64();
-        while (ld_acquire(bar) < target) {
-            if (*reinterpret_cast<volatile unsigned long long *>(err) != 0ull ||
-                clock64() - t0 > kBarrierCycles) {
-                atomicExch(err, 1ull);
-                ok = 0;
-                break;
-            }
-            __nanosleep(100);
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 template <int C, int LANES>
 __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(

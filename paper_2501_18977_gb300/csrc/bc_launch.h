@@ -48,6 +48,16 @@ cudaError_t launch_small_batch(int C, const Launch &L, const DevFilter &f, const
 cudaError_t launch_query(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                          uint64_t n, uint64_t *bitmap);
 
+// Many-filter execution (bc_many.cu): one cooperative insert launch over the
+// rounds of a work list, and one query launch over its bitmap words.
+struct ManyItem;
+uint64_t many_tile();
+cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
+                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
+                               unsigned long long *err, int sms);
+cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
+                              uint32_t nitems, const uint32_t *prefix);
+
 // Load histogram: hist[L] += blocks with L set bits (hist has 513 entries).
 cudaError_t launch_stats(const Launch &L, const uint64_t *words, uint64_t M,
                          unsigned long long *hist);

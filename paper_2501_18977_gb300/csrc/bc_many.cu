@@ -1,0 +1,684 @@
+// Many independent filters in one launch per phase (work-list execution).
+//
+// The work list holds one entry per filter (its addressing, hash multipliers,
+// rank table, keys, batch size, choice scratch, counters, bitmap). Insertion
+// proceeds in rounds: round r runs the r-th batch of every filter that has
+// one, as a choose phase, a grid barrier, a set phase and another barrier, so
+// each filter sees exactly its own batch rule. Work inside a phase is cut
+// into tiles of kTile keys of one filter; warps take tiles in turn and find a
+// tile's filter by binary search over the round's tile prefix sums.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bc_filter.h"
+#include "bc_launch.h"
+#include "bc_phases.cuh"
+
+namespace bc {
+
+// Device work-list entry of one filter.
+struct ManyItem {
+    DevFilter f;
+    const uint16_t *rank;
+    const uint64_t *keys;
+    uint64_t n;
+    uint64_t B;
+    uint8_t *sel;                  // min(B, n) choice bytes (insert)
+    unsigned long long *counters;  // the filter's counters (inserted, skipped)
+    uint64_t *bitmap;              // query output
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint64_t kTile = 512;  // keys per insert tile
+
+// Index of the tile's item: the last f with prefix[f] <= t (prefix has
+// nitems + 1 ascending entries, prefix[0] = 0).
+__device__ __forceinline__ uint32_t find_item(const uint32_t *prefix, uint32_t nitems, uint32_t t) {
+    uint32_t lo = 0, hi = nitems;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Copies the item's addressing (not its bit multipliers) into registers and
+// its bit multipliers into the warp's shared slot.
+__device__ __forceinline__ void load_item(const ManyItem *it, DevFilter &f, uint64_t *s_amul, int lane) {
+    f.words = it->f.words;
+    f.M = it->f.M;
+    f.k = it->f.k;
+    f.range_kind = it->f.range_kind;
+    f.shift = it->f.shift;
+    f.c = it->f.c;
+    f.a_block[0] = it->f.a_block[0];
+    f.a_block[1] = it->f.a_block[1];
+    f.a_block[2] = it->f.a_block[2];
+    __syncwarp();
+    if ((uint32_t)lane < f.k) s_amul[lane] = it->f.a_bit[lane];
+    __syncwarp();
+}
+
+template <int C, int LANES>
+__global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *__restrict__ items, uint32_t nitems,
+                                                               const uint32_t *__restrict__ prefix,
+                                                               uint32_t nrounds, unsigned int *bar,
+                                                               unsigned long long *err) {
+    constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    __shared__ uint64_t s_amul[kWarps][32];
+    __shared__ __align__(16) uint32_t s_mask[kWarps * G * region_u32<LANES>()];
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned int target = 0;
+    for (uint32_t r = 0; r < nrounds; ++r) {
+        const uint32_t *pre = prefix + (uint64_t)r * (nitems + 1);
+        const uint32_t ntiles = __ldg(pre + nitems);
+        for (int phase = 0; phase < 2; ++phase) {
+            for (uint32_t t = warp; t < ntiles; t += nwarps) {
+                const uint32_t fi = find_item(pre, nitems, t);
+                const ManyItem *it = items + fi;
+                DevFilter f;
+                load_item(it, f, s_amul[wib], lane);
+                const uint64_t B = it->B, n = it->n;
+                const uint64_t bstart = (uint64_t)r * B;
+                const uint64_t bend = bstart + B < n ? bstart + B : n;
+                const uint64_t start = bstart + (uint64_t)(t - __ldg(pre + fi)) * kTile;
+                const uint64_t cnt = bend - start < kTile ? bend - start : kTile;
+                uint32_t ins = 0, skp = 0;
+                for (uint64_t base = 0; base < cnt; base += G) {
+                    const uint64_t i = start + base + g;  // key index within the filter
+                    if (phase == 0) {
+                        const bool valid = base + g < cnt;
+                        const uint64_t x = valid ? load_key(it->keys + i) : 0ull;
+                        uint64_t m[W];
+                        key_mask_shared<LANES>(s_amul[wib], f.k, x, q, region, m);
+                        const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, it->rank, m);
+                        if (valid && q == 0) {
+                            it->sel[i - bstart] = (uint8_t)s;
+                            if (s == kSkip) ++skp; else ++ins;
+                        }
+                    } else {
+                        const uint32_t s = base + g < cnt ? (uint32_t)__ldcg(it->sel + (i - bstart)) : kSkip;
+                        const uint64_t x = s != kSkip ? load_key(it->keys + i) : 0ull;
+                        uint64_t m[W];
+                        key_mask_shared<LANES>(s_amul[wib], f.k, x, q, region, m);
+                        if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
+                    }
+                }
+                if (phase == 0) {
+#pragma unroll
+                    for (int sh = 16; sh > 0; sh >>= 1) {
+                        ins += __shfl_xor_sync(kFull, ins, sh);
+                        skp += __shfl_xor_sync(kFull, skp, sh);
+                    }
+                    if (lane == 0) {
+                        if (ins) atomicAdd(&it->counters[0], (unsigned long long)ins);
+                        if (skp) atomicAdd(&it->counters[1], (unsigned long long)skp);
+                    }
+                }
+            }
+            if (phase == 1 && r + 1 == nrounds) break;
+            target += gridDim.x;
+            if (!grid_barrier(bar, target, err)) return;
+        }
+    }
+}
+
+template <int C, int LANES, bool EARLY>
+__global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__restrict__ items, uint32_t nitems,
+                                                              const uint32_t *__restrict__ prefix) {
+    constexpr int G = 32 / LANES;
+    __shared__ uint64_t s_amul[kWarps][32];
+    __shared__ __align__(16) uint32_t s_mask[kWarps * G * region_u32<LANES>()];
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t ntiles = __ldg(prefix + nitems);
+    uint32_t cur = 0xFFFFFFFFu;
+    DevFilter f;
+    const ManyItem *it = items;
+    for (uint32_t t = warp; t < ntiles; t += nwarps) {
+        const uint32_t fi = find_item(prefix, nitems, t);
+        if (fi != cur) {
+            it = items + fi;
+            load_item(it, f, s_amul[wib], lane);
+            cur = fi;
+        }
+        const uint64_t wd = t - __ldg(prefix + fi);
+        const uint64_t word = query_word<C, LANES, EARLY>(f, it->keys, it->n, wd, s_amul[wib], region, q, g);
+        if (lane == 0) it->bitmap[wd] = word;
+    }
+}
+
+template <int C, int LANES>
+cudaError_t insert_many_launch(int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
+                               const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
+                               unsigned long long *err, int sms) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_many_kernel<C, LANES>,
+                                                                  kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int g = std::min(std::max(grid, 1), per_sm * sms);
+    e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&items, (void *)&nitems, (void *)&prefix, (void *)&nrounds, (void *)&bar,
+                    (void *)&err};
+    return cudaLaunchCooperativeKernel((const void *)insert_many_kernel<C, LANES>, dim3(g), dim3(kThreads),
+                                       args, 0, s);
+}
+
+template <int C>
+cudaError_t insert_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
+                                 const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
+                                 unsigned long long *err, int sms) {
+    switch (lanes) {
+        case 1: return insert_many_launch<C, 1>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 2: return insert_many_launch<C, 2>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 4: return insert_many_launch<C, 4>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 8: return insert_many_launch<C, 8>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int C, bool EARLY>
+cudaError_t query_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
+                                const uint32_t *prefix) {
+    switch (lanes) {
+        case 1: query_many_kernel<C, 1, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 2: query_many_kernel<C, 2, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 4: query_many_kernel<C, 4, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 8: query_many_kernel<C, 8, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
+                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
+                               unsigned long long *err, int sms) {
+    switch (C) {
+        case 1: return insert_many_dispatch<1>(lanes, grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 2: return insert_many_dispatch<2>(lanes, grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 3: return insert_many_dispatch<3>(lanes, grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
+                              uint32_t nitems, const uint32_t *prefix) {
+    switch (C) {
+        case 1: return query_many_dispatch<1, false>(lanes, grid, s, items, nitems, prefix);
+        case 2: return early ? query_many_dispatch<2, true>(lanes, grid, s, items, nitems, prefix)
+                             : query_many_dispatch<2, false>(lanes, grid, s, items, nitems, prefix);
+        case 3: return early ? query_many_dispatch<3, true>(lanes, grid, s, items, nitems, prefix)
+                             : query_many_dispatch<3, false>(lanes, grid, s, items, nitems, prefix);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+uint64_t many_tile() { return kTile; }
+
+}  // namespace bc
+
+// ---------------------------------------------------------------------------
+// Host side: the batch object.
+
+namespace {
+
+using bc::ManyItem;
+
+// One call's device work list and the pinned staging it is uploaded from.
+struct ManyPlan {
+    struct Group {
+        int C;
+        uint32_t item0, nitems;   // range in the item array
+        size_t prefix0;           // offset in the prefix array
+        uint32_t nrounds;         // insert only
+    };
+    ManyItem *d_items = nullptr, *h_items = nullptr;
+    size_t d_items_cap = 0, h_items_cap = 0;
+    uint32_t *d_prefix = nullptr, *h_prefix = nullptr;
+    size_t d_prefix_cap = 0, h_prefix_cap = 0;
+    uint8_t *d_sel = nullptr;
+    size_t sel_cap = 0;
+    cudaEvent_t staged = nullptr;  // staging may be rewritten once this completed
+    std::vector<Group> groups;
+    std::vector<blowchoc_work> side;  // items run by the single-filter kernels
+};
+
+void free_plan(ManyPlan &p) {
+    cudaFree(p.d_items);
+    cudaFree(p.d_prefix);
+    cudaFree(p.d_sel);
+    cudaFreeHost(p.h_items);
+    cudaFreeHost(p.h_prefix);
+    if (p.staged) cudaEventDestroy(p.staged);
+    p = ManyPlan();
+}
+
+}  // namespace
+
+struct blowchoc_batch {
+    int device = 0;
+    int sms = 0;
+    unsigned long long *d_state = nullptr;  // [0] error word, [1] barrier arrivals (u32)
+    ManyPlan live_ins, live_qry, rec_ins, rec_qry;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int lanes_choose = 2, lanes_query = 1, query_early = 1, ctas_per_sm = 8;
+};
+
+namespace {
+
+// A filter whose insert would need more rounds than this (tiny batches over
+// many keys), or that inserts one key at a time (B = 1), runs through the
+// single-filter kernels (the sequential or single-CTA batch kernel, which need
+// no grid barrier per batch) instead of adding rounds to the whole launch.
+constexpr uint64_t kManyMaxRounds = 4096;
+
+bool side_path(const blowchoc_work &w) {
+    const uint64_t B = w.filter->p.batch;
+    return B == 1 || (B <= bc::kSmallBatchMax && (w.n + B - 1) / B > kManyMaxRounds);
+}
+
+int set_err(int code, const char *msg) { return bc_set_error(code, msg); }
+
+int cuda_err(cudaError_t e, const char *what) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    return bc_set_error(e == cudaErrorMemoryAllocation ? BLOWCHOC_ENOMEM : BLOWCHOC_ECUDA, msg);
+}
+
+#define MANY_CUDA(call, what)                                \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_err(e_, what);    \
+    } while (0)
+
+template <typename T>
+int grow_device(T *&ptr, size_t &cap, size_t need, const char *what) {
+    if (need <= cap) return BLOWCHOC_OK;
+    MANY_CUDA(cudaDeviceSynchronize(), what);  // earlier launches may still read the old buffer
+    cudaFree(ptr);
+    ptr = nullptr;
+    const size_t n = std::max(need, cap * 2);
+    cap = 0;
+    MANY_CUDA(cudaMalloc((void **)&ptr, n * sizeof(T)), what);
+    cap = n;
+    return BLOWCHOC_OK;
+}
+
+template <typename T>
+int grow_host(T *&ptr, size_t &cap, size_t need, const char *what) {
+    if (need <= cap) return BLOWCHOC_OK;
+    cudaFreeHost(ptr);
+    ptr = nullptr;
+    const size_t n = std::max(need, cap * 2);
+    cap = 0;
+    MANY_CUDA(cudaHostAlloc((void **)&ptr, n * sizeof(T), cudaHostAllocDefault), what);
+    cap = n;
+    return BLOWCHOC_OK;
+}
+
+int check_items(const blowchoc_batch *b, const blowchoc_work *items, uint32_t count, bool query) {
+    if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
+    if (count && !items) return set_err(BLOWCHOC_EINVAL, "items is NULL");
+    std::vector<const blowchoc_filter *> seen;
+    seen.reserve(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        const blowchoc_work &w = items[i];
+        if (!w.filter) return set_err(BLOWCHOC_EINVAL, "item without a filter");
+        if (w.n && !w.d_keys) return set_err(BLOWCHOC_EINVAL, "item keys are NULL");
+        if (query && w.n && !w.d_bitmap) return set_err(BLOWCHOC_EINVAL, "item bitmap is NULL");
+        if (w.filter->device != b->device) return set_err(BLOWCHOC_EINVAL, "item filter is on another device");
+        seen.push_back(w.filter);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return set_err(BLOWCHOC_EINVAL, "a filter appears twice in one many-filter call");
+    return BLOWCHOC_OK;
+}
+
+ManyItem make_item(const blowchoc_work &w) {
+    ManyItem it;
+    std::memset(&it, 0, sizeof it);
+    it.f = w.filter->dev;
+    it.rank = w.filter->d_rank;
+    it.keys = w.d_keys;
+    it.n = w.n;
+    it.B = w.filter->p.batch;
+    it.counters = w.filter->d_counters;
+    it.bitmap = w.d_bitmap;
+    return it;
+}
+
+// Builds one call's work list into `p` and uploads it on stream `s`: from
+// pinned staging, asynchronously; or with a synchronous copy if `sync`.
+int prepare(ManyPlan &p, const blowchoc_work *items, uint32_t count, bool query, cudaStream_t s,
+            bool sync) {
+    if (p.staged) MANY_CUDA(cudaEventSynchronize(p.staged), "batch staging");
+    else MANY_CUDA(cudaEventCreateWithFlags(&p.staged, cudaEventDisableTiming), "batch event");
+    p.groups.clear();
+    p.side.clear();
+    std::vector<ManyItem> list;
+    std::vector<uint32_t> prefix;
+    std::vector<size_t> sel_off;
+    size_t sel_total = 0;
+    for (int C = 1; C <= 3; ++C) {
+        ManyPlan::Group g{C, (uint32_t)list.size(), 0, prefix.size(), 0};
+        std::vector<ManyItem> mine;
+        for (uint32_t i = 0; i < count; ++i) {
+            const blowchoc_work &w = items[i];
+            if ((int)w.filter->p.choices != C || w.n == 0) continue;
+            if (!query && side_path(w)) {
+                p.side.push_back(w);
+                continue;
+            }
+            const ManyItem it = make_item(w);
+            if (!query) {
+                sel_off.push_back(sel_total);
+                sel_total += (std::min(it.B, it.n) + 15) & ~uint64_t(15);
+            }
+            mine.push_back(it);
+        }
+        if (mine.empty()) continue;
+        g.nitems = (uint32_t)mine.size();
+        if (query) {
+            prefix.push_back(0);
+            for (const ManyItem &it : mine) {
+                const uint64_t next = prefix.back() + (it.n + 63) / 64;
+                if (next > 0xFFFFFFFFull) return set_err(BLOWCHOC_EINVAL, "work list too large");
+                prefix.push_back((uint32_t)next);
+            }
+        } else {
+            uint64_t rounds = 0;
+            for (const ManyItem &it : mine) rounds = std::max<uint64_t>(rounds, (it.n + it.B - 1) / it.B);
+            if (rounds > (1u << 24)) return set_err(BLOWCHOC_EINVAL, "too many batches in one call");
+            g.nrounds = (uint32_t)rounds;
+            const uint64_t T = bc::many_tile();
+            for (uint64_t r = 0; r < rounds; ++r) {
+                prefix.push_back(0);
+                for (const ManyItem &it : mine) {
+                    const uint64_t s0 = r * it.B;
+                    const uint64_t cnt = s0 < it.n ? std::min(it.B, it.n - s0) : 0;
+                    const uint64_t next = prefix.back() + (cnt + T - 1) / T;
+                    if (next > 0xFFFFFFFFull) return set_err(BLOWCHOC_EINVAL, "work list too large");
+                    prefix.push_back((uint32_t)next);
+                }
+            }
+        }
+        list.insert(list.end(), mine.begin(), mine.end());
+        p.groups.push_back(g);
+    }
+    int rc = BLOWCHOC_OK;
+    if (!query && sel_total) {
+        rc = grow_device(p.d_sel, p.sel_cap, sel_total, "batch choice scratch");
+        if (rc) return rc;
+        for (size_t i = 0; i < list.size(); ++i) list[i].sel = p.d_sel + sel_off[i];
+    }
+    if (list.empty()) return BLOWCHOC_OK;
+    rc = grow_device(p.d_items, p.d_items_cap, list.size(), "batch work list");
+    if (!rc) rc = grow_device(p.d_prefix, p.d_prefix_cap, prefix.size(), "batch tile table");
+    if (rc) return rc;
+    if (sync) {
+        MANY_CUDA(cudaMemcpy(p.d_items, list.data(), list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice),
+                  "upload work list");
+        MANY_CUDA(cudaMemcpy(p.d_prefix, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),
+                  "upload tile table");
+        return BLOWCHOC_OK;
+    }
+    rc = grow_host(p.h_items, p.h_items_cap, list.size(), "batch staging");
+    if (!rc) rc = grow_host(p.h_prefix, p.h_prefix_cap, prefix.size(), "batch staging");
+    if (rc) return rc;
+    std::memcpy(p.h_items, list.data(), list.size() * sizeof(ManyItem));
+    std::memcpy(p.h_prefix, prefix.data(), prefix.size() * sizeof(uint32_t));
+    MANY_CUDA(cudaMemcpyAsync(p.d_items, p.h_items, list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice, s),
+              "upload work list");
+    MANY_CUDA(cudaMemcpyAsync(p.d_prefix, p.h_prefix, prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s),
+              "upload tile table");
+    MANY_CUDA(cudaEventRecord(p.staged, s), "batch event");
+    return BLOWCHOC_OK;
+}
+
+// Queues the prepared work on stream `s`.
+int launch(blowchoc_batch *b, const ManyPlan &p, bool query, cudaStream_t s) {
+    unsigned long long *err = b->d_state;
+    unsigned int *bar = reinterpret_cast<unsigned int *>(b->d_state + 1);
+    for (const ManyPlan::Group &g : p.groups) {
+        const ManyItem *items = p.d_items + g.item0;
+        const uint32_t *prefix = p.d_prefix + g.prefix0;
+        const int grid = b->sms * b->ctas_per_sm;
+        cudaError_t e;
+        if (query)
+            e = bc::launch_query_many(g.C, b->lanes_query, b->query_early != 0, grid, s, items, g.nitems, prefix);
+        else
+            e = bc::launch_insert_many(g.C, b->lanes_choose, grid, s, items, g.nitems, prefix, g.nrounds, bar, err,
+                                       b->sms);
+        if (e != cudaSuccess) return cuda_err(e, query ? "query_many launch" : "insert_many launch");
+        bc_note_launch();
+    }
+    for (const blowchoc_work &w : p.side) {
+        const int rc = blowchoc_insert(w.filter, w.d_keys, w.n, s);
+        if (rc) return rc;
+    }
+    return BLOWCHOC_OK;
+}
+
+int run_many(blowchoc_batch *b, ManyPlan &p, const blowchoc_work *items, uint32_t count, bool query,
+             cudaStream_t s) {
+    int rc = check_items(b, items, count, query);
+    if (rc) return rc;
+    if (count == 0) return BLOWCHOC_OK;
+    rc = prepare(p, items, count, query, s, false);
+    if (rc) return rc;
+    return launch(b, p, query, s);
+}
+
+bool lanes_ok(uint32_t l) { return l == 1 || l == 2 || l == 4 || l == 8; }
+
+}  // namespace
+
+extern "C" {
+
+int blowchoc_batch_create(blowchoc_batch **out) {
+    if (!out) return set_err(BLOWCHOC_EINVAL, "out is NULL");
+    *out = nullptr;
+    blowchoc_batch *b = new blowchoc_batch();
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_state, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->d_state, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(b->d_state);
+        delete b;
+        return cuda_err(e, "blowchoc_batch_create");
+    }
+    *out = b;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_destroy(blowchoc_batch *b) {
+    if (!b) return BLOWCHOC_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    free_plan(b->live_ins);
+    free_plan(b->live_qry);
+    free_plan(b->rec_ins);
+    free_plan(b->rec_qry);
+    cudaFree(b->d_state);
+    delete b;
+    if (e != cudaSuccess) return cuda_err(e, "blowchoc_batch_destroy");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_insert_many(blowchoc_batch *b, const blowchoc_work *items, uint32_t count, void *stream) {
+    if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
+    return run_many(b, b->live_ins, items, count, false, (cudaStream_t)stream);
+}
+
+int blowchoc_query_many(blowchoc_batch *b, const blowchoc_work *items, uint32_t count, void *stream) {
+    if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
+    return run_many(b, b->live_qry, items, count, true, (cudaStream_t)stream);
+}
+
+int blowchoc_batch_record(blowchoc_batch *b, const blowchoc_work *ins, uint32_t n_ins,
+                          const blowchoc_work *qry, uint32_t n_qry) {
+    if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
+    int rc = check_items(b, ins, n_ins, false);
+    if (!rc) rc = check_items(b, qry, n_qry, true);
+    if (rc) return rc;
+    if (n_ins) rc = prepare(b->rec_ins, ins, n_ins, false, nullptr, true);
+    if (!rc && n_qry) rc = prepare(b->rec_qry, qry, n_qry, true, nullptr, true);
+    if (rc) return rc;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    cudaStream_t cs;
+    MANY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "record stream");
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_err(e, "begin capture");
+    }
+    if (n_ins) rc = launch(b, b->rec_ins, false, cs);
+    if (!rc && n_qry) rc = launch(b, b->rec_qry, true, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_err(e, "end capture");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_err(e, "graph instantiate");
+    }
+    b->graph = g;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_replay(blowchoc_batch *b, void *stream) {
+    if (!b || !b->exec) return set_err(BLOWCHOC_EINVAL, "no recorded graph");
+    MANY_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "graph launch");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out) {
+    if (!b || !out) return set_err(BLOWCHOC_EINVAL, "NULL argument");
+    out->lanes_choose = (uint32_t)b->lanes_choose;
+    out->lanes_set = (uint32_t)b->lanes_choose;
+    out->lanes_query = (uint32_t)b->lanes_query;
+    out->query_early = (uint32_t)b->query_early;
+    out->ctas_per_sm = (uint32_t)b->ctas_per_sm;
+    out->persistent = 1;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t) {
+    if (!b || !t) return set_err(BLOWCHOC_EINVAL, "NULL argument");
+    if (!lanes_ok(t->lanes_choose) || !lanes_ok(t->lanes_query))
+        return set_err(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
+    if (t->query_early > 1) return set_err(BLOWCHOC_EINVAL, "query_early must be 0 or 1");
+    if (t->ctas_per_sm < 1 || t->ctas_per_sm > 16) return set_err(BLOWCHOC_EINVAL, "ctas_per_sm must be in 1..16");
+    b->lanes_choose = (int)t->lanes_choose;
+    b->lanes_query = (int)t->lanes_query;
+    b->query_early = (int)t->query_early;
+    b->ctas_per_sm = (int)t->ctas_per_sm;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_t n_ins,
+                            const blowchoc_work *qry, uint32_t n_qry, void *stream, blowchoc_tuning *best) {
+    if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
+    int rc = check_items(b, ins, n_ins, false);
+    if (!rc) rc = check_items(b, qry, n_qry, true);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch copies of every filter, so that the callers' filters stay untouched
+    std::vector<blowchoc_filter *> scratch;
+    std::vector<blowchoc_work> sins(ins, ins + n_ins), sqry(qry, qry + n_qry);
+    auto clone = [&](blowchoc_filter *orig) -> blowchoc_filter * {
+        for (size_t i = 0; i < scratch.size(); i += 2)
+            if ((blowchoc_filter *)scratch[i + 1] == orig) return scratch[i];
+        blowchoc_filter *c = nullptr;
+        if (blowchoc_create(&orig->p, stream, &c)) return nullptr;
+        scratch.push_back(c);
+        scratch.push_back(orig);
+        return c;
+    };
+    uint64_t bitmap_words = 0;
+    for (auto &w : sqry) bitmap_words += (w.n + 63) / 64;
+    uint64_t *d_bm = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (bitmap_words && cudaMalloc(&d_bm, bitmap_words * sizeof(uint64_t)) != cudaSuccess) {
+        return set_err(BLOWCHOC_ENOMEM, "autotune bitmap");
+    }
+    rc = BLOWCHOC_OK;
+    for (auto &w : sins) if (!rc && !(w.filter = clone(w.filter))) rc = BLOWCHOC_ENOMEM;
+    uint64_t off = 0;
+    for (auto &w : sqry) {
+        if (!rc && !(w.filter = clone(w.filter))) rc = BLOWCHOC_ENOMEM;
+        w.d_bitmap = d_bm + off;
+        off += (w.n + 63) / 64;
+    }
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = set_err(BLOWCHOC_ECUDA, "autotune events");
+    const int saved[4] = {b->lanes_choose, b->lanes_query, b->query_early, b->ctas_per_sm};
+    float best_ms = -1.0f;
+    int best_cfg[4] = {saved[0], saved[1], saved[2], saved[3]};
+    const int lanes_c[] = {1, 2, 4}, lanes_q[] = {1, 2}, ctas[] = {4, 8};
+    for (int lc : lanes_c)
+        for (int lq : lanes_q)
+            for (int cp : ctas) {
+                if (rc) break;
+                b->lanes_choose = lc;
+                b->lanes_query = lq;
+                b->query_early = 1;
+                b->ctas_per_sm = cp;
+                float total = 0.0f;
+                for (int rep = 0; rep < 2 && !rc; ++rep) {
+                    for (size_t i = 0; i < scratch.size() && !rc; i += 2) rc = blowchoc_clear(scratch[i], stream);
+                    if (rc) break;
+                    cudaEventRecord(e0, s);
+                    if (!sins.empty()) rc = blowchoc_insert_many(b, sins.data(), (uint32_t)sins.size(), stream);
+                    if (!rc && !sqry.empty()) rc = blowchoc_query_many(b, sqry.data(), (uint32_t)sqry.size(), stream);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_err(BLOWCHOC_ECUDA, "autotune sync");
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep) total += ms;  // first repetition warms up
+                }
+                if (!rc && (best_ms < 0.0f || total < best_ms)) {
+                    best_ms = total;
+                    best_cfg[0] = lc; best_cfg[1] = lq; best_cfg[2] = 1; best_cfg[3] = cp;
+                }
+            }
+    for (size_t i = 0; i < scratch.size(); i += 2) blowchoc_destroy(scratch[i]);
+    cudaFree(d_bm);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->lanes_choose = rc ? saved[0] : best_cfg[0];
+    b->lanes_query = rc ? saved[1] : best_cfg[1];
+    b->query_early = rc ? saved[2] : best_cfg[2];
+    b->ctas_per_sm = rc ? saved[3] : best_cfg[3];
+    if (!rc && best) blowchoc_batch_get_tuning(b, best);
+    return rc;
+}
+
+}  // extern "C"

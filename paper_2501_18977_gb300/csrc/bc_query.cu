@@ -1,57 +1,17 @@
 // Membership query (Section 3.1) and load statistics (Appendix C, Fig. 8).
 #include "bc_launch.h"
+#include "bc_phases.cuh"
 
 namespace bc {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-// ANDs each group's LANES ballot bits down onto the group's first bit.
-template <int LANES>
-__device__ __forceinline__ uint32_t fold_groups(uint32_t b) {
-#pragma unroll
-    for (int s = 1; s < LANES; s <<= 1) b &= b >> s;
-    return b;
-}
-
-// Gathers bit g*LANES of v for g = 0..G-1 into bits 0..G-1 (mask-and-shift
-// compaction in log2(G) steps).
-template <int LANES>
-__device__ __forceinline__ uint32_t compress_groups(uint32_t v) {
-    if constexpr (LANES == 1) {
-        return v;
-    } else if constexpr (LANES == 2) {
-        v &= 0x55555555u;
-        v = (v | (v >> 1)) & 0x33333333u;
-        v = (v | (v >> 2)) & 0x0F0F0F0Fu;
-        v = (v | (v >> 4)) & 0x00FF00FFu;
-        return (v | (v >> 8)) & 0x0000FFFFu;
-    } else if constexpr (LANES == 4) {
-        v &= 0x11111111u;
-        v = (v | (v >> 3)) & 0x03030303u;
-        v = (v | (v >> 6)) & 0x000F000Fu;
-        return (v | (v >> 12)) & 0x000000FFu;
-    } else {
-        static_assert(LANES == 8, "LANES must be 1, 2, 4 or 8");
-        v &= 0x01010101u;
-        v = (v | (v >> 7)) & 0x00030003u;
-        return (v | (v >> 14)) & 0x0000000Fu;
-    }
-}
-
 constexpr int kThreads = 256;
 
-// One warp answers 64 consecutive keys and writes one bitmap word. Per key, a
-// group of LANES lanes builds the key's mask once (key_mask_shared), then
-// tests the candidate blocks: each lane checks its W words for
-// F(x) & ~block == 0, a ballot per candidate ANDs the lanes of each group,
-// and the candidates OR. EARLY = false issues all C block loads before any
-// test. EARLY = true loads candidate i+1 only for groups whose key was not
-// found in candidates 1..i, so members cost fewer block reads.
+// One warp answers 64 consecutive keys per step (query_word) and writes one
+// bitmap word; warps stride over the words of the bitmap.
 template <int C, int LANES, bool EARLY>
 __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint64_t *__restrict__ keys,
                                                          uint64_t n, uint64_t *__restrict__ bitmap) {
-    constexpr int W = kBlockWords / LANES;
     constexpr int G = 32 / LANES;
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
@@ -63,55 +23,7 @@ __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nwords = (n + 63) / 64;
     for (uint64_t wd = warp; wd < nwords; wd += nwarps) {
-        uint64_t word = 0;
-        for (int it = 0; it < 64 / G; ++it) {
-            const uint64_t i = wd * 64 + (uint64_t)it * G + g;
-            const bool valid = i < n;
-            const uint64_t x = valid ? load_key(keys + i) : 0ull;
-            uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
-            uint32_t hits = 0;
-            if constexpr (!EARLY) {
-                uint64_t blk[C][W];
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const uint64_t b = block_addr(f, f.a_block[c], x);
-                    if (valid) {
-                        load_words<W, kLoadNC>(f.words + b * kBlockWords + (uint64_t)q * W, blk[c]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < W; ++j) blk[c][j] = 0ull;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    uint64_t miss = 0;
-#pragma unroll
-                    for (int j = 0; j < W; ++j) miss |= m[j] & ~blk[c][j];
-                    hits |= fold_groups<LANES>(__ballot_sync(kFull, valid && miss == 0));
-                }
-            } else {
-                bool need = valid;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    uint64_t blk[W];
-                    if (need) {
-                        const uint64_t b = block_addr(f, f.a_block[c], x);
-                        load_words<W, kLoadNC>(f.words + b * kBlockWords + (uint64_t)q * W, blk);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < W; ++j) blk[j] = 0ull;
-                    }
-                    uint64_t miss = 0;
-#pragma unroll
-                    for (int j = 0; j < W; ++j) miss |= m[j] & ~blk[j];
-                    const uint32_t got = fold_groups<LANES>(__ballot_sync(kFull, need && miss == 0));
-                    hits |= got;
-                    need = need && !((got >> (g * LANES)) & 1u);
-                }
-            }
-            word |= (uint64_t)compress_groups<LANES>(hits) << (it * G);
-        }
+        const uint64_t word = query_word<C, LANES, EARLY>(f, keys, n, wd, s_amul, region, q, g);
         if (lane == 0) bitmap[wd] = word;
     }
 }

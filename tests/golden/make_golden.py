@@ -10,6 +10,7 @@ algorithmic bytes of member queries).
 Usage: python tests/golden/make_golden.py dna        (about 5 minutes on one core)
        python tests/golden/make_golden.py sweep I    (one filter setting I = 0..6 of the
                                                       overload sweep, about 30 minutes)
+       python tests/golden/make_golden.py many       (the 256-filter workload, about 6 minutes)
 """
 import hashlib
 import os
@@ -119,6 +120,28 @@ def sweep(idx):
     lines.append("# oracle_seconds = %.0f" % (time.time() - t0))
     with open(os.path.join(HERE, sweep_name(idx)), "w") as fh:
         fh.write("\n".join(lines) + "\n")
+
+
+def many():
+    """256 independent filters (workloads.many_filter_config): k = 11, c = 2,
+    cost^EXP beta = golden ratio, hash_seed = the filter's key seed, B_f as
+    configured; per filter: all keys inserted, then its queries."""
+    t0 = time.time()
+    cfg = workloads.many_filter_config()
+    lines = ["# Oracle results of the 256-filter workload (written by make_golden.py many).",
+             "# k = 11, c = 2, cost^EXP beta = golden ratio; per filter: n, M, B, hash_seed = key seed.",
+             "# f | n | M | B | inserted | skipped | words_sha256 | bitmap_sha256"]
+    for it in cfg:
+        keys, queries = workloads.many_filter_keys(it)
+        o = OracleFilter(it["M"], 11, 2, COST_EXP, GOLDEN_RATIO, seed=it["key_seed"], batch=it["B"])
+        o.insert(keys)
+        bm = o.query(queries)
+        lines.append("%d | %d | %d | %d | %d | %d | %s | %s" % (
+            it["index"], it["n"], it["M"], it["B"], o.inserted, o.skipped, sha(o.words), sha(bm)))
+    lines.append("# oracle_seconds = %.0f" % (time.time() - t0))
+    with open(os.path.join(HERE, "many_filters_256.txt"), "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    print(lines[-1])
 
 
 if __name__ == "__main__":

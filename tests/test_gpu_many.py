@@ -1,0 +1,162 @@
+"""Many filters in one launch per phase, against the oracle filter by filter.
+
+Each filter of a many-filter call must end up exactly as if blowchoc_insert
+and blowchoc_query had been called on it alone: words, bitmaps and counters
+equal the oracle's for every filter, whatever the mix of sizes, hash range
+kinds, choice counts, k and batch sizes in the work list.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import COST_MIX, COST_LA, COST_EXP
+from oracle.oracle import GOLDEN_RATIO
+from tests.gpu_helpers import to_dev, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+# (M, k, c, cost, param, B, n)
+MIX = [
+    (32, 11, 2, COST_EXP, GOLDEN_RATIO, 16, 1000),
+    (1000, 11, 2, COST_EXP, GOLDEN_RATIO, 1024, 30000),
+    (999, 14, 3, COST_LA, 3.5, 2048, 25000),
+    (6150, 9, 1, COST_MIX, 50.0, 4096, 40000),
+    (1, 3, 2, COST_MIX, 50.0, 1024, 300),
+    (4096, 20, 3, COST_MIX, 2.5, 100000, 60000),
+    (777, 7, 2, COST_LA, 3.5, 1, 3000),        # sequential: single-filter kernel
+    (2048, 16, 2, COST_EXP, GOLDEN_RATIO, 1 << 20, 50000),
+    (512, 12, 3, COST_EXP, GOLDEN_RATIO, 1500, 0),   # empty
+    (300, 5, 1, COST_EXP, GOLDEN_RATIO, 1024, 9000),
+    (257, 32, 2, COST_MIX, 50.0, 1030, 12345),
+]
+
+
+def _setup(bc, cases, seed0):
+    filters, keys, queries = [], [], []
+    for j, (M, k, c, kind, par, B, n) in enumerate(cases):
+        filters.append(bc.Filter(M, k, c, kind, par, hash_seed=seed0 + j, batch=B))
+        kk = workloads.uniform_keys(seed0 * 100 + j, n)
+        neg = workloads.disjoint_keys(seed0 * 100 + j + 50, n // 2 + 1, kk)
+        keys.append(kk)
+        queries.append(np.concatenate([kk[: n // 2], neg]))
+    return filters, keys, queries
+
+
+def _check_against_oracle(cases, filters, keys, queries, bitmaps, seed0):
+    for j, (M, k, c, kind, par, B, n) in enumerate(cases):
+        o, obm, _, _ = oracle_run(M, k, c, kind, par, seed0 + j, B, keys[j], queries[j])
+        assert np.array_equal(filters[j].words_host(), o.words), j
+        got = bitmaps[j].cpu().numpy().view(np.uint64)[: (len(queries[j]) + 63) // 64]
+        assert np.array_equal(got, obm), j
+        st = filters[j].stats()
+        assert (st.inserted, st.skipped) == (o.inserted, o.skipped), j
+
+
+def test_insert_and_query_many_match_the_oracle():
+    import torch
+    import paper_2501_18977_gb300 as bc
+    seed0 = 11
+    filters, keys, queries = _setup(bc, MIX, seed0)
+    dk = [to_dev(k) for k in keys]
+    dq = [to_dev(q) for q in queries]
+    bms = [torch.zeros(max(1, (len(q) + 63) // 64), dtype=torch.int64, device="cuda") for q in queries]
+    batch = bc.Batch()
+    try:
+        batch.insert_many([(f, d, len(k), None) for f, d, k in zip(filters, dk, keys)])
+        batch.query_many([(f, d, len(q), b) for f, d, q, b in zip(filters, dq, queries, bms)])
+        torch.cuda.synchronize()
+        _check_against_oracle(MIX, filters, keys, queries, bms, seed0)
+    finally:
+        batch.close()
+        for f in filters:
+            f.close()
+
+
+def test_many_equals_one_call_per_filter():
+    """Two many-filter calls in a row compose like two calls per filter."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    cases = MIX[:6]
+    a, keys, _ = _setup(bc, cases, 5)
+    b, _, _ = _setup(bc, cases, 5)
+    batch = bc.Batch()
+    try:
+        halves = [(k[: len(k) // 2], k[len(k) // 2:]) for k in keys]
+        for part in (0, 1):
+            dks = [to_dev(h[part]) for h in halves]
+            batch.insert_many([(f, d, len(h[part]), None) for f, d, h in zip(a, dks, halves)])
+            for f, d, h in zip(b, dks, halves):
+                f.insert(d)
+        torch.cuda.synchronize()
+        for fa, fb in zip(a, b):
+            assert np.array_equal(fa.words_host(), fb.words_host())
+    finally:
+        batch.close()
+        for f in a + b:
+            f.close()
+
+
+def test_recorded_graph_replays_the_same_work():
+    import torch
+    import paper_2501_18977_gb300 as bc
+    cases = [MIX[1], MIX[2], MIX[5], MIX[7]]
+    seed0 = 21
+    filters, keys, queries = _setup(bc, cases, seed0)
+    dk = [to_dev(k) for k in keys]
+    dq = [to_dev(q) for q in queries]
+    bms = [torch.zeros(max(1, (len(q) + 63) // 64), dtype=torch.int64, device="cuda") for q in queries]
+    batch = bc.Batch()
+    try:
+        batch.record([(f, d, len(k), None) for f, d, k in zip(filters, dk, keys)],
+                     [(f, d, len(q), b) for f, d, q, b in zip(filters, dq, queries, bms)])
+        for rep in range(2):
+            for f in filters:
+                f.clear()
+            batch.replay()
+            torch.cuda.synchronize()
+            _check_against_oracle(cases, filters, keys, queries, bms, seed0)
+    finally:
+        batch.close()
+        for f in filters:
+            f.close()
+
+
+def test_autotune_leaves_filters_untouched_and_results_unchanged():
+    import torch
+    import paper_2501_18977_gb300 as bc
+    cases = [MIX[1], MIX[3], MIX[7]]
+    seed0 = 31
+    filters, keys, queries = _setup(bc, cases, seed0)
+    dk = [to_dev(k) for k in keys]
+    dq = [to_dev(q) for q in queries]
+    bms = [torch.zeros(max(1, (len(q) + 63) // 64), dtype=torch.int64, device="cuda") for q in queries]
+    batch = bc.Batch()
+    try:
+        ins = [(f, d, len(k), None) for f, d, k in zip(filters, dk, keys)]
+        qry = [(f, d, len(q), b) for f, d, q, b in zip(filters, dq, queries, bms)]
+        best = batch.autotune(ins, qry)
+        assert best.lanes_choose in (1, 2, 4) and best.ctas_per_sm in (4, 8)
+        for f in filters:
+            assert not f.words_host().any()
+        batch.insert_many(ins)
+        batch.query_many(qry)
+        torch.cuda.synchronize()
+        _check_against_oracle(cases, filters, keys, queries, bms, seed0)
+    finally:
+        batch.close()
+        for f in filters:
+            f.close()
+
+
+def test_many_rejects_a_repeated_filter():
+    import paper_2501_18977_gb300 as bc
+    f = bc.Filter(64, 8, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=2048)
+    batch = bc.Batch()
+    try:
+        d = to_dev(workloads.uniform_keys(1, 100))
+        with pytest.raises(bc.BlowChocError) as ei:
+            batch.insert_many([(f, d, 100, None), (f, d, 100, None)])
+        assert ei.value.code == bc.BLOWCHOC_EINVAL
+    finally:
+        batch.close()
+        f.close()

@@ -130,3 +130,28 @@ def uniform01(seed: int, n: int) -> np.ndarray:
     """n doubles in (0, 1) from splitmix64 (53-bit mantissa)."""
     u = splitmix64(seed, n)
     return ((u >> np.uint64(11)).astype(np.float64) + 0.5) / float(1 << 53)
+
+
+def many_filter_config(seed: int = 4, n_filters: int = 256, bits_per_key: int = 16):
+    """The many-filter workload: key counts lognormal (median 200,000, sigma 1,
+    clipped to 1,000..20,000,000, seed `seed`), M_f = ceil(bits_per_key n_f / 512)
+    blocks, batch B_f = 2^floor(log2(M_f / 2)) (at least 1); keys of filter f are
+    the splitmix64 stream of seed (seed << 32) | f, its queries are its first
+    ceil(n_f / 2) keys followed by floor(n_f / 2) keys of seed ((seed + 1) << 32) | f."""
+    counts = lognormal_counts(seed, n_filters)
+    out = []
+    for f, n in enumerate(counts):
+        n = int(n)
+        M = -(-bits_per_key * n // 512)
+        B = 1 << max(0, int(math.floor(math.log2(max(M / 2.0, 1.0)))))
+        out.append(dict(index=f, n=n, M=M, B=B, key_seed=(seed << 32) | f,
+                        query_seed=((seed + 1) << 32) | f))
+    return out
+
+
+def many_filter_keys(item):
+    """(keys, queries) of one filter of many_filter_config."""
+    keys = splitmix64(item["key_seed"], item["n"])
+    half = (item["n"] + 1) // 2
+    other = splitmix64(item["query_seed"], item["n"] // 2)
+    return keys, np.concatenate([keys[:half], other])
