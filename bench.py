@@ -18,7 +18,14 @@ Other measurements (--workload): `gather` sweeps the random 64-byte gather
 ceiling of the device over footprints from 2 MiB to 4 GiB; `many` runs 256
 independent filters of lognormal sizes (k = 11, c = 2, cost^EXP) as plain
 per-filter calls, as one launch per phase over a work list, and as a replayed
-CUDA graph, and checks that all three give the same words and bitmaps.
+CUDA graph, and checks that all three give the same words and bitmaps;
+`serve` runs the request-serving loop on 64 filters under a Poisson stream of
+10,000 insert/query requests at 50/80/95% of its measured capacity; `sweep`
+grows 512 MiB filters (k = 12; one choice, and two and three choices under
+each cost) from 20 to 6 bits per key against 10^8 negatives per point;
+`batching` reports the FPR and load-balance cost of batch size B against
+one-key-at-a-time insertion; `small` times the small uniform configuration
+(10^6 keys into 2^24 bits, k = 14, two choices, cost^MIX, B = 65536 and 1).
 """
 import argparse
 import json
@@ -52,7 +59,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["dna", "gather", "many"], default="dna")
+    ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small"],
+                    default="dna")
+    ap.add_argument("--requests", type=int, default=10000)
     return ap.parse_args()
 
 
@@ -293,6 +302,236 @@ def run_many(args):
     print(json.dumps(out))
 
 
+def run_serve(args):
+    """64 device-resident filters (2^20..2^31 bits log-uniform, k = 14, c = 2,
+    cost^MIX sigma = 50), 10,000 requests (70% query, sizes log-uniform in
+    1..10^6 keys, uniform target filter), 80 GB HBM budget. Capacity is the
+    closed-loop rate (all requests arrive at once); the Poisson stream is then
+    offered at 50/80/95% of it. The same requests run through plain per-request
+    calls on one stream give the comparison rate and the reference results."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    filters, reqs = workloads.serving_config(n_requests=args.requests)
+    sizes = [r["n"] for r in reqs]
+    total_keys = int(sum(sizes))
+    offs = np.zeros(len(reqs) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(sizes)
+    pinned = torch.empty(total_keys, dtype=torch.int64).pin_memory()
+    host = pinned.numpy().view(np.uint64)
+    for r in reqs:
+        host[offs[r["index"]]:offs[r["index"] + 1]] = workloads.serving_keys(filters, r)
+    keys = {r["index"]: host[offs[r["index"]]:offs[r["index"] + 1]] for r in reqs}
+
+    def serve(time_scale):
+        srv = bc.Server(80 * 10**9, staging_bytes=4 << 30, streams=4, max_wave_requests=64)
+        ids = [srv.add_filter(f["M"], 14, 2, bc.COST_MIX, 50.0, f["key_seed"], f["B"]) for f in filters]
+        bms = {}
+        for r in reqs:
+            bm = np.zeros((r["n"] + 63) // 64, dtype=np.uint64) if r["kind"] == 1 else None
+            if bm is not None:
+                bms[r["index"]] = bm
+            srv.submit(ids[r["filter"]], r["kind"], keys[r["index"]], bm, r["arrival"] * time_scale)
+        launches0 = bc.blowchoc_launch_count()
+        srv.start()
+        srv.wait(600.0)
+        st = srv.stats()
+        launches = bc.blowchoc_launch_count() - launches0
+        srv.close()
+        span = st.last_done_s - st.first_arrival_s
+        return bms, st, span, launches
+
+    # plain: one request at a time, in arrival order, one stream
+    fs = [bc.Filter(f["M"], 14, 2, bc.COST_MIX, 50.0, hash_seed=f["key_seed"], batch=f["B"])
+          for f in filters]
+    dev = torch.empty(max(sizes), dtype=torch.int64, device="cuda")
+    dbm = torch.empty((max(sizes) + 63) // 64, dtype=torch.int64, device="cuda")
+    plain_bms = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in sorted(reqs, key=lambda r: (r["arrival"], r["index"])):
+        n = r["n"]
+        dev[:n].copy_(pinned[offs[r["index"]]:offs[r["index"] + 1]], non_blocking=True)
+        if r["kind"] == 0:
+            fs[r["filter"]].insert(dev[:n])
+        else:
+            fs[r["filter"]].query(dev[:n], dbm)
+            out = np.zeros((n + 63) // 64, dtype=np.uint64)
+            out[:] = dbm[: (n + 63) // 64].cpu().numpy().view(np.uint64)
+            plain_bms[r["index"]] = out
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    for f in fs:
+        f.close()
+
+    closed_bms, closed_st, closed_span, _ = serve(0.0)
+    capacity = total_keys / closed_span
+    mean_req = total_keys / len(reqs)
+    same = all(np.array_equal(closed_bms[j], b) for j, b in plain_bms.items())
+    loads = []
+    for load in (0.5, 0.8, 0.95):
+        rate = load * capacity / mean_req          # requests per second
+        bms, st, span, launches = serve(1.0 / rate)
+        same = same and all(np.array_equal(bms[j], b) for j, b in plain_bms.items())
+        loads.append({"offered_load": load, "offered_mkeys_s": round(load * capacity / 1e6, 1),
+                      "achieved_mkeys_s": round(total_keys / span / 1e6, 1),
+                      "p50_ms": round(st.p50_latency_s * 1e3, 3), "p99_ms": round(st.p99_latency_s * 1e3, 3),
+                      "max_ms": round(st.max_latency_s * 1e3, 3), "waves": int(st.waves),
+                      "mean_wave_requests": round(st.mean_wave_requests, 2), "gpu_launches": int(launches)})
+    out = {"workload": "serving_64_filters", "metric": "served keys/s with p50/p99 latency",
+           "requests": len(reqs), "keys": total_keys,
+           "filter_gb": round(sum(f["M"] for f in filters) * 64 / 1e9, 3),
+           "plain_per_request_mkeys_s": round(total_keys / plain_s / 1e6, 1),
+           "served_capacity_mkeys_s": round(capacity / 1e6, 1),
+           "served_vs_plain": round(capacity / (total_keys / plain_s), 2),
+           "closed_loop": {"p50_ms": round(closed_st.p50_latency_s * 1e3, 3),
+                           "p99_ms": round(closed_st.p99_latency_s * 1e3, 3),
+                           "waves": int(closed_st.waves),
+                           "mean_wave_requests": round(closed_st.mean_wave_requests, 2)},
+           "poisson": loads, "identical_to_plain_results": bool(same),
+           "timing": "host steady clock (server) and wall clock (plain); keys from pinned host memory"}
+    print(json.dumps(out))
+
+
+SWEEP_SETTINGS = [(1, "EXP", 0), (2, "MIX", 50.0), (2, "LA", 3.5), (2, "EXP", 0), (3, "MIX", 50.0),
+                  (3, "LA", 3.5), (3, "EXP", 0)]
+SWEEP_BITS = [20, 18, 16, 14, 12, 10, 8, 6]
+
+
+def run_sweep(args):
+    """Overload / FPR sweep: M = 2^23 blocks (512 MiB), k = 12, B = 2^20, hash
+    seed 3001; keys: splitmix64 seed 3001, grown by one insert call per point to
+    floor(2^32 / b) keys for b = 20, 18, ..., 6 bits per key; 10^8 negatives
+    (seed 3002) per point. Reports measured FPR W/N beside the one-choice
+    blocked-Bloom formula, the standard Bloom formula and the histogram
+    estimate, and insert / query rates."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    from oracle import closed_forms as cf
+    M, k, B = 1 << 23, 12, 1 << 20
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    kinds = {"MIX": bc.COST_MIX, "LA": bc.COST_LA, "EXP": bc.COST_EXP}
+    nmax = (1 << 32) // SWEEP_BITS[-1]
+    keys = torch.empty(nmax, dtype=torch.int64, device="cuda")
+    chunk = 1 << 25
+    for s0 in range(0, nmax, chunk):
+        c = min(chunk, nmax - s0)
+        keys[s0:s0 + c].copy_(torch.from_numpy(workloads.splitmix64(3001, c, s0).view(np.int64)))
+    neg = torch.from_numpy(workloads.uniform_keys(3002, 100_000_000).view(np.int64)).cuda()
+    bm = torch.empty((neg.numel() + 63) // 64, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    rows = []
+    for c, cname, par in SWEEP_SETTINGS:
+        par = phi if cname == "EXP" else par
+        f = bc.Filter(M, k, c, kinds[cname], par, hash_seed=3001, batch=B)
+        n_prev = 0
+        for b in SWEEP_BITS:
+            n = (1 << 32) // b
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(s)
+            f.insert(keys[n_prev:n], s)
+            e[1].record(s)
+            f.query(neg, bm, s)
+            e[2].record(s)
+            torch.cuda.synchronize()
+            st = f.stats()
+            W = int(np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")[: neg.numel()].sum())
+            rows.append({"c": c, "cost": cname, "bits_per_key": b, "n": n, "fpr": W / neg.numel(),
+                         "false_positives": W, "fpr_est_hist": st.fpr_est,
+                         "blocked_bloom_formula": cf.blocked_bloom_fpr(n, M, k),
+                         "bloom_formula": cf.bloom_fpr(n, M * 512, k),
+                         "inserted": st.inserted, "skipped": st.skipped, "set_bits": st.set_bits,
+                         "insert_mkeys_s": round((n - n_prev) / (e[0].elapsed_time(e[1]) / 1e3) / 1e6, 1),
+                         "query_mkeys_s": round(neg.numel() / (e[1].elapsed_time(e[2]) / 1e3) / 1e6, 1)})
+            n_prev = n
+        f.close()
+    print(json.dumps({"workload": "overload_sweep", "M": M, "k": k, "B": B, "negatives": neg.numel(),
+                      "rows": rows}))
+
+
+def run_batching(args):
+    """FPR and load balance against the batch size B: M = 2^16 blocks (4 MiB),
+    k = 12, c in {2, 3}, cost^EXP beta = golden ratio, 12 bits per key
+    (2^32/12 / 128 = 2,796,202 keys, seed 3001), B from 1 (the paper's
+    sequential insertion) to 2^20; 10^8 negatives (seed 3002)."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    M, k = 1 << 16, 12
+    n = ((1 << 32) // 12) >> 7
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    keys = torch.from_numpy(workloads.uniform_keys(3001, n).view(np.int64)).cuda()
+    neg = torch.from_numpy(workloads.uniform_keys(3002, 100_000_000).view(np.int64)).cuda()
+    bm = torch.empty((neg.numel() + 63) // 64, dtype=torch.int64, device="cuda")
+    rows = []
+    for c in (2, 3):
+        for B in (1, 16, 256, 4096, 1 << 14, 1 << 16, 1 << 18, 1 << 20):
+            f = bc.Filter(M, k, c, bc.COST_EXP, phi, hash_seed=3001, batch=B)
+            s = torch.cuda.current_stream()
+            a = torch.cuda.Event(enable_timing=True)
+            b2 = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            f.insert(keys, s)
+            b2.record(s)
+            f.query(neg, bm, s)
+            torch.cuda.synchronize()
+            st = f.stats()
+            W = int(np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")[: neg.numel()].sum())
+            L = np.arange(513)
+            h = np.array(list(st.hist), dtype=np.float64)
+            mean = float((h * L).sum() / M)
+            sd = float(math.sqrt((h * (L - mean) ** 2).sum() / M))
+            rows.append({"c": c, "B": B, "fpr": W / neg.numel(), "fpr_est_hist": st.fpr_est,
+                         "mean_load": round(mean, 3), "sd_load": round(sd, 3),
+                         "insert_ms": round(a.elapsed_time(b2), 3)})
+            f.close()
+    print(json.dumps({"workload": "batching_cost", "M": M, "k": k, "n": n, "cost": "EXP golden ratio",
+                      "rows": rows}))
+
+
+def run_small(args):
+    """10^6 uniform keys (seed 1) into M = 32768 blocks (2^24 bits, L2-resident),
+    k = 14, c = 2, cost^MIX sigma = 50; B = 65536 and B = 1; queries: the keys
+    plus 10^6 disjoint keys (seed 1001). Insert and query rates, FPR."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    keys = workloads.uniform_keys(1, 1_000_000)
+    neg = workloads.disjoint_keys(1001, 1_000_000, keys)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dq = torch.from_numpy(np.concatenate([keys, neg]).view(np.int64)).cuda()
+    bm = torch.empty((dq.numel() + 63) // 64, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    rows = []
+    for B in (65536, 1):
+        f = bc.Filter(32768, 14, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=B)
+        reps = max(1, args.steps) if B > 1 else 1
+        ti, tq = [], []
+        for _ in range(reps + (1 if B > 1 else 0)):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            f.clear(s)
+            e[0].record(s)
+            f.insert(dk, s)
+            e[1].record(s)
+            f.query(dq, bm, s)
+            e[2].record(s)
+            torch.cuda.synchronize()
+            ti.append(e[0].elapsed_time(e[1]))
+            tq.append(e[1].elapsed_time(e[2]))
+        if B > 1:
+            ti, tq = ti[1:], tq[1:]
+        h = bm.cpu().numpy().view(np.uint8)
+        bits = np.unpackbits(h, bitorder="little")[: dq.numel()]
+        st = f.stats()
+        rows.append({"B": B, "insert_ms": round(statistics.median(ti), 4),
+                     "insert_mkeys_s": round(1e6 / (statistics.median(ti) / 1e3) / 1e6, 1),
+                     "query_ms": round(statistics.median(tq), 4),
+                     "query_mkeys_s": round(2e6 / (statistics.median(tq) / 1e3) / 1e6, 1),
+                     "false_negatives": int(1_000_000 - bits[:1_000_000].sum()),
+                     "fpr": float(bits[1_000_000:].mean()), "fpr_est_hist": st.fpr_est,
+                     "inserted": st.inserted, "skipped": st.skipped})
+        f.close()
+    print(json.dumps({"workload": "small_uniform", "M": 32768, "k": 14, "c": 2, "cost": "MIX 50",
+                      "rows": rows}))
+
+
 def golden_pbar():
     """Mean 1-based index of the first candidate block holding an inserted
     31-mer of this workload, as counted by the oracle (tests/golden)."""
@@ -366,6 +605,18 @@ def main():
         return
     if args.workload == "many":
         run_many(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
+        return
+    if args.workload == "sweep":
+        run_sweep(args)
+        return
+    if args.workload == "batching":
+        run_batching(args)
+        return
+    if args.workload == "small":
+        run_small(args)
         return
     import torch
     import torch.distributed as dist

@@ -180,6 +180,17 @@ int blowchoc_words(blowchoc_filter *f, uint64_t **d_words, uint64_t *nwords);
 int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit);
 
 /*
+ * blowchoc_set_cost_table -- replace the filter's cost by a table (a learned
+ * cost, or any cost outside Eq. 4-6): costs[L * (k + 1) + a] for block load
+ * L = 0..512 and new bits a = 0..k; entries with L + a > 512 are never used.
+ * Not in the paper. Choices stay exact: the table is ranked on the host like
+ * the built-in costs (equal values share a rank; ties go to the lowest
+ * choice index). Takes effect for inserts queued after the call.
+ * Errors: EINVAL (NULL, c = 1, a used entry not finite), ENOMEM, ECUDA.
+ */
+int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs);
+
+/*
  * blowchoc_read_words / blowchoc_write_words -- copy filter words
  * [first, first + count) to or from HOST memory (checkpoint and restore: a
  * filter is fully determined by its parameters and its words). Both run on
@@ -261,6 +272,134 @@ int blowchoc_batch_record(blowchoc_batch *b, const blowchoc_work *ins, uint32_t 
 int blowchoc_batch_replay(blowchoc_batch *b, void *stream);
 
 /*
+ * ---- Serving --------------------------------------------------------------
+ * A request-serving loop for device-resident filters: insert and query
+ * requests arrive over time (host key buffers, arrival times); a scheduler
+ * thread admits filters under an HBM budget, keeps one FIFO per filter, and
+ * launches "waves": at most one request per filter (so two inserts of one
+ * filter are never merged into one batch), coalesced across filters into one
+ * insert_many and one query_many launch, on several streams, ordered per
+ * filter by events. Each request's result is exactly what it gives when the
+ * requests of its filter run alone, one after another, in arrival order.
+ * Not in the paper: a library service.
+ */
+typedef struct blowchoc_server blowchoc_server;
+
+typedef struct {
+    uint64_t hbm_budget_bytes;   /* device memory for admitted filters */
+    uint64_t staging_bytes;      /* device memory for in-flight request keys/bitmaps */
+    uint32_t streams;            /* concurrent waves, 1..16 */
+    uint32_t max_wave_requests;  /* requests per wave, >= 1 */
+} blowchoc_server_config;
+
+#define BLOWCHOC_REQ_INSERT 0u
+#define BLOWCHOC_REQ_QUERY 1u
+
+typedef struct {
+    uint64_t completed;          /* requests finished */
+    uint64_t keys;               /* keys of finished requests */
+    uint64_t waves;              /* launch waves */
+    double first_arrival_s, last_done_s;
+    double p50_latency_s, p99_latency_s, max_latency_s;  /* arrival -> completion */
+    double mean_wave_requests;
+    uint64_t max_filter_bytes_used;  /* high-water mark of admitted filter memory */
+    uint32_t filters_admitted, filters_pending;
+} blowchoc_server_summary;
+
+/* Create a server on the current device (its thread starts at
+ * blowchoc_server_start). Errors: EINVAL, ENOMEM, ECUDA. */
+int blowchoc_server_create(const blowchoc_server_config *cfg, blowchoc_server **out);
+
+/* Register a filter. It is created (admitted) as soon as its memory fits the
+ * budget, in registration order; until then its requests wait. *id receives
+ * its index. Errors: EINVAL, EBUDGET (larger than the whole budget). */
+int blowchoc_server_add_filter(blowchoc_server *s, const blowchoc_params *p, uint32_t *id);
+
+/* Destroy a filter after all its submitted requests have completed, freeing
+ * its budget for pending filters. Errors: EINVAL. */
+int blowchoc_server_remove_filter(blowchoc_server *s, uint32_t id);
+
+/* Submit a request (thread-safe). h_keys: n host keys (pinned memory copies
+ * asynchronously); h_bitmap: query result, ceil(n/64) host words. Both stay
+ * owned by the caller and must stay valid until the request completes. The
+ * request counts as arriving at arrival_s seconds after start (or at submit
+ * time if later). *req_id may be NULL. Errors: EINVAL, EBUDGET (request
+ * larger than the staging memory). */
+int blowchoc_server_submit(blowchoc_server *s, uint32_t filter_id, uint32_t kind, const uint64_t *h_keys,
+                           uint64_t n, uint64_t *h_bitmap, double arrival_s, uint64_t *req_id);
+
+/* Start the clock and the scheduler thread. Errors: EINVAL (started). */
+int blowchoc_server_start(blowchoc_server *s);
+
+/* Block until every submitted request has completed (or timeout_s passed:
+ * ETIMEOUT). Errors: EINVAL, ECUDA (a launch failed), ETIMEOUT. */
+int blowchoc_server_wait(blowchoc_server *s, double timeout_s);
+
+/* Times of one request in seconds since start: arrival, launch, completion
+ * (negative while not reached). Errors: EINVAL. */
+int blowchoc_server_request_times(blowchoc_server *s, uint64_t req_id, double *arrival, double *launch,
+                                  double *done);
+
+/* Aggregate statistics of the completed requests. Errors: EINVAL. */
+int blowchoc_server_stats(blowchoc_server *s, blowchoc_server_summary *out);
+
+/* The filter behind an admitted id (NULL while pending); owned by the server.
+ * Use only while no request of it is in flight. Errors: EINVAL. */
+int blowchoc_server_filter(blowchoc_server *s, uint32_t id, blowchoc_filter **f);
+
+/* Stop the thread, wait for the GPU, free everything. NULL is accepted. */
+int blowchoc_server_destroy(blowchoc_server *s);
+
+/*
+ * ---- Learned cost (not in the paper) ----------------------------------------
+ * A network g(x), x = ((L + a) / 512, a / k) -- the load after insertion and
+ * the new bits relative to k, the arguments of the paper's costs -- with two
+ * tanh hidden layers of 32 units and a linear output, fp32. Its values on the
+ * whole (L, a) grid form a cost table for blowchoc_set_cost_table. Training
+ * (score-function estimator) runs on the GPU: blowchoc_insert_sampled draws
+ * each choice from softmax(-g / tau) and accumulates d log pi / d g per grid
+ * point; blowchoc_mlp_backward turns those weights into parameter gradients
+ * (fp64 accumulation); blowchoc_mlp_adam_step updates the parameters.
+ * Parameter layout: W1[32][2], b1[32], W2[32][32] (row = output unit), b2[32],
+ * w3[32], b3 (1185 floats).
+ */
+typedef struct blowchoc_mlp blowchoc_mlp;
+
+/* Network for filters with k bit hashes; weights uniform in +-1/sqrt(fan in)
+ * from splitmix64(seed), biases 0. Errors: EINVAL, ENOMEM, ECUDA. */
+int blowchoc_mlp_create(uint32_t k, uint64_t seed, blowchoc_mlp **out);
+int blowchoc_mlp_destroy(blowchoc_mlp *m);
+uint32_t blowchoc_mlp_param_count(void);
+
+/* Host copies of the parameters (1185 floats) and of the accumulated
+ * gradient (1185 doubles); either pointer may be NULL. Synchronous. */
+int blowchoc_mlp_get_params(blowchoc_mlp *m, float *h_params, double *h_grad);
+int blowchoc_mlp_set_params(blowchoc_mlp *m, const float *h_params);
+
+/* d_table[L (k+1) + a] = g(((L + a) / 512, a / k)) for L = 0..512, a = 0..k. */
+int blowchoc_mlp_forward(blowchoc_mlp *m, float *d_table, void *stream);
+
+/* gradient += scale * sum_p d_w[p] * d g(x_p) / d parameters. */
+int blowchoc_mlp_backward(blowchoc_mlp *m, const float *d_w, double scale, void *stream);
+
+/* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) down the accumulated
+ * gradient, which is then cleared. */
+int blowchoc_mlp_adam_step(blowchoc_mlp *m, float lr, void *stream);
+
+/*
+ * blowchoc_insert_sampled -- training-mode insertion with the filter's batch
+ * rule: a key already held by a candidate is skipped as usual; otherwise its
+ * choice is drawn from softmax(-d_table[p_i] / tau) over its candidates
+ * (p_i = L_i (k+1) + a_i), with the uniform taken from the splitmix64 stream
+ * of `seed` at the key's index in this call, and
+ * d_w[p_i] += (pi_i - 1{i chosen}) / tau  (= d log pi(chosen) / d g(p_i)).
+ * d_choice (optional, n bytes) receives the choices (255 = skipped).
+ * Errors: EINVAL (c = 1, tau <= 0, NULL pointers), ENOMEM, ECUDA.
+ */
+int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, const float *d_table,
+                            float tau, uint64_t seed, float *d_w, uint8_t *d_choice, void *stream);
+
+/*
  * Launch configuration of a filter's kernels. It never changes any result
  * (words, bitmaps, counters are identical for every valid setting); it only
  * changes speed. Defaults are set at create.
@@ -270,11 +409,20 @@ int blowchoc_batch_replay(blowchoc_batch *b, void *stream);
  *       candidates 1..i (fewer block reads for members); 0 = load all first.
  *   ctas_per_sm: grid size of the grid-wide kernels, in CTAs per SM (1..16;
  *       the persistent insert caps it at what is co-resident).
- *   persistent: 1 = an insert of batches above 16384 keys runs as one
+ *   persistent: 1 = an insert of batches above 2048 keys runs as one
  *       cooperative launch with grid barriers between phases (each barrier
  *       wait is bounded; on expiry the filter's error word is set and
  *       blowchoc_stats returns ETIMEOUT); 0 = two launches per batch.
- *       lanes_choose then applies to both phases.
+ *       lanes_choose then applies to both phases. Batches of 2 to 2048 keys
+ *       run in one CTA with CTA barriers, B = 1 in one warp.
+ *   keys_per_cta: grid of the persistent insert, as keys of one batch per
+ *       CTA (grid = ceil(min(B, n) / keys_per_cta), at most ctas_per_sm CTAs
+ *       per SM): fewer CTAs make the barriers of small batches cheaper.
+ *   set_mode: how the persistent insert ORs a batch in: 0 = 64-bit atomic OR
+ *       of each key's words at L2; 1 = sort by block: bucket the batch's keys
+ *       by ranges of 256 blocks, stage each touched range in shared memory,
+ *       OR there, write the range back (offered while ceil(M / 256) <= 65536;
+ *       larger filters use 0).
  */
 typedef struct {
     uint32_t lanes_choose;
@@ -283,6 +431,8 @@ typedef struct {
     uint32_t query_early;
     uint32_t ctas_per_sm;
     uint32_t persistent;
+    uint32_t keys_per_cta;
+    uint32_t set_mode;
 } blowchoc_tuning;
 
 /* Read / replace a filter's launch configuration. set_tuning checks every

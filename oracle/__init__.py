@@ -10,9 +10,9 @@ Every oracle function is pinned by a test against something other than
 itself (printed values, closed forms, invariants, brute force); see
 ``tests/test_oracle_pins.py``.
 """
-from .oracle import (OracleFilter, COST_MIX, COST_LA, COST_EXP, derive_multipliers,
+from .oracle import (OracleFilter, COST_MIX, COST_LA, COST_EXP, COST_TABLE, derive_multipliers,
                      hash_lin, cost, bit_positions, splitmix64_next)
 from . import closed_forms
 
-__all__ = ["OracleFilter", "COST_MIX", "COST_LA", "COST_EXP", "derive_multipliers",
+__all__ = ["OracleFilter", "COST_MIX", "COST_LA", "COST_EXP", "COST_TABLE", "derive_multipliers",
            "hash_lin", "cost", "bit_positions", "splitmix64_next", "closed_forms"]

@@ -33,7 +33,18 @@
 
 #define ORC_BLOCK_BITS 512u
 
-enum { ORC_COST_MIX = 0, ORC_COST_LA = 1, ORC_COST_EXP = 2 };
+enum { ORC_COST_MIX = 0, ORC_COST_LA = 1, ORC_COST_EXP = 2, ORC_COST_TABLE = 3 };
+
+/* A cost given as a table over (load L, new bits a): cost = table[L (k+1) + a]
+ * with L = j - a. Used for costs that are not among Eq. 4-6 (a learned cost). */
+static const double *orc_table = NULL;
+static uint32_t orc_table_k = 0;
+
+void orc_set_cost_table(const double *table, uint32_t k)
+{
+    orc_table = table;
+    orc_table_k = k;
+}
 
 /* splitmix64 (Steele, Lea and Flood, OOPSLA 2014): add the golden-ratio
  * increment to the state, then apply the variant-13 finaliser of MurmurHash3
@@ -124,6 +135,8 @@ int orc_derive_multipliers(uint64_t seed, uint64_t M, uint32_t k, uint32_t c,
 double orc_cost(int kind, double param, uint32_t k, uint32_t j, uint32_t a)
 {
     double dk = (double)k;
+    if (kind == ORC_COST_TABLE)
+        return (orc_table != NULL && k == orc_table_k) ? orc_table[(j - a) * (k + 1) + a] : NAN;
     if (kind == ORC_COST_MIX)
         return (param * dk) * pow((double)j / 256.0, dk) + (double)a;
     if (kind == ORC_COST_LA)

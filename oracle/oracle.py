@@ -10,7 +10,7 @@ import numpy as np
 
 from . import build as _build
 
-COST_MIX, COST_LA, COST_EXP = 0, 1, 2
+COST_MIX, COST_LA, COST_EXP, COST_TABLE = 0, 1, 2, 3
 GOLDEN_RATIO = (1.0 + math.sqrt(5.0)) / 2.0
 
 _lib = None
@@ -44,6 +44,8 @@ def _load():
     lib.orc_block_terms.argtypes = [vp, u64, vp, u32, u64,
                                     ctypes.POINTER(u32), ctypes.POINTER(u32)]
     lib.orc_block_terms.restype = None
+    lib.orc_set_cost_table.argtypes = [vp, u32]
+    lib.orc_set_cost_table.restype = None
     _lib = lib
     return lib
 
@@ -110,8 +112,16 @@ class OracleFilter:
         self.inserted = 0
         self.skipped = 0
 
+    def set_cost_table(self, table):
+        """Use costs table[L * (k + 1) + a] (a table cost, e.g. a learned one)."""
+        self.cost_kind = COST_TABLE
+        self.table = np.ascontiguousarray(table, dtype=np.float64).copy()
+        assert self.table.shape == (513 * (self.k + 1),)
+
     def insert(self, keys, batch=None, return_choices=False):
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        if self.cost_kind == COST_TABLE:
+            _load().orc_set_cost_table(_ptr(self.table), self.k)
         B = self.batch if batch is None else int(batch)
         n = len(keys)
         choices = np.empty(max(n, 1), dtype=np.int8) if return_choices else None

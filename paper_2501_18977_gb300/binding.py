@@ -45,13 +45,30 @@ class blowchoc_filter_stats(ctypes.Structure):
 class blowchoc_tuning(ctypes.Structure):
     _fields_ = [("lanes_choose", ctypes.c_uint32), ("lanes_set", ctypes.c_uint32),
                 ("lanes_query", ctypes.c_uint32), ("query_early", ctypes.c_uint32),
-                ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32)]
+                ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
+                ("keys_per_cta", ctypes.c_uint32), ("set_mode", ctypes.c_uint32)]
 
 
 class blowchoc_work(ctypes.Structure):
     _fields_ = [("filter", ctypes.c_void_p), ("d_keys", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("d_bitmap", ctypes.c_void_p)]
 
+
+class blowchoc_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("staging_bytes", ctypes.c_uint64),
+                ("streams", ctypes.c_uint32), ("max_wave_requests", ctypes.c_uint32)]
+
+
+class blowchoc_server_summary(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("keys", ctypes.c_uint64), ("waves", ctypes.c_uint64),
+                ("first_arrival_s", ctypes.c_double), ("last_done_s", ctypes.c_double),
+                ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+                ("max_latency_s", ctypes.c_double), ("mean_wave_requests", ctypes.c_double),
+                ("max_filter_bytes_used", ctypes.c_uint64), ("filters_admitted", ctypes.c_uint32),
+                ("filters_pending", ctypes.c_uint32)]
+
+
+REQ_INSERT, REQ_QUERY = 0, 1
 
 # name -> (argtypes, restype)
 _VP, _U64, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
@@ -67,6 +84,7 @@ _SIGS = {
     "blowchoc_read_words": ([_VP, _U64, _U64, _VP], _I),
     "blowchoc_write_words": ([_VP, _U64, _U64, _VP], _I),
     "blowchoc_clear": ([_VP, _VP], _I),
+    "blowchoc_set_cost_table": ([_VP, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
     "blowchoc_batch_create": ([ctypes.POINTER(_VP)], _I),
@@ -81,6 +99,27 @@ _SIGS = {
     "blowchoc_batch_autotune": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32,
                                  ctypes.POINTER(blowchoc_work), ctypes.c_uint32, _VP,
                                  ctypes.POINTER(blowchoc_tuning)], _I),
+    "blowchoc_server_create": ([ctypes.POINTER(blowchoc_server_config), ctypes.POINTER(_VP)], _I),
+    "blowchoc_server_add_filter": ([_VP, ctypes.POINTER(blowchoc_params), ctypes.POINTER(ctypes.c_uint32)], _I),
+    "blowchoc_server_remove_filter": ([_VP, ctypes.c_uint32], _I),
+    "blowchoc_server_submit": ([_VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _U64, _VP, ctypes.c_double,
+                                ctypes.POINTER(_U64)], _I),
+    "blowchoc_server_start": ([_VP], _I),
+    "blowchoc_server_wait": ([_VP, ctypes.c_double], _I),
+    "blowchoc_server_request_times": ([_VP, _U64, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
+    "blowchoc_server_stats": ([_VP, ctypes.POINTER(blowchoc_server_summary)], _I),
+    "blowchoc_server_filter": ([_VP, ctypes.c_uint32, ctypes.POINTER(_VP)], _I),
+    "blowchoc_server_destroy": ([_VP], _I),
+    "blowchoc_mlp_create": ([ctypes.c_uint32, _U64, ctypes.POINTER(_VP)], _I),
+    "blowchoc_mlp_destroy": ([_VP], _I),
+    "blowchoc_mlp_param_count": ([], ctypes.c_uint32),
+    "blowchoc_mlp_get_params": ([_VP, _VP, _VP], _I),
+    "blowchoc_mlp_set_params": ([_VP, _VP], _I),
+    "blowchoc_mlp_forward": ([_VP, _VP, _VP], _I),
+    "blowchoc_mlp_backward": ([_VP, _VP, ctypes.c_double, _VP], _I),
+    "blowchoc_mlp_adam_step": ([_VP, ctypes.c_float, _VP], _I),
+    "blowchoc_insert_sampled": ([_VP, _VP, _U64, _VP, ctypes.c_float, _U64, _VP, _VP, _VP], _I),
     "blowchoc_gather_probe": ([_VP, _U64, _U64, _U64, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP], _I),
     "blowchoc_get_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
     "blowchoc_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
@@ -188,6 +227,13 @@ def blowchoc_read_words(f, first: int, count: int, h_dst):
 
 def blowchoc_write_words(f, first: int, count: int, h_src):
     _check(load_library().blowchoc_write_words(f, int(first), int(count), h_src.ctypes.data))
+
+
+def blowchoc_set_cost_table(f, costs):
+    """costs: numpy float64 array of 513 * (k + 1) values, costs[L * (k + 1) + a]."""
+    import numpy as np
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    _check(load_library().blowchoc_set_cost_table(f, c.ctypes.data))
 
 
 def blowchoc_clear(f, stream=None):
@@ -314,6 +360,148 @@ class Batch:
         return blowchoc_batch_autotune(self.handle, ins, qry, stream)
 
 
+class Server:
+    """Request-serving loop (blowchoc_server_*). Host key and bitmap buffers
+    are numpy uint64 arrays (pinned torch tensors also work via .numpy());
+    the caller keeps them alive until wait() returns."""
+
+    def __init__(self, hbm_budget_bytes, staging_bytes=1 << 30, streams=4, max_wave_requests=64):
+        cfg = blowchoc_server_config(hbm_budget_bytes=int(hbm_budget_bytes),
+                                     staging_bytes=int(staging_bytes), streams=int(streams),
+                                     max_wave_requests=int(max_wave_requests))
+        h = _VP()
+        _check(load_library().blowchoc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = []
+
+    def add_filter(self, nblocks, k, choices, cost, cost_param, hash_seed, batch):
+        p = blowchoc_params(nblocks=int(nblocks), k=int(k), choices=int(choices), cost=int(cost),
+                            bitsel=0, cost_param=float(cost_param), hash_seed=int(hash_seed),
+                            batch=int(batch))
+        out = ctypes.c_uint32()
+        _check(load_library().blowchoc_server_add_filter(self.handle, ctypes.byref(p), ctypes.byref(out)))
+        return out.value
+
+    def remove_filter(self, fid):
+        _check(load_library().blowchoc_server_remove_filter(self.handle, int(fid)))
+
+    def submit(self, fid, kind, h_keys, h_bitmap=None, arrival_s=0.0):
+        rid = _U64()
+        self._keep.append((h_keys, h_bitmap))
+        _check(load_library().blowchoc_server_submit(
+            self.handle, int(fid), int(kind), h_keys.ctypes.data, len(h_keys),
+            h_bitmap.ctypes.data if h_bitmap is not None else None, float(arrival_s), ctypes.byref(rid)))
+        return rid.value
+
+    def start(self):
+        _check(load_library().blowchoc_server_start(self.handle))
+
+    def wait(self, timeout_s=600.0):
+        _check(load_library().blowchoc_server_wait(self.handle, float(timeout_s)))
+
+    def request_times(self, rid):
+        a, l, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load_library().blowchoc_server_request_times(self.handle, int(rid), ctypes.byref(a),
+                                                            ctypes.byref(l), ctypes.byref(d)))
+        return a.value, l.value, d.value
+
+    def stats(self):
+        out = blowchoc_server_summary()
+        _check(load_library().blowchoc_server_stats(self.handle, ctypes.byref(out)))
+        return out
+
+    def filter_handle(self, fid):
+        h = _VP()
+        _check(load_library().blowchoc_server_filter(self.handle, int(fid), ctypes.byref(h)))
+        return h
+
+    def words_host(self, fid):
+        import numpy as np
+        h = self.filter_handle(fid)
+        if not h.value:
+            return None
+        _, n = blowchoc_words(h)
+        out = np.empty(n, dtype=np.uint64)
+        blowchoc_read_words(h, 0, n, out)
+        return out
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().blowchoc_server_destroy(self.handle)
+        self.handle = None
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """The learned-cost network (blowchoc_mlp_*)."""
+
+    def __init__(self, k, seed):
+        h = _VP()
+        _check(load_library().blowchoc_mlp_create(int(k), int(seed), ctypes.byref(h)))
+        self.handle = h
+        self.k = int(k)
+        self.nparams = int(load_library().blowchoc_mlp_param_count())
+
+    def params(self):
+        import numpy as np
+        p = np.empty(self.nparams, dtype=np.float32)
+        _check(load_library().blowchoc_mlp_get_params(self.handle, p.ctypes.data, None))
+        return p
+
+    def grad(self):
+        import numpy as np
+        g = np.empty(self.nparams, dtype=np.float64)
+        _check(load_library().blowchoc_mlp_get_params(self.handle, None, g.ctypes.data))
+        return g
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load_library().blowchoc_mlp_set_params(self.handle, p.ctypes.data))
+
+    def forward(self, d_table, stream=None):
+        _check(load_library().blowchoc_mlp_forward(self.handle, _dev_ptr_any(d_table), _stream(stream)))
+
+    def backward(self, d_w, scale, stream=None):
+        _check(load_library().blowchoc_mlp_backward(self.handle, _dev_ptr_any(d_w), float(scale),
+                                                    _stream(stream)))
+
+    def adam_step(self, lr, stream=None):
+        _check(load_library().blowchoc_mlp_adam_step(self.handle, float(lr), _stream(stream)))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().blowchoc_mlp_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dev_ptr_any(x):
+    """Device address of a contiguous CUDA tensor of any dtype (or an int)."""
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return x.data_ptr()
+
+
+def blowchoc_insert_sampled(f, d_keys, n, d_table, tau, seed, d_w, d_choice=None, stream=None):
+    _check(load_library().blowchoc_insert_sampled(
+        f, _dev_ptr(d_keys), int(n), _dev_ptr_any(d_table), float(tau), int(seed), _dev_ptr_any(d_w),
+        _dev_ptr_any(d_choice) if d_choice is not None else None, _stream(stream)))
+
+
 def blowchoc_launch_count() -> int:
     return int(load_library().blowchoc_launch_count())
 
@@ -383,6 +571,9 @@ class Filter:
 
     def clear(self, stream=None):
         blowchoc_clear(self.handle, stream)
+
+    def set_cost_table(self, costs):
+        blowchoc_set_cost_table(self.handle, costs)
 
     def tuning(self):
         return blowchoc_get_tuning(self.handle)

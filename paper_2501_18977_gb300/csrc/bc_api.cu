@@ -91,15 +91,16 @@ double cost_value(int kind, double par, uint32_t k, uint32_t j, uint32_t a) {
 }
 
 // Integer rank of every reachable (L, a) cost: equal doubles share a rank,
-// so comparing ranks on the device is comparing the doubles exactly.
-std::vector<uint16_t> rank_table(int kind, double par, uint32_t k) {
+// so comparing ranks on the device is comparing the doubles exactly. With
+// `given` the costs come from a table instead of Eq. 4-6.
+std::vector<uint16_t> rank_table(int kind, double par, uint32_t k, const double *given = nullptr) {
     const uint32_t k1 = k + 1;
     std::vector<double> cost(513 * k1, INFINITY);
     std::vector<double> vals;
     vals.reserve(513 * k1);
     for (uint32_t L = 0; L <= 512; ++L)
         for (uint32_t a = 0; a <= k && L + a <= 512; ++a) {
-            cost[L * k1 + a] = cost_value(kind, par, k, L + a, a);
+            cost[L * k1 + a] = given ? given[L * k1 + a] : cost_value(kind, par, k, L + a, a);
             vals.push_back(cost[L * k1 + a]);
         }
     std::sort(vals.begin(), vals.end());
@@ -234,7 +235,7 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
                 "sequential insert launch");
         return BLOWCHOC_OK;
     }
-    if (B <= bc::kSmallBatchMax) {
+    if (B <= bc::kSingleCtaBatch || (!f->persistent && B <= bc::kSmallBatchMax)) {
         bc::Launch L{1, f->lanes_choose, s};
         BC_CUDA(counted(bc::launch_small_batch(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_counters)),
                 "small-batch insert launch");
@@ -243,7 +244,26 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
     int rc = ensure_sel(f, std::min(B, n));
     if (rc) return rc;
     if (f->persistent) {
-        bc::Launch L{f->sms * f->ctas_per_sm, f->lanes_choose, s};
+        const uint64_t per = std::min(B, n);
+        const uint64_t want = (per + (uint64_t)f->keys_per_cta - 1) / (uint64_t)f->keys_per_cta;
+        const uint64_t cap = (uint64_t)f->sms * (uint64_t)f->ctas_per_sm;
+        bc::Launch L{(int)std::max<uint64_t>(1, std::min(want, cap)), f->lanes_choose, s};
+        const uint64_t R = (f->dev.M + bc::kRangeBlocks - 1) / bc::kRangeBlocks;
+        if (f->set_mode == 1 && R <= bc::kSortedMaxRanges) {
+            const uint64_t need = 3 * R + 1 + per;
+            if (need > f->sorted_cap) {
+                cudaFree(f->d_sorted);
+                f->d_sorted = nullptr;
+                f->sorted_cap = 0;
+                BC_CUDA(cudaMalloc(&f->d_sorted, need * sizeof(uint32_t)), "cudaMalloc(sorted scratch)");
+                f->sorted_cap = need;
+            }
+            unsigned int *bar = reinterpret_cast<unsigned int *>(f->d_counters + 516);
+            BC_CUDA(counted(bc::launch_sorted_insert(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_sel,
+                                                     f->d_counters, bar, f->d_sorted, (uint32_t)R, f->sms)),
+                    "sorted insert launch");
+            return BLOWCHOC_OK;
+        }
         unsigned int *bar = reinterpret_cast<unsigned int *>(f->d_counters + 516);
         BC_CUDA(counted(bc::launch_persistent_insert(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_sel,
                                                      f->d_counters, bar, f->sms)),
@@ -303,6 +323,7 @@ int blowchoc_destroy(blowchoc_filter *f) {
     cudaFree(f->d_counters);
     cudaFree(f->d_rank);
     cudaFree(f->d_sel);
+    cudaFree(f->d_sorted);
     delete f;
     if (e != cudaSuccess) return cuda_fail(e, "blowchoc_destroy");
     return BLOWCHOC_OK;
@@ -344,6 +365,21 @@ int blowchoc_write_words(blowchoc_filter *f, uint64_t first, uint64_t count, con
     return BLOWCHOC_OK;
 }
 
+int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs) {
+    if (!f || !costs) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    if (f->dev.c < 2 || !f->d_rank) return fail(BLOWCHOC_EINVAL, "one choice has no cost");
+    const uint32_t k = f->dev.k, k1 = k + 1;
+    for (uint32_t L = 0; L <= 512; ++L)
+        for (uint32_t a = 0; a <= k && L + a <= 512; ++a)
+            if (!std::isfinite(costs[L * k1 + a])) return fail(BLOWCHOC_EINVAL, "cost table value not finite");
+    std::vector<uint16_t> rank = rank_table(0, 0.0, k, costs);
+    // ordered after earlier work on the home stream, like an insert would be
+    BC_CUDA(cudaMemcpyAsync(f->d_rank, rank.data(), rank.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                            f->home), "cost table upload");
+    BC_CUDA(cudaStreamSynchronize(f->home), "cost table upload");
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     if (!f || !out) return fail(BLOWCHOC_EINVAL, "NULL argument");
     out->lanes_choose = (uint32_t)f->lanes_choose;
@@ -352,6 +388,8 @@ int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     out->query_early = (uint32_t)f->query_early;
     out->ctas_per_sm = (uint32_t)f->ctas_per_sm;
     out->persistent = (uint32_t)f->persistent;
+    out->keys_per_cta = (uint32_t)f->keys_per_cta;
+    out->set_mode = (uint32_t)f->set_mode;
     return BLOWCHOC_OK;
 }
 
@@ -363,12 +401,17 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     if (t->query_early > 1) return fail(BLOWCHOC_EINVAL, "query_early must be 0 or 1");
     if (t->ctas_per_sm < 1 || t->ctas_per_sm > 16) return fail(BLOWCHOC_EINVAL, "ctas_per_sm must be in 1..16");
     if (t->persistent > 1) return fail(BLOWCHOC_EINVAL, "persistent must be 0 or 1");
+    if (t->keys_per_cta < 32 || t->keys_per_cta > (1u << 24))
+        return fail(BLOWCHOC_EINVAL, "keys_per_cta must be in 32..2^24");
+    if (t->set_mode > 1) return fail(BLOWCHOC_EINVAL, "set_mode must be 0 or 1");
     f->lanes_choose = (int)t->lanes_choose;
     f->lanes_set = (int)t->lanes_set;
     f->lanes_query = (int)t->lanes_query;
     f->query_early = (int)t->query_early;
     f->ctas_per_sm = (int)t->ctas_per_sm;
     f->persistent = (int)t->persistent;
+    f->keys_per_cta = (int)t->keys_per_cta;
+    f->set_mode = (int)t->set_mode;
     return BLOWCHOC_OK;
 }
 

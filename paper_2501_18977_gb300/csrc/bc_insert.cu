@@ -226,6 +226,147 @@ __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
     flush_counts(ins, skp, counters);
 }
 
+// ---------------------------------------------------------------------------
+// Sort-by-block set variant. After the choose phase of a batch, the chosen
+// blocks are bucketed by range of kRangeBlocks blocks (count, scan, scatter);
+// then each CTA takes whole ranges, stages the range's words in shared memory,
+// ORs the masks of the range's keys in with shared atomics and writes the
+// range back: no global atomics on the filter, one read and one write per
+// touched range. It pays when a batch hits blocks many times (small M or
+// large B).
+
+template <int C, int LANES>
+__global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
+    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
+    const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters, unsigned int *bar,
+    uint32_t *cnt, uint32_t *cur, uint32_t *off, uint32_t *perm, uint32_t R) {
+    constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint64_t *s_range = reinterpret_cast<uint64_t *>(s_dyn);            // kRangeBlocks x 8 words
+    uint32_t *s_range32 = reinterpret_cast<uint32_t *>(s_dyn);
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_dyn + kRangeBlocks * 64);
+    __shared__ uint64_t s_amul[32];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    __shared__ uint32_t s_part[kThreads];
+    stage_bit_mults(f, s_amul);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    if constexpr (C == 1) __syncthreads();
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long *err = counters + 2;
+    unsigned int target = 0;
+    uint32_t ins = 0, skp = 0;
+    for (uint64_t s0 = 0; s0 < n; s0 += B) {
+        const uint64_t cnt_b = (n - s0) < B ? (n - s0) : B;
+        const uint64_t *bk = keys + s0;
+        // choose against the filter as the batch starts
+        for (uint64_t base = warp * G; base < cnt_b; base += nwarps * G) {
+            const uint64_t i = base + g;
+            const bool valid = i < cnt_b;
+            const uint64_t x = valid ? load_key(bk + i) : 0ull;
+            uint64_t m[W];
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank, m);
+            if (valid && q == 0) {
+                sel[i] = (uint8_t)s;
+                if (s == kSkip) ++skp; else ++ins;
+            }
+        }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, err)) return;
+        // count keys per range
+        for (uint64_t i = tid; i < cnt_b; i += nthreads) {
+            const uint32_t s = __ldcg(sel + i);
+            if (s == kSkip) continue;
+            const uint64_t x = load_key(bk + i);
+            atomicAdd(cnt + (uint32_t)(block_addr(f, block_mult(f, s), x) / kRangeBlocks), 1u);
+        }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, err)) return;
+        // exclusive scan of the counts (one CTA), cursors to zero
+        if (blockIdx.x == 0) {
+            const uint32_t per = (R + blockDim.x - 1) / blockDim.x;
+            const uint32_t lo = threadIdx.x * per, hi = lo + per < R ? lo + per : R;
+            uint32_t sum = 0;
+            for (uint32_t r = lo; r < hi; ++r) sum += __ldcg(cnt + r);
+            s_part[threadIdx.x] = sum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t acc = 0;
+                for (int t = 0; t < (int)blockDim.x; ++t) {
+                    const uint32_t v = s_part[t];
+                    s_part[t] = acc;
+                    acc += v;
+                }
+                off[R] = acc;
+            }
+            __syncthreads();
+            uint32_t acc = s_part[threadIdx.x];
+            for (uint32_t r = lo; r < hi; ++r) {
+                off[r] = acc;
+                acc += __ldcg(cnt + r);
+                cur[r] = 0;
+            }
+        }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, err)) return;
+        // scatter key indices into their ranges
+        for (uint64_t i = tid; i < cnt_b; i += nthreads) {
+            const uint32_t s = __ldcg(sel + i);
+            if (s == kSkip) continue;
+            const uint64_t x = load_key(bk + i);
+            const uint32_t r = (uint32_t)(block_addr(f, block_mult(f, s), x) / kRangeBlocks);
+            perm[__ldcg(off + r) + atomicAdd(cur + r, 1u)] = (uint32_t)i;
+        }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, err)) return;
+        // apply: one range at a time per CTA, staged in shared memory
+        for (uint32_t r = blockIdx.x; r < R; r += gridDim.x) {
+            const uint32_t c0 = __ldcg(off + r), c1 = __ldcg(off + r + 1);
+            if (threadIdx.x == 0) cnt[r] = 0;  // ready for the next batch
+            if (c0 == c1) continue;
+            const uint64_t first = (uint64_t)r * kRangeBlocks;
+            const uint64_t nb = f.M - first < kRangeBlocks ? f.M - first : kRangeBlocks;
+            const uint64_t *src = f.words + first * kBlockWords;
+            for (uint32_t w = threadIdx.x; w < nb * kBlockWords; w += blockDim.x) s_range[w] = __ldcg(src + w);
+            __syncthreads();
+            for (uint32_t base = c0 + wib * G; base < c1; base += wpc * G) {
+                const uint32_t idx = base + g;
+                const bool valid = idx < c1;
+                const uint32_t i = valid ? __ldcg(perm + idx) : 0u;
+                const uint32_t s = valid ? (uint32_t)__ldcg(sel + i) : kSkip;
+                const uint64_t x = valid ? load_key(bk + i) : 0ull;
+                uint64_t m[W];
+                key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+                if (valid) {
+                    const uint64_t local = block_addr(f, block_mult(f, s), x) - first;
+                    uint32_t *dst = s_range32 + (local * kBlockWords + (uint64_t)q * W) * 2;
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        if ((uint32_t)m[j]) atomicOr(dst + 2 * j, (uint32_t)m[j]);
+                        if ((uint32_t)(m[j] >> 32)) atomicOr(dst + 2 * j + 1, (uint32_t)(m[j] >> 32));
+                    }
+                }
+            }
+            __syncthreads();
+            uint64_t *dst = f.words + first * kBlockWords;
+            for (uint32_t w = threadIdx.x; w < nb * kBlockWords; w += blockDim.x) dst[w] = s_range[w];
+            __syncthreads();
+        }
+        if (s0 + B < n) {
+            target += gridDim.x;
+            if (!grid_barrier(bar, target, err)) return;
+        }
+    }
+    flush_counts(ins, skp, counters);
+}
+
 inline size_t rank_bytes(int C, uint32_t k) { return C > 1 ? 513u * (k + 1) * sizeof(uint16_t) : 0; }
 
 template <int C>
@@ -298,7 +439,56 @@ cudaError_t persistent_dispatch(const Launch &L, const DevFilter &f, const uint6
     }
 }
 
+template <int C, int LANES>
+cudaError_t sorted_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n, uint64_t B,
+                          const uint16_t *rank, uint8_t *sel, unsigned long long *counters, unsigned int *bar,
+                          uint32_t *scratch, uint32_t R, int sms) {
+    const size_t sm = kRangeBlocks * 64 + rank_bytes(C, f.k);
+    cudaError_t e = cudaFuncSetAttribute(sorted_insert_kernel<C, LANES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sorted_insert_kernel<C, LANES>, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int want = L.grid > 0 ? L.grid : 1;
+    const int grid = want < per_sm * sms ? want : per_sm * sms;
+    e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), L.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, (size_t)R * sizeof(uint32_t), L.stream);
+    if (e != cudaSuccess) return e;
+    uint32_t *cnt = scratch, *cur = scratch + R, *off = scratch + 2 * (size_t)R, *perm = scratch + 3 * (size_t)R + 1;
+    void *args[] = {(void *)&f, (void *)&keys, (void *)&n, (void *)&B, (void *)&rank, (void *)&sel,
+                    (void *)&counters, (void *)&bar, (void *)&cnt, (void *)&cur, (void *)&off, (void *)&perm,
+                    (void *)&R};
+    return cudaLaunchCooperativeKernel((const void *)sorted_insert_kernel<C, LANES>, dim3(grid), dim3(kThreads),
+                                       args, sm, L.stream);
+}
+
+template <int C>
+cudaError_t sorted_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n, uint64_t B,
+                            const uint16_t *rank, uint8_t *sel, unsigned long long *counters, unsigned int *bar,
+                            uint32_t *scratch, uint32_t R, int sms) {
+    switch (L.lanes) {
+        case 1:  // one lane per key: register-hungry next to the staged range
+        case 2: return sorted_launch<C, 2>(L, f, keys, n, B, rank, sel, counters, bar, scratch, R, sms);
+        case 4: return sorted_launch<C, 4>(L, f, keys, n, B, rank, sel, counters, bar, scratch, R, sms);
+        case 8: return sorted_launch<C, 8>(L, f, keys, n, B, rank, sel, counters, bar, scratch, R, sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sorted_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                 uint64_t B, const uint16_t *rank, uint8_t *sel, unsigned long long *counters,
+                                 unsigned int *bar, uint32_t *scratch, uint32_t R, int sms) {
+    switch (C) {
+        case 1: return sorted_dispatch<1>(L, f, keys, n, B, rank, sel, counters, bar, scratch, R, sms);
+        case 2: return sorted_dispatch<2>(L, f, keys, n, B, rank, sel, counters, bar, scratch, R, sms);
+        case 3: return sorted_dispatch<3>(L, f, keys, n, B, rank, sel, counters, bar, scratch, R, sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_persistent_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                                      uint64_t n, uint64_t B, const uint16_t *rank, uint8_t *sel,

@@ -10,6 +10,8 @@ namespace bc {
 
 // Largest batch the single-CTA batch kernel holds in shared memory.
 constexpr uint64_t kSmallBatchMax = 16384;
+// Batches up to this size use the single-CTA kernel in blowchoc_insert.
+constexpr uint64_t kSingleCtaBatch = 2048;
 
 struct Launch {
     int grid;          // CTAs
@@ -34,6 +36,16 @@ cudaError_t launch_set(const Launch &L, const DevFilter &f, const uint64_t *keys
 cudaError_t launch_persistent_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                                      uint64_t n, uint64_t B, const uint16_t *rank, uint8_t *sel,
                                      unsigned long long *counters, unsigned int *bar, int sms);
+
+// Sort-by-block variant of the persistent insert: blocks per range, and the
+// number of ranges up to which it is offered.
+constexpr uint32_t kRangeBlocks = 256;
+constexpr uint64_t kSortedMaxRanges = 1u << 16;
+
+// scratch: 3 R + 1 + min(B, n) u32 (counts, cursors, offsets, key order).
+cudaError_t launch_sorted_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                 uint64_t B, const uint16_t *rank, uint8_t *sel, unsigned long long *counters,
+                                 unsigned int *bar, uint32_t *scratch, uint32_t R, int sms);
 
 // B = 1: one warp inserts the keys strictly one after another.
 cudaError_t launch_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys,

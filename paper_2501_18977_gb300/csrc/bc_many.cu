@@ -587,6 +587,8 @@ int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out) {
     out->query_early = (uint32_t)b->query_early;
     out->ctas_per_sm = (uint32_t)b->ctas_per_sm;
     out->persistent = 1;
+    out->keys_per_cta = 0;
+    out->set_mode = 0;
     return BLOWCHOC_OK;
 }
 

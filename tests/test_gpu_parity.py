@@ -141,6 +141,16 @@ def test_config_small_uniform_full():
     dict(lanes_choose=1, lanes_set=2, lanes_query=1, query_early=0, ctas_per_sm=8, persistent=1),
     dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=1, ctas_per_sm=1, persistent=1),
     dict(lanes_choose=8, lanes_set=2, lanes_query=4, query_early=1, ctas_per_sm=16, persistent=1),
+    dict(lanes_choose=2, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=8, persistent=1,
+         keys_per_cta=32),
+    dict(lanes_choose=4, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=4, persistent=1,
+         keys_per_cta=1 << 20),
+    dict(lanes_choose=2, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=8, persistent=1,
+         set_mode=1),
+    dict(lanes_choose=4, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=2, persistent=1,
+         keys_per_cta=64, set_mode=1),
+    dict(lanes_choose=8, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=16, persistent=1,
+         set_mode=1),
 ])
 def test_results_independent_of_launch_configuration(tune):
     """Every launch configuration gives the oracle's words and bitmap."""
@@ -170,9 +180,37 @@ def test_set_tuning_rejects_bad_values():
     try:
         before = (f.tuning().lanes_query, f.tuning().ctas_per_sm)
         for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=2),
-                    dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2)]:
+                    dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2),
+                    dict(keys_per_cta=8), dict(set_mode=2)]:
             with pytest.raises(bc.BlowChocError):
                 f.set_tuning(**bad)
         assert (f.tuning().lanes_query, f.tuning().ctas_per_sm) == before
     finally:
         f.close()
+
+
+@pytest.mark.parametrize("M,k,c,kind,par,B,n", [
+    (999, 11, 2, COST_EXP, PHI, 4096, 60000),      # partial last range
+    (1, 5, 3, COST_MIX, 50.0, 3000, 20000),        # one block, one range
+    (70000, 14, 2, COST_MIX, 50.0, 65536, 300000), # many ranges, dense batches
+    (32768, 14, 2, COST_MIX, 50.0, 65536, 1000000),  # the small uniform configuration
+    (6150, 16, 3, COST_LA, 3.5, 1 << 20, 200000),  # one batch
+])
+def test_sort_by_block_set_matches_oracle(M, k, c, kind, par, B, n):
+    import paper_2501_18977_gb300 as bc
+    keys = workloads.uniform_keys(M + 17, n)
+    neg = workloads.disjoint_keys(M + 18, 50000, keys)
+    queries = np.concatenate([keys[:50000], neg])
+    f = bc.Filter(M, k, c, kind, par, hash_seed=5, batch=B)
+    try:
+        f.set_tuning(set_mode=1, persistent=1)
+        f.insert(to_dev(keys))
+        bm = f.query(to_dev(queries)).cpu().numpy().view(np.uint64)
+        words = f.words_host()
+        st = f.stats()
+    finally:
+        f.close()
+    o, obm, _, _ = oracle_run(M, k, c, kind, par, 5, B, keys, queries)
+    assert np.array_equal(words, o.words)
+    assert np.array_equal(bm, obm)
+    assert (st.inserted, st.skipped) == (o.inserted, o.skipped)

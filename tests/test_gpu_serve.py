@@ -1,0 +1,123 @@
+"""The serving loop: every request's result equals the result of running the
+requests of its filter alone, one after another, in arrival order (tolerance
+0), while waves of requests of different filters share launches and overlap
+on several streams; filters beyond the HBM budget wait for admission."""
+import numpy as np
+import pytest
+
+import workloads
+from tests.gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_trace(n_filters=12, n_requests=300, max_keys=20000, seed=7):
+    filters, reqs = workloads.serving_config(seed=seed, n_filters=n_filters, n_requests=n_requests,
+                                             max_keys=max_keys)
+    for f in filters:          # smaller filters for a quick test: 2^16..2^22 bits
+        f["M"] = max(1, f["M"] // 512)
+        f["B"] = 1 << max(0, (max(f["M"] // 2, 1)).bit_length() - 1)
+    return filters, reqs
+
+
+def _alone(bc, filters, reqs, keys):
+    """Each filter's requests through the plain API, in arrival order."""
+    import torch
+    fs = [bc.Filter(f["M"], 14, 2, bc.COST_MIX, 50.0, hash_seed=f["key_seed"], batch=f["B"])
+          for f in filters]
+    out = {}
+    for r in sorted(reqs, key=lambda r: (r["arrival"], r["index"])):
+        f = fs[r["filter"]]
+        d = to_dev(keys[r["index"]])
+        if r["kind"] == 0:
+            f.insert(d)
+        else:
+            out[r["index"]] = f.query(d).cpu().numpy().view(np.uint64).copy()
+    torch.cuda.synchronize()
+    words = [f.words_host() for f in fs]
+    for f in fs:
+        f.close()
+    return out, words
+
+
+def _serve(bc, filters, reqs, keys, budget=1 << 30, streams=3, wave=8, time_scale=1e-4,
+           remove=()):
+    srv = bc.Server(budget, staging_bytes=64 << 20, streams=streams, max_wave_requests=wave)
+    ids = [srv.add_filter(f["M"], 14, 2, bc.COST_MIX, 50.0, f["key_seed"], f["B"]) for f in filters]
+    bms = {}
+    for r in reqs:
+        h = keys[r["index"]]
+        bm = np.zeros((r["n"] + 63) // 64, dtype=np.uint64) if r["kind"] == 1 else None
+        if bm is not None:
+            bms[r["index"]] = bm
+        srv.submit(ids[r["filter"]], r["kind"], h, bm, r["arrival"] * time_scale)
+    pending_before = srv.stats().filters_pending
+    srv.start()
+    for fid in remove:
+        srv.remove_filter(fid)
+    srv.wait(60.0)
+    st = srv.stats()
+    words = [srv.words_host(i) for i in ids]
+    srv.close()
+    return bms, words, st, pending_before
+
+
+def test_served_results_equal_alone_results():
+    import paper_2501_18977_gb300 as bc
+    filters, reqs = _small_trace()
+    keys = {r["index"]: workloads.serving_keys(filters, r, seed=7) for r in reqs}
+    alone, alone_words = _alone(bc, filters, reqs, keys)
+    served, served_words, st, _ = _serve(bc, filters, reqs, keys)
+    assert st.completed == len(reqs)
+    assert st.waves >= 1 and st.mean_wave_requests >= 1.0
+    assert st.p50_latency_s <= st.p99_latency_s <= st.max_latency_s
+    for j, bm in alone.items():
+        assert np.array_equal(served[j], bm), j
+    for a, b in zip(alone_words, served_words):
+        assert np.array_equal(a, b)
+
+
+def test_concurrent_waves_share_launches():
+    """With all requests arriving at once, waves carry many filters' requests."""
+    import paper_2501_18977_gb300 as bc
+    filters, reqs = _small_trace(n_filters=16, n_requests=200, seed=8)
+    keys = {r["index"]: workloads.serving_keys(filters, r, seed=8) for r in reqs}
+    alone, _ = _alone(bc, filters, reqs, keys)
+    served, _, st, _ = _serve(bc, filters, reqs, keys, time_scale=0.0, wave=16, streams=4)
+    assert st.mean_wave_requests > 2.0
+    for j, bm in alone.items():
+        assert np.array_equal(served[j], bm), j
+
+
+def test_admission_waits_for_budget():
+    import paper_2501_18977_gb300 as bc
+    filters, reqs = _small_trace(n_filters=4, n_requests=80, seed=9)
+    for f in filters:
+        f["M"], f["B"] = 4096, 2048
+    one = 4096 * 64 + 513 * 15 * 2 + 520 * 8
+    keys = {r["index"]: workloads.serving_keys(filters, r, seed=9) for r in reqs}
+    alone, _ = _alone(bc, filters, reqs, keys)
+    served, _, st, pending = _serve(bc, filters, reqs, keys, budget=int(2.5 * one), remove=(0, 1))
+    assert pending == 2
+    assert st.completed == len(reqs)
+    assert st.max_filter_bytes_used <= int(2.5 * one)
+    for j, bm in alone.items():
+        assert np.array_equal(served[j], bm), j
+
+
+def test_server_rejects_what_cannot_fit():
+    import paper_2501_18977_gb300 as bc
+    srv = bc.Server(1 << 20, staging_bytes=1 << 16, streams=1, max_wave_requests=1)
+    try:
+        with pytest.raises(bc.BlowChocError) as ei:
+            srv.add_filter(1 << 20, 14, 2, bc.COST_MIX, 50.0, 1, 1024)
+        assert ei.value.code == bc.BLOWCHOC_EBUDGET
+        fid = srv.add_filter(64, 14, 2, bc.COST_MIX, 50.0, 1, 1024)
+        big = workloads.uniform_keys(1, 1 << 14)
+        with pytest.raises(bc.BlowChocError) as ei:
+            srv.submit(fid, bc.REQ_INSERT, big)
+        assert ei.value.code == bc.BLOWCHOC_EBUDGET
+        with pytest.raises(bc.BlowChocError):
+            srv.submit(fid, 7, big[:10])
+    finally:
+        srv.close()

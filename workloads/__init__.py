@@ -30,6 +30,16 @@ def splitmix64(seed: int, n: int, start: int = 0) -> np.ndarray:
         return z ^ (z >> np.uint64(31))
 
 
+def splitmix64_at(seed: int, positions) -> np.ndarray:
+    """splitmix64 outputs of `seed` at the given 0-based stream positions."""
+    with np.errstate(over="ignore"):
+        idx = np.asarray(positions, dtype=np.uint64) + np.uint64(1)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
 def uniform_keys(seed: int, n: int) -> np.ndarray:
     """n uniform 64-bit keys: the first n splitmix64 outputs of `seed`."""
     return splitmix64(seed, n)
@@ -155,3 +165,55 @@ def many_filter_keys(item):
     half = (item["n"] + 1) // 2
     other = splitmix64(item["query_seed"], item["n"] // 2)
     return keys, np.concatenate([keys[:half], other])
+
+
+def serving_config(seed: int = 5, n_filters: int = 64, n_requests: int = 10000,
+                   query_frac: float = 0.7, max_keys: int = 1000000):
+    """The serving workload: filters of 2^U bits with U uniform in [20, 31]
+    (rounded up to whole 512-bit blocks), batch 2^floor(log2(M / 2)) (at
+    least 1); requests with exponential inter-arrival gaps of mean 1 (scaled
+    by the caller to an offered rate), kind query with probability query_frac,
+    target filter uniform, size log-uniform in [1, max_keys]. Insert request j
+    of filter f takes the next keys of the filter's splitmix64 stream (seed
+    (seed << 40) | f); a query takes half of its keys from keys inserted
+    earlier into its filter (uniform positions) and half from a fresh stream
+    (seed (seed << 40) | (1 << 32) | j)."""
+    u = uniform01(seed, n_filters)
+    filters = []
+    for f in range(n_filters):
+        U = 20.0 + 11.0 * float(u[f])
+        M = int(math.ceil((2.0 ** U) / 512.0))
+        B = 1 << max(0, int(math.floor(math.log2(max(M / 2.0, 1.0)))))
+        filters.append(dict(index=f, M=M, B=B, key_seed=(seed << 40) | f))
+    r = uniform01(seed + 1, 4 * n_requests).reshape(n_requests, 4)
+    gaps = -np.log(r[:, 0])
+    arrivals = np.cumsum(gaps) - gaps[0]
+    requests = []
+    inserted = [0] * n_filters
+    for j in range(n_requests):
+        kind = 1 if r[j, 1] < query_frac else 0
+        f = min(n_filters - 1, int(r[j, 2] * n_filters))
+        n = max(1, min(max_keys, int(math.floor(math.exp(r[j, 3] * math.log(max_keys + 1.0))))))
+        req = dict(index=j, arrival=float(arrivals[j]), kind=kind, filter=f, n=n)
+        if kind == 0:
+            req["key_start"] = inserted[f]
+            inserted[f] += n
+        else:
+            req["members_from"] = inserted[f]
+        requests.append(req)
+    return filters, requests
+
+
+def serving_keys(filters, req, seed: int = 5):
+    """Keys of one request of serving_config."""
+    f = filters[req["filter"]]
+    n = req["n"]
+    if req["kind"] == 0:
+        return splitmix64(f["key_seed"], n, req["key_start"])
+    have = req["members_from"]
+    n_mem = n // 2 if have else 0
+    fresh = splitmix64((seed << 40) | (1 << 32) | req["index"], n - n_mem)
+    if n_mem == 0:
+        return fresh
+    pos = splitmix64((seed << 40) | (2 << 32) | req["index"], n_mem) % np.uint64(have)
+    return np.concatenate([splitmix64_at(f["key_seed"], pos), fresh])
