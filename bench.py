@@ -25,7 +25,9 @@ grows 512 MiB filters (k = 12; one choice, and two and three choices under
 each cost) from 20 to 6 bits per key against 10^8 negatives per point;
 `batching` reports the FPR and load-balance cost of batch size B against
 one-key-at-a-time insertion; `small` times the small uniform configuration
-(10^6 keys into 2^24 bits, k = 14, two choices, cost^MIX, B = 65536 and 1).
+(10^6 keys into 2^24 bits, k = 14, two choices, cost^MIX, B = 65536 and 1);
+`learn` trains the learned cost on the small configuration's shape and
+compares its greedy filter with cost^EXP and cost^MIX on held-out keys.
 """
 import argparse
 import json
@@ -59,8 +61,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small"],
-                    default="dna")
+    ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
+                                           "learn"], default="dna")
+    ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--requests", type=int, default=10000)
     return ap.parse_args()
 
@@ -532,6 +535,52 @@ def run_small(args):
                       "rows": rows}))
 
 
+def run_learn(args):
+    """Learned cost: train on 32 small filters per step (512 blocks, the small
+    configuration's 16 bits per key, k = 14, c = 2), then insert
+    10^6 held-out keys (seed 11) greedily with the learned table, cost^EXP
+    (golden ratio) and cost^MIX (sigma = 50); FPR from 10^8 negatives
+    (seed 12) and from the load histogram."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    from paper_2501_18977_gb300.learned import train_cost_table
+    M, k, c, B, n = 32768, 14, 2, 65536, 1_000_000
+    held = torch.from_numpy(workloads.uniform_keys(11, n).view(np.int64)).cuda()
+    neg = torch.from_numpy(workloads.uniform_keys(12, 100_000_000).view(np.int64)).cuda()
+    bm = torch.empty((neg.numel() + 63) // 64, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    # training filters: 32 filters of 512 blocks at the same 16 bits per key, k, c and 16 batches
+    Mt = 512
+    nt = Mt * 512 // 16
+    table, rewards, mlp = train_cost_table(Mt, k, c, nt // 16, nt, steps=args.train_steps, filters=32,
+                                           tau=0.05, lr=3e-3, seed=7)
+    train_s = time.perf_counter() - t0
+    mlp.close()
+
+    def evaluate(kind, par, tab=None):
+        f = bc.Filter(M, k, c, kind, par, hash_seed=1, batch=B)
+        if tab is not None:
+            f.set_cost_table(tab)
+        f.insert(held)
+        f.query(neg, bm)
+        torch.cuda.synchronize()
+        W = int(np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")[: neg.numel()].sum())
+        st = f.stats()
+        f.close()
+        return {"fpr": W / neg.numel(), "fpr_est_hist": st.fpr_est, "set_bits": st.set_bits}
+
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    learned = evaluate(bc.COST_EXP, phi, table)
+    exp_cost = evaluate(bc.COST_EXP, phi)
+    mix_cost = evaluate(bc.COST_MIX, 50.0)
+    print(json.dumps({"workload": "learned_cost", "M": M, "k": k, "c": c, "B": B, "n": n,
+                      "train_steps": args.train_steps, "train_seconds": round(train_s, 2),
+                      "reward_first10": float(np.mean(rewards[:10])), "reward_last10": float(np.mean(rewards[-10:])),
+                      "learned": learned, "exp_golden_ratio": exp_cost, "mix_sigma50": mix_cost,
+                      "fpr_gain_vs_exp": exp_cost["fpr"] / learned["fpr"] if learned["fpr"] else None,
+                      "note": "gain > 1 means the learned table gives a lower FPR than cost^EXP"}))
+
+
 def golden_pbar():
     """Mean 1-based index of the first candidate block holding an inserted
     31-mer of this workload, as counted by the oracle (tests/golden)."""
@@ -617,6 +666,9 @@ def main():
         return
     if args.workload == "small":
         run_small(args)
+        return
+    if args.workload == "learn":
+        run_learn(args)
         return
     import torch
     import torch.distributed as dist

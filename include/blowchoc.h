@@ -379,8 +379,11 @@ int blowchoc_mlp_set_params(blowchoc_mlp *m, const float *h_params);
 /* d_table[L (k+1) + a] = g(((L + a) / 512, a / k)) for L = 0..512, a = 0..k. */
 int blowchoc_mlp_forward(blowchoc_mlp *m, float *d_table, void *stream);
 
-/* gradient += scale * sum_p d_w[p] * d g(x_p) / d parameters. */
-int blowchoc_mlp_backward(blowchoc_mlp *m, const float *d_w, double scale, void *stream);
+/* gradient += sum_r d_scales[r] * sum_p d_w[r * P + p] * d g(x_p) / d params,
+ * P = 513 (k + 1): `rows` rows of per-point weights (device), one device
+ * scale per row (e.g. one training filter's advantage each). */
+int blowchoc_mlp_backward(blowchoc_mlp *m, const float *d_w, uint32_t rows, const double *d_scales,
+                          void *stream);
 
 /* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) down the accumulated
  * gradient, which is then cleared. */
@@ -467,6 +470,16 @@ int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_
  */
 int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, uint64_t nreads, uint64_t seed,
                           uint32_t lanes, uint32_t ctas_per_sm, uint64_t *d_sink, void *stream);
+
+/*
+ * blowchoc_barrier_selftest -- diagnostic of the bounded device waits, not
+ * part of the filter: a cooperative launch of `ctas` CTAs in which the last
+ * CTA never arrives at a grid barrier; the others wait at most `seconds`
+ * (0 < seconds <= 10) of SM clock and give up. Returns BLOWCHOC_ETIMEOUT when
+ * the bound worked (the expected outcome), BLOWCHOC_OK never, and leaves the
+ * context usable. Synchronises `stream`. Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int blowchoc_barrier_selftest(uint32_t ctas, double seconds, void *stream);
 
 /* Text of the calling thread's last error ("" if none). Never NULL. */
 const char *blowchoc_last_error(void);

@@ -16,4 +16,5 @@ from .binding import (  # noqa: F401
     blowchoc_query_many, blowchoc_batch_record, blowchoc_batch_replay, blowchoc_batch_get_tuning,
     blowchoc_batch_set_tuning, blowchoc_batch_autotune, Server, blowchoc_server_config,
     blowchoc_server_summary, REQ_INSERT, REQ_QUERY, Mlp, blowchoc_insert_sampled,
+    blowchoc_barrier_selftest,
     load_library, exported_symbols, LIB_PATH)

@@ -117,9 +117,10 @@ _SIGS = {
     "blowchoc_mlp_get_params": ([_VP, _VP, _VP], _I),
     "blowchoc_mlp_set_params": ([_VP, _VP], _I),
     "blowchoc_mlp_forward": ([_VP, _VP, _VP], _I),
-    "blowchoc_mlp_backward": ([_VP, _VP, ctypes.c_double, _VP], _I),
+    "blowchoc_mlp_backward": ([_VP, _VP, ctypes.c_uint32, _VP, _VP], _I),
     "blowchoc_mlp_adam_step": ([_VP, ctypes.c_float, _VP], _I),
     "blowchoc_insert_sampled": ([_VP, _VP, _U64, _VP, ctypes.c_float, _U64, _VP, _VP, _VP], _I),
+    "blowchoc_barrier_selftest": ([ctypes.c_uint32, ctypes.c_double, _VP], _I),
     "blowchoc_gather_probe": ([_VP, _U64, _U64, _U64, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP], _I),
     "blowchoc_get_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
     "blowchoc_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
@@ -468,9 +469,11 @@ class Mlp:
     def forward(self, d_table, stream=None):
         _check(load_library().blowchoc_mlp_forward(self.handle, _dev_ptr_any(d_table), _stream(stream)))
 
-    def backward(self, d_w, scale, stream=None):
-        _check(load_library().blowchoc_mlp_backward(self.handle, _dev_ptr_any(d_w), float(scale),
-                                                    _stream(stream)))
+    def backward(self, d_w, d_scales, stream=None):
+        """d_w: device float32 rows x 513 (k + 1); d_scales: device float64 rows."""
+        rows = d_scales.numel()
+        _check(load_library().blowchoc_mlp_backward(self.handle, _dev_ptr_any(d_w), int(rows),
+                                                    _dev_ptr_any(d_scales), _stream(stream)))
 
     def adam_step(self, lr, stream=None):
         _check(load_library().blowchoc_mlp_adam_step(self.handle, float(lr), _stream(stream)))
@@ -500,6 +503,12 @@ def blowchoc_insert_sampled(f, d_keys, n, d_table, tau, seed, d_w, d_choice=None
     _check(load_library().blowchoc_insert_sampled(
         f, _dev_ptr(d_keys), int(n), _dev_ptr_any(d_table), float(tau), int(seed), _dev_ptr_any(d_w),
         _dev_ptr_any(d_choice) if d_choice is not None else None, _stream(stream)))
+
+
+def blowchoc_barrier_selftest(ctas=8, seconds=0.5, stream=None) -> int:
+    """Runs the bounded-barrier diagnostic; returns the library's code
+    (BLOWCHOC_ETIMEOUT when the bound worked)."""
+    return int(load_library().blowchoc_barrier_selftest(int(ctas), float(seconds), _stream(stream)))
 
 
 def blowchoc_launch_count() -> int:

@@ -64,18 +64,24 @@ __device__ __forceinline__ void warp_add(double *dst, float v, int lane) {
     if (lane == 0 && v != 0.0f) atomicAdd(dst, (double)v);
 }
 
-// grad += scale * sum_p w[p] * d g(x_p) / d params, one thread per grid point.
+// grad += sum_r scales[r] * sum_p w[r][p] * d g(x_p) / d params: rows r of
+// per-point weights (one per training filter) with one scale each; one
+// thread per grid point.
 __global__ void __launch_bounds__(128) mlp_backward_kernel(const float *__restrict__ params, uint32_t k,
-                                                           const float *__restrict__ w, double scale,
+                                                           const float *__restrict__ w, uint32_t rows,
+                                                           const double *__restrict__ scales,
                                                            double *__restrict__ grad) {
     __shared__ float p[kParams];
     for (int t = threadIdx.x; t < kParams; t += blockDim.x) p[t] = params[t];
     __syncthreads();
-    const uint32_t k1 = k + 1;
+    const uint32_t k1 = k + 1, npts = 513u * k1;
     const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const bool valid = idx < 513u * k1;
-    const float gw = valid ? (float)(scale * (double)w[idx]) : 0.0f;
+    const bool valid = idx < npts;
+    double acc = 0.0;
+    if (valid)
+        for (uint32_t r = 0; r < rows; ++r) acc += scales[r] * (double)w[(uint64_t)r * npts + idx];
+    const float gw = (float)acc;
     if (__ballot_sync(0xffffffffu, gw != 0.0f) == 0u) return;  // whole warp idle
     const uint32_t L = valid ? idx / k1 : 0, a = valid ? idx % k1 : 0;
     const float x0 = (float)(L + a) / 512.0f, x1 = (float)a / (float)k;
@@ -312,11 +318,12 @@ int blowchoc_mlp_forward(blowchoc_mlp *m, float *d_table, void *stream) {
     return BLOWCHOC_OK;
 }
 
-int blowchoc_mlp_backward(blowchoc_mlp *m, const float *d_w, double scale, void *stream) {
-    if (!m || !d_w) return bc_set_error(BLOWCHOC_EINVAL, "NULL argument");
+int blowchoc_mlp_backward(blowchoc_mlp *m, const float *d_w, uint32_t rows, const double *d_scales,
+                          void *stream) {
+    if (!m || !d_w || !d_scales || rows == 0) return bc_set_error(BLOWCHOC_EINVAL, "bad backward arguments");
     const uint32_t npts = 513u * (m->k + 1);
-    mlp_backward_kernel<<<(npts + 127) / 128, 128, 0, (cudaStream_t)stream>>>(m->d_params, m->k, d_w, scale,
-                                                                              m->d_grad);
+    mlp_backward_kernel<<<(npts + 127) / 128, 128, 0, (cudaStream_t)stream>>>(m->d_params, m->k, d_w, rows,
+                                                                              d_scales, m->d_grad);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bc_set_error(BLOWCHOC_ECUDA, cudaGetErrorString(e));
     bc_note_launch();

@@ -94,7 +94,7 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
 // `target`. A wait past kBarrierCycles, or an error word already set by
 // another CTA, sets *err and returns false; the caller then leaves.
 __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int target,
-                                             unsigned long long *err) {
+                                             unsigned long long *err, long long limit = kBarrierCycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -104,7 +104,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int tar
         const long long t0 = clock64();
         while (ld_acquire(bar) < target) {
             if (*reinterpret_cast<volatile unsigned long long *>(err) != 0ull ||
-                clock64() - t0 > kBarrierCycles) {
+                clock64() - t0 > limit) {
                 atomicExch(err, 1ull);
                 ok = 0;
                 break;

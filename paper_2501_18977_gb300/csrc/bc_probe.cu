@@ -3,6 +3,7 @@
 // the streaming copy bandwidth.
 #include "bc_filter.h"
 #include "bc_launch.h"
+#include "bc_phases.cuh"
 
 namespace {
 
@@ -39,7 +40,44 @@ __global__ void __launch_bounds__(kThreads) gather_probe_kernel(const uint64_t *
     if (lane == 0) sink[((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
 }
 
+// Barrier self-test: every CTA but the last arrives at one grid barrier; the
+// last never does, so the others must give up after `limit` clock cycles and
+// set *err. Nothing spins without a bound.
+__global__ void barrier_selftest_kernel(unsigned int *bar, unsigned long long *err, long long limit) {
+    if (blockIdx.x + 1 == gridDim.x) return;  // the CTA that never arrives
+    bc::grid_barrier(bar, gridDim.x, err, limit);
+}
+
 }  // namespace
+
+extern "C" int blowchoc_barrier_selftest(uint32_t ctas, double seconds, void *stream) {
+    if (ctas < 2 || ctas > 1024 || !(seconds > 0.0) || seconds > 10.0)
+        return bc_set_error(BLOWCHOC_EINVAL, "ctas in 2..1024, seconds in (0, 10]");
+    int dev = 0, rate_khz = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&rate_khz, cudaDevAttrClockRate, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bc_set_error(BLOWCHOC_ECUDA, "no usable CUDA device");
+    if ((int)ctas > sms) return bc_set_error(BLOWCHOC_EINVAL, "more CTAs than SMs");
+    const long long limit = (long long)(seconds * 1e3 * (double)(rate_khz > 0 ? rate_khz : 2000000));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d = nullptr;  // [0] error word, [1] arrivals
+    if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        return bc_set_error(BLOWCHOC_ENOMEM, "self-test words");
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s);
+    unsigned int *bar = reinterpret_cast<unsigned int *>(d + 1);
+    void *args[] = {(void *)&bar, (void *)&d, (void *)&limit};
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void *)barrier_selftest_kernel, dim3(ctas), dim3(32), args, 0, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return bc_set_error(BLOWCHOC_ECUDA, cudaGetErrorString(e));
+    bc_note_launch();
+    if (h[0] != 0) return bc_set_error(BLOWCHOC_ETIMEOUT, "grid barrier wait gave up (as intended)");
+    return BLOWCHOC_OK;
+}
 
 extern "C" int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, uint64_t nreads,
                                      uint64_t seed, uint32_t lanes, uint32_t ctas_per_sm,

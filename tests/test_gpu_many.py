@@ -160,3 +160,50 @@ def test_many_rejects_a_repeated_filter():
     finally:
         batch.close()
         f.close()
+
+
+def test_many_filter_workload_full_size_matches_oracle_digests():
+    """The 256-filter workload at full size, through insert_many and
+    query_many, against the oracle's per-filter digests
+    (tests/golden/many_filters_256.txt, written by make_golden.py many)."""
+    import hashlib
+    import os
+    import torch
+    import paper_2501_18977_gb300 as bc
+    path = os.path.join(os.path.dirname(__file__), "golden", "many_filters_256.txt")
+    rows = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or "|" not in line:
+                continue
+            f = [x.strip() for x in line.split("|")]
+            rows[int(f[0])] = f
+    cfg = workloads.many_filter_config()
+    phi = GOLDEN_RATIO
+    filters, ins, qry, bms, nq = [], [], [], [], []
+    for it in cfg:
+        keys, queries = workloads.many_filter_keys(it)
+        f = bc.Filter(it["M"], 11, 2, bc.COST_EXP, phi, hash_seed=it["key_seed"], batch=it["B"])
+        filters.append(f)
+        dk, dq = to_dev(keys), to_dev(queries)
+        b = torch.zeros(max(1, (len(queries) + 63) // 64), dtype=torch.int64, device="cuda")
+        ins.append((f, dk, len(keys), None))
+        qry.append((f, dq, len(queries), b))
+        bms.append(b)
+        nq.append(len(queries))
+    batch = bc.Batch()
+    try:
+        batch.insert_many(ins)
+        batch.query_many(qry)
+        torch.cuda.synchronize()
+        for it, f, b, n in zip(cfg, filters, bms, nq):
+            row = rows[it["index"]]
+            st = f.stats()
+            assert (st.inserted, st.skipped) == (int(row[4]), int(row[5])), it["index"]
+            assert hashlib.sha256(f.words_host().astype("<u8").tobytes()).hexdigest() == row[6], it["index"]
+            h = b.cpu().numpy().view(np.uint64)[: (n + 63) // 64]
+            assert hashlib.sha256(h.astype("<u8").tobytes()).hexdigest() == row[7], it["index"]
+    finally:
+        batch.close()
+        for f in filters:
+            f.close()

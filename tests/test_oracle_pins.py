@@ -379,3 +379,73 @@ def test_query_bitmap_layout():
     for t in range(40):
         assert hits[t] == ((int(bm[0]) >> t) & 1 == 1)
     assert len(f.query(keys[:0])) == 0
+
+
+# ---------------------------------------------------------------- learned-cost oracle
+
+def test_learned_forward_hand_value():
+    """With W1 = 0 and b1 = 0 the first layer is 0; b2[0] = atanh(1/2) makes
+    h2[0] = 1/2; w3[0] = 2 and b3 = 0.25 give g = 1.25 at every grid point."""
+    from oracle import learned as lr
+    p = np.zeros(lr.NPARAMS)
+    H = lr.H
+    p[3 * H + H * H + 0] = math.atanh(0.5)      # b2[0]
+    p[4 * H + H * H + 0] = 2.0                   # w3[0]
+    p[5 * H + H * H] = 0.25                      # b3
+    g = lr.forward(p, 7)
+    assert g.shape == (513 * 8,)
+    assert np.allclose(g, 1.25, rtol=0, atol=1e-15)
+
+
+def test_learned_backward_matches_finite_differences():
+    from oracle import learned as lr
+    rng = np.random.default_rng(3)
+    k = 5
+    p = rng.normal(0, 0.4, lr.NPARAMS)
+    w = rng.normal(0, 1.0, 513 * (k + 1))
+    w[rng.random(w.shape) < 0.7] = 0.0
+    g = lr.backward(p, k, w)
+    idx = rng.choice(lr.NPARAMS, 60, replace=False)
+    for i in list(idx) + [lr.NPARAMS - 1, 0, 2 * lr.H]:
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (w @ lr.forward(pp, k) - w @ lr.forward(pm, k)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_learned_sampling_limits_and_invariants():
+    """Score weights sum to zero per decision; as tau -> 0 the sampled
+    choices are the greedy (least table cost, lowest index on ties) ones."""
+    from oracle import learned as lr
+    from oracle.oracle import COST_TABLE
+    k, M, c = 6, 16, 3
+    rng = np.random.default_rng(1)
+    table = rng.normal(0, 1, 513 * (k + 1))
+    pre = workloads.uniform_keys(201, 400)
+    keys = workloads.uniform_keys(202, 300)
+    f = _filter(M, k, c, COST_EXP, GOLDEN_RATIO, seed=4, B=1)
+    f.insert(pre)
+    choices, w, _ = lr.sampled_batch(f, keys, table, 1e-9, seed=5)
+    assert abs(w.sum()) < 1e-3 * max(1.0, np.abs(w).sum() * 1e-12)
+    g = _filter(M, k, c, COST_EXP, GOLDEN_RATIO, seed=4, B=1)
+    g.insert(pre)
+    g.set_cost_table(table)
+    greedy = g.insert(keys, batch=len(keys), return_choices=True)
+    # compare where the least table value is unique (tied candidates, e.g. two
+    # choices on the same block, are sampled among; greedy takes the first)
+    k1 = k + 1
+    unique = []
+    for x in keys:
+        vals = [table[L * k1 + a] for L, a in (f.block_terms(b, int(x)) for b in f.candidates(int(x)))]
+        unique.append(sum(1 for v in vals if v == min(vals)) == 1)
+    unique = np.array(unique)
+    assert unique.sum() > 200
+    got = np.where(choices == 255, -1, choices)
+    assert np.array_equal(got[unique], greedy.astype(np.int64)[unique])
+    assert np.array_equal(got == -1, greedy == -1)
+    # a moderate tau draws non-greedy choices too, still with zero-sum weights
+    ch2, w2, _ = lr.sampled_batch(f, keys, table, 1.0, seed=6)
+    assert abs(w2.sum()) < 1e-9 * max(1.0, np.abs(w2).sum())
+    assert (ch2 != np.where(choices == 255, 255, choices)).any()
