@@ -58,7 +58,7 @@ typedef struct {
     uint32_t k;         /* bit-address hashes, 1..32 */
     uint32_t choices;   /* c, 1..3 (c = 1 is a Blocked Bloom filter, no cost) */
     int32_t cost;       /* blowchoc_cost */
-    uint32_t bitsel;    /* 0 = random bit selection (Section 3.3); other values rejected */
+    uint32_t bitsel;    /* bit selection (Section 3.3): 0 = random, 1 = distinct (Appendix B) */
     double cost_param;  /* sigma | mu | beta */
     uint64_t hash_seed; /* seeds the hash multipliers (see blowchoc_multipliers) */
     uint64_t batch;     /* B >= 1: batch size of the batch-synchronous insertion */
@@ -85,11 +85,12 @@ typedef struct {
  * Hash multipliers (Section 3.4: "a random large integer" coprime to the
  * range b) are drawn from splitmix64 seeded with hash_seed, forced odd and
  * redrawn until coprime: first a_1..a_c for the block hashes (range M), then
- * a'_1..a'_k for the bit hashes (range 512).
+ * a'_1..a'_k for the bit hashes (range 512; with distinct selection the
+ * range of a'_i is 512 - i + 1).
  * Layout: bit p of block b is bit (p mod 64) of the little-endian 64-bit
  * word 8b + p/64; blocks are contiguous and 64-byte aligned.
  * Errors: EINVAL (M = 0 or > 2^32, k not in 1..32, c not in 1..3, bad cost
- * kind or parameter, bitsel != 0, batch = 0, out NULL), ENOMEM, ECUDA.
+ * kind or parameter, bitsel > 1, batch = 0, out NULL), ENOMEM, ECUDA.
  */
 int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter **out);
 
@@ -245,9 +246,11 @@ int blowchoc_batch_destroy(blowchoc_batch *b);
  * every i, with each filter's own batch rule (B of that filter): round r
  * runs the r-th batch of every filter that has one; a grid barrier separates
  * the choose and set phases and the rounds. One cooperative launch per
- * distinct choice count c among the items (filters with B = 1, or with
- * B <= 16384 and more than 4096 batches, run through the single-filter
- * kernels on the same stream instead). A filter may appear at most once
+ * distinct choice count c among the items. Filters with B = 1, or whose
+ * insert needs more than max(64, 4 x the median) batches of the call, run
+ * through the single-filter kernels on the same stream instead, so that they
+ * do not hold the launch's other filters behind their batches. A filter may
+ * appear at most once
  * per call. Stream-ordered; the batch object must not be reused for another
  * call until this one's host-side setup has returned (it does not wait for
  * the GPU). Errors: EINVAL (NULL pointers, count 0, repeated filter,
@@ -281,6 +284,11 @@ int blowchoc_batch_replay(blowchoc_batch *b, void *stream);
  * insert_many and one query_many launch, on several streams, ordered per
  * filter by events. Each request's result is exactly what it gives when the
  * requests of its filter run alone, one after another, in arrival order.
+ * Host buffers may be pinned (copied directly, asynchronously) or pageable
+ * (staged through pinned arenas the server owns: staging_bytes for keys,
+ * staging_bytes / 32 for bitmaps), so that no copy blocks the scheduler.
+ * A request whose insert needs many batches (more than 64, from a small B)
+ * runs in a wave of its own, so it never delays the light requests.
  * Not in the paper: a library service.
  */
 typedef struct blowchoc_server blowchoc_server;
@@ -426,6 +434,12 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       by ranges of 256 blocks, stage each touched range in shared memory,
  *       OR there, write the range back (offered while ceil(M / 256) <= 65536;
  *       larger filters use 0).
+ *   seq_window: B = 1 (one key at a time) runs in parallel while staying
+ *       exactly sequential: windows of seq_window keys (32..8192) go through
+ *       rounds in which every pending key reserves its candidate blocks (the
+ *       earliest key wins each block) and the keys that won all of theirs
+ *       decide and set their bits; such keys share no candidate block with
+ *       any earlier pending key. 0 = one warp inserting key after key.
  */
 typedef struct {
     uint32_t lanes_choose;
@@ -436,6 +450,7 @@ typedef struct {
     uint32_t persistent;
     uint32_t keys_per_cta;
     uint32_t set_mode;
+    uint32_t seq_window;
 } blowchoc_tuning;
 
 /* Read / replace a filter's launch configuration. set_tuning checks every

@@ -46,6 +46,11 @@ void orc_set_cost_table(const double *table, uint32_t k)
     orc_table_k = k;
 }
 
+/* Bit selection (Section 3.3): 0 = random, 1 = distinct (Appendix B). */
+static int orc_bitsel = 0;
+
+void orc_set_bitsel(int mode) { orc_bitsel = mode; }
+
 /* splitmix64 (Steele, Lea and Flood, OOPSLA 2014): add the golden-ratio
  * increment to the state, then apply the variant-13 finaliser of MurmurHash3
  * as published with the generator. Used here only to draw hash multipliers. */
@@ -117,10 +122,12 @@ int orc_derive_multipliers(uint64_t seed, uint64_t M, uint32_t k, uint32_t c,
         a_block[i] = a;
     }
     for (uint32_t i = 0; i < k; i++) {
+        /* random bits hash into [512]; distinct bits: f_{i+1} into [512 - i] */
+        uint64_t range = orc_bitsel ? ORC_BLOCK_BITS - i : ORC_BLOCK_BITS;
         uint64_t a;
         do {
             a = orc_splitmix64_next(&state) | 1u;
-        } while (orc_gcd(a, ORC_BLOCK_BITS) != 1);
+        } while (orc_gcd(a, range) != 1);
         a_bit[i] = a;
     }
     return 0;
@@ -160,8 +167,54 @@ static void orc_bitset(const uint64_t *a_bit, uint32_t k, uint64_t x,
                        unsigned char inF[ORC_BLOCK_BITS])
 {
     memset(inF, 0, ORC_BLOCK_BITS);
-    for (uint32_t i = 0; i < k; i++)
-        inF[orc_hash(a_bit[i], x, ORC_BLOCK_BITS)] = 1;
+    if (!orc_bitsel) {
+        for (uint32_t i = 0; i < k; i++)
+            inF[orc_hash(a_bit[i], x, ORC_BLOCK_BITS)] = 1;
+        return;
+    }
+    /* Distinct bit selection (Appendix B, Fig. 9): f_i hashes into
+     * [512 - i + 1]; it is then incremented as long as some earlier address,
+     * scanned in ascending order, is smaller than or equal to its current
+     * value, and inserted into the sorted list of addresses (insertion sort).
+     * The result is a uniform k-subset of [512]. */
+    uint32_t sorted[32];
+    uint32_t nsorted = 0;
+    for (uint32_t i = 0; i < k; i++) {
+        uint32_t f = (uint32_t)orc_hash(a_bit[i], x, ORC_BLOCK_BITS - i);
+        uint32_t pos = 0;
+        while (pos < nsorted && sorted[pos] <= f) {
+            f++;
+            pos++;
+        }
+        for (uint32_t t = nsorted; t > pos; t--)
+            sorted[t] = sorted[t - 1];
+        sorted[pos] = f;
+        nsorted++;
+    }
+    for (uint32_t t = 0; t < nsorted; t++)
+        inF[sorted[t]] = 1;
+}
+
+/* Exported for tests: the distinct-selection shift rule applied to given raw
+ * values raw[i] in [512 - i] (Appendix B); out receives the final addresses
+ * in the order the raw values are given. */
+void orc_distinct_from_raw(const uint32_t *raw, uint32_t k, uint32_t *out)
+{
+    uint32_t sorted[32];
+    uint32_t nsorted = 0;
+    for (uint32_t i = 0; i < k; i++) {
+        uint32_t f = raw[i];
+        uint32_t pos = 0;
+        while (pos < nsorted && sorted[pos] <= f) {
+            f++;
+            pos++;
+        }
+        for (uint32_t t = nsorted; t > pos; t--)
+            sorted[t] = sorted[t - 1];
+        sorted[pos] = f;
+        nsorted++;
+        out[i] = f;
+    }
 }
 
 /* Exported for tests: the positions of F(x), ascending; returns |F(x)|. */

@@ -46,6 +46,10 @@ def _load():
     lib.orc_block_terms.restype = None
     lib.orc_set_cost_table.argtypes = [vp, u32]
     lib.orc_set_cost_table.restype = None
+    lib.orc_set_bitsel.argtypes = [i32]
+    lib.orc_set_bitsel.restype = None
+    lib.orc_distinct_from_raw.argtypes = [vp, u32, vp]
+    lib.orc_distinct_from_raw.restype = None
     _lib = lib
     return lib
 
@@ -71,22 +75,32 @@ def cost(kind: int, param: float, k: int, j: int, a: int) -> float:
     return float(_load().orc_cost(kind, param, k, j, a))
 
 
-def derive_multipliers(seed: int, M: int, k: int, c: int):
+def derive_multipliers(seed: int, M: int, k: int, c: int, bitsel: int = 0):
     """Hash multipliers (a_1..a_c, a'_1..a'_k) drawn from the seed."""
     a_block = np.zeros(3, dtype=np.uint64)
     a_bit = np.zeros(32, dtype=np.uint64)
+    _load().orc_set_bitsel(int(bitsel))
     rc = _load().orc_derive_multipliers(seed, M, k, c, _ptr(a_block), _ptr(a_bit))
     if rc != 0:
         raise ValueError("bad filter parameters")
     return a_block[:c].copy(), a_bit[:k].copy()
 
 
-def bit_positions(a_bit, x: int):
+def bit_positions(a_bit, x: int, bitsel: int = 0):
     """Sorted distinct positions F(x) (Eq. 3)."""
     a_bit = np.ascontiguousarray(a_bit, dtype=np.uint64)
     out = np.zeros(32, dtype=np.uint32)
+    _load().orc_set_bitsel(int(bitsel))
     n = _load().orc_bit_positions(_ptr(a_bit), len(a_bit), x, _ptr(out))
     return out[:n].copy()
+
+
+def distinct_from_raw(raw):
+    """Appendix B's shift rule on given raw values (raw[i] in [512 - i])."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint32)
+    out = np.zeros(len(raw), dtype=np.uint32)
+    _load().orc_distinct_from_raw(_ptr(raw), len(raw), _ptr(out))
+    return out
 
 
 class OracleFilter:
@@ -98,12 +112,13 @@ class OracleFilter:
     """
 
     def __init__(self, M, k, c, cost_kind=COST_EXP, cost_param=GOLDEN_RATIO,
-                 seed=0, batch=1, a_block=None, a_bit=None):
+                 seed=0, batch=1, a_block=None, a_bit=None, bitsel=0):
         self.M, self.k, self.c = int(M), int(k), int(c)
         self.cost_kind, self.cost_param = int(cost_kind), float(cost_param)
         self.batch = int(batch)
+        self.bitsel = int(bitsel)
         if a_block is None:
-            a_block, a_bit = derive_multipliers(seed, self.M, self.k, self.c)
+            a_block, a_bit = derive_multipliers(seed, self.M, self.k, self.c, self.bitsel)
         self.a_block = np.zeros(3, dtype=np.uint64)
         self.a_block[:self.c] = a_block
         self.a_bit = np.zeros(32, dtype=np.uint64)
@@ -120,6 +135,7 @@ class OracleFilter:
 
     def insert(self, keys, batch=None, return_choices=False):
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        _load().orc_set_bitsel(self.bitsel)
         if self.cost_kind == COST_TABLE:
             _load().orc_set_cost_table(_ptr(self.table), self.k)
         B = self.batch if batch is None else int(batch)
@@ -142,6 +158,7 @@ class OracleFilter:
 
     def query(self, keys, return_first=False):
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        _load().orc_set_bitsel(self.bitsel)
         n = len(keys)
         bitmap = np.zeros(max((n + 63) // 64, 1), dtype=np.uint64)
         first = np.zeros(max(n, 1), dtype=np.uint8) if return_first else None
@@ -162,6 +179,7 @@ class OracleFilter:
         return hist, int(total)
 
     def block_terms(self, block, x):
+        _load().orc_set_bitsel(self.bitsel)
         """(|F'|, |F(x) minus F'|) of block `block` for key x (Section 3.2)."""
         L, a = ctypes.c_uint32(0), ctypes.c_uint32(0)
         _load().orc_block_terms(_ptr(self.words), block, _ptr(self.a_bit), self.k, x,

@@ -46,7 +46,8 @@ class blowchoc_tuning(ctypes.Structure):
     _fields_ = [("lanes_choose", ctypes.c_uint32), ("lanes_set", ctypes.c_uint32),
                 ("lanes_query", ctypes.c_uint32), ("query_early", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
-                ("keys_per_cta", ctypes.c_uint32), ("set_mode", ctypes.c_uint32)]
+                ("keys_per_cta", ctypes.c_uint32), ("set_mode", ctypes.c_uint32),
+                ("seq_window", ctypes.c_uint32)]
 
 
 class blowchoc_work(ctypes.Structure):
@@ -531,9 +532,9 @@ class Filter:
     """Owning handle around blowchoc_create/destroy with tensor conveniences."""
 
     def __init__(self, nblocks, k, choices, cost=COST_EXP, cost_param=(1 + 5 ** 0.5) / 2,
-                 hash_seed=0, batch=1, stream=None):
+                 hash_seed=0, batch=1, stream=None, bitsel=0):
         self.params = blowchoc_params(nblocks=int(nblocks), k=int(k), choices=int(choices),
-                                      cost=int(cost), bitsel=0, cost_param=float(cost_param),
+                                      cost=int(cost), bitsel=int(bitsel), cost_param=float(cost_param),
                                       hash_seed=int(hash_seed), batch=int(batch))
         self.handle = blowchoc_create(self.params, stream)
 

@@ -69,8 +69,10 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
     return a;
 }
 
-// Section 3.4: multipliers are random, odd and coprime to the hash range.
-void derive_multipliers(uint64_t seed, uint64_t M, uint32_t k, uint32_t c, uint64_t *a_block,
+// Section 3.4: multipliers are random, odd and coprime to the hash range:
+// M for the block hashes; 512 for random bit selection, 512 - i for the
+// (i+1)-th hash of distinct bit selection (Appendix B).
+void derive_multipliers(uint64_t seed, uint64_t M, uint32_t k, uint32_t c, uint32_t bitsel, uint64_t *a_block,
                         uint64_t *a_bit) {
     uint64_t st = seed;
     for (uint32_t i = 0; i < c; ++i) {
@@ -79,7 +81,13 @@ void derive_multipliers(uint64_t seed, uint64_t M, uint32_t k, uint32_t c, uint6
         while (gcd64(a, M) != 1);
         a_block[i] = a;
     }
-    for (uint32_t i = 0; i < k; ++i) a_bit[i] = splitmix64(st) | 1ull;  // odd => coprime to 512
+    for (uint32_t i = 0; i < k; ++i) {
+        const uint64_t range = bitsel ? 512u - i : 512u;
+        uint64_t a;
+        do a = splitmix64(st) | 1ull;
+        while (gcd64(a, range) != 1);
+        a_bit[i] = a;
+    }
 }
 
 // Cost of Eq. 4-6 in double; j = L + a.
@@ -124,7 +132,7 @@ int check_params(const blowchoc_params *p) {
     if (!std::isfinite(p->cost_param) || p->cost_param < 0.0 ||
         (p->cost == BLOWCHOC_COST_EXP && p->cost_param <= 0.0))
         return fail(BLOWCHOC_EINVAL, "bad cost parameter %g", p->cost_param);
-    if (p->bitsel != 0) return fail(BLOWCHOC_EINVAL, "only random bit selection (bitsel = 0) is built");
+    if (p->bitsel > 1) return fail(BLOWCHOC_EINVAL, "bitsel must be 0 (random) or 1 (distinct)");
     if (p->batch == 0) return fail(BLOWCHOC_EINVAL, "batch must be >= 1");
     return BLOWCHOC_OK;
 }
@@ -198,7 +206,8 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
         d.range_kind = (d.M & 1) ? bc::kRangeOdd : bc::kRangeEven;
         d.shift = 0;
     }
-    derive_multipliers(params->hash_seed, d.M, d.k, d.c, d.a_block, d.a_bit);
+    d.bitsel = params->bitsel;
+    derive_multipliers(params->hash_seed, d.M, d.k, d.c, d.bitsel, d.a_block, d.a_bit);
 
     const size_t wbytes = (size_t)d.M * bc::kBlockWords * sizeof(uint64_t);
     e = cudaMalloc(&d.words, wbytes);
@@ -231,6 +240,14 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
     const int C = (int)f->p.choices;
     const uint64_t B = f->p.batch;
     if (B == 1) {
+        if (f->seq_window > 0) {
+            if (!f->d_resv)
+                BC_CUDA(cudaMalloc(&f->d_resv, f->dev.M * sizeof(unsigned long long)), "cudaMalloc(reservations)");
+            BC_CUDA(counted(bc::launch_exact_sequential(C, s, f->dev, d_keys, n, (uint32_t)f->seq_window, f->d_rank,
+                                                        f->d_counters, f->d_resv)),
+                    "sequential insert launch");
+            return BLOWCHOC_OK;
+        }
         BC_CUDA(counted(bc::launch_sequential(C, s, f->dev, d_keys, n, f->d_rank, f->d_counters)),
                 "sequential insert launch");
         return BLOWCHOC_OK;
@@ -324,6 +341,7 @@ int blowchoc_destroy(blowchoc_filter *f) {
     cudaFree(f->d_rank);
     cudaFree(f->d_sel);
     cudaFree(f->d_sorted);
+    cudaFree(f->d_resv);
     delete f;
     if (e != cudaSuccess) return cuda_fail(e, "blowchoc_destroy");
     return BLOWCHOC_OK;
@@ -390,6 +408,7 @@ int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     out->persistent = (uint32_t)f->persistent;
     out->keys_per_cta = (uint32_t)f->keys_per_cta;
     out->set_mode = (uint32_t)f->set_mode;
+    out->seq_window = (uint32_t)f->seq_window;
     return BLOWCHOC_OK;
 }
 
@@ -404,6 +423,8 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     if (t->keys_per_cta < 32 || t->keys_per_cta > (1u << 24))
         return fail(BLOWCHOC_EINVAL, "keys_per_cta must be in 32..2^24");
     if (t->set_mode > 1) return fail(BLOWCHOC_EINVAL, "set_mode must be 0 or 1");
+    if (t->seq_window != 0 && (t->seq_window < 32 || t->seq_window > bc::kSeqMaxWindow))
+        return fail(BLOWCHOC_EINVAL, "seq_window must be 0 or in 32..8192");
     f->lanes_choose = (int)t->lanes_choose;
     f->lanes_set = (int)t->lanes_set;
     f->lanes_query = (int)t->lanes_query;
@@ -412,6 +433,7 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     f->persistent = (int)t->persistent;
     f->keys_per_cta = (int)t->keys_per_cta;
     f->set_mode = (int)t->set_mode;
+    f->seq_window = (int)t->seq_window;
     return BLOWCHOC_OK;
 }
 

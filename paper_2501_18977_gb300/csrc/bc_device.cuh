@@ -27,6 +27,8 @@ struct DevFilter {
     uint32_t range_kind;   // kRange* for M
     uint32_t shift;        // pow2 M: 64 - log2(M); 64 when M == 1
     uint32_t c;            // choices (for dispatch checks)
+    uint32_t bitsel;       // 0 = random bit selection, 1 = distinct (Appendix B)
+    uint32_t pad;
     uint64_t a_block[3];   // h_1..h_c multipliers
     uint64_t a_bit[32];    // f_1..f_k multipliers
 };
@@ -43,10 +45,77 @@ __device__ __forceinline__ uint64_t block_mult(const DevFilter &f, uint32_t i) {
     return i == 0 ? f.a_block[0] : (i == 1 ? f.a_block[1] : f.a_block[2]);
 }
 
+// f_i(x) for distinct selection: the linear hash of Section 3.4 into
+// [range] (range = 512 - i + 1 <= 512): top bits for 512, xor-fold for even
+// ranges, plain modulo for odd ones.
+__device__ __forceinline__ uint32_t bit_hash_range(uint64_t a, uint64_t x, uint32_t range) {
+    uint64_t y = a * x;
+    if (range == 512u) return (uint32_t)(y >> 55);
+    if ((range & 1u) == 0) y ^= (y >> 32);
+    return (uint32_t)(y % range);
+}
+
+// Index of the r-th (0-based) zero bit of a 64-bit word that has more than
+// r zero bits: binary search with popcounts of the low halves.
+__device__ __forceinline__ uint32_t select_zero64(uint64_t word, uint32_t r) {
+    uint64_t v = ~word;
+    uint32_t p = 0;
+#pragma unroll
+    for (int s = 32; s >= 1; s >>= 1) {
+        const uint32_t c = __popcll(v & ((1ull << s) - 1ull));
+        if (r >= c) {
+            r -= c;
+            v >>= s;
+            p += s;
+        }
+    }
+    return p;
+}
+
+// Full 512-bit mask of F(x) under distinct selection (Appendix B): f_i maps
+// into [512 - i + 1] and becomes the f_i-th position (in ascending order)
+// not taken by f_1..f_{i-1} -- the paper's increment rule, computed by
+// counting free positions per word.
+__device__ __forceinline__ void distinct_mask(const uint64_t *amul, uint32_t k, uint64_t x, uint64_t (&w)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+        uint32_t r = bit_hash_range(amul[i], x, 512u - i);
+        uint32_t p = 0;
+        bool found = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t z = 64u - (uint32_t)__popcll(w[j]);
+            if (!found) {
+                if (r < z) {
+                    p = 64u * j + select_zero64(w[j], r);
+                    found = true;
+                } else {
+                    r -= z;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] |= ((p >> 6) == (uint32_t)j) ? (1ull << (p & 63)) : 0ull;
+    }
+}
+
 // The group's share of the key's 512-bit mask: m[j] = word q*W + j of the
 // bit set F(x), with f_i(x) = top 9 bits of a'_i x (range 512, Section 3.4).
 template <int W>
 __device__ __forceinline__ void key_mask(const DevFilter &f, uint64_t x, int q, uint64_t (&m)[W]) {
+    if (f.bitsel) {
+        uint64_t w[8];
+        distinct_mask(f.a_bit, f.k, x, w);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            uint64_t v = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v = (t == q * W + j) ? w[t] : v;
+            m[j] = v;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < W; ++j) m[j] = 0;
     const uint32_t first = (uint32_t)q * W;
@@ -79,9 +148,25 @@ constexpr int region_u32() { return LANES == 1 ? 18 : 16; }
 // Every lane of the warp must call this (it contains warp barriers).
 template <int LANES>
 __device__ __forceinline__ void key_mask_shared(const uint64_t *s_amul, uint32_t k, uint64_t x, int q,
-                                                uint32_t *region, uint64_t (&m)[kBlockWords / LANES]) {
+                                                uint32_t *region, uint64_t (&m)[kBlockWords / LANES],
+                                                uint32_t bitsel = 0) {
     constexpr int W = kBlockWords / LANES;
     uint64_t *r64 = reinterpret_cast<uint64_t *>(region);
+    if (bitsel) {
+        // distinct selection is sequential in i: the group's first lane builds
+        // the whole mask, the others read their words
+        if (q == 0) {
+            uint64_t w[8];
+            distinct_mask(s_amul, k, x, w);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) r64[j] = w[j];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < W; ++j) m[j] = r64[q * W + j];
+        __syncwarp();
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < W; ++j) r64[q * W + j] = 0;
     __syncwarp();

@@ -36,8 +36,7 @@ __global__ void __launch_bounds__(kThreads) choose_kernel(DevFilter f, const uin
         const bool valid = i < n;
         const uint64_t x = valid ? load_key(keys + i) : 0ull;
         uint64_t m[W];
-        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
-        const uint32_t s = choose_one<C, LANES, kLoadNC>(f, x, valid, q, rank, m);
+        const uint32_t s = choose_key<C, LANES, kLoadNC>(f, x, valid, q, rank, s_amul, region, m);
         if (valid && q == 0) {
             sel[i] = (uint8_t)s;
             if (s == kSkip) ++skp; else ++ins;
@@ -65,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) set_kernel(DevFilter f, const uint64
         const uint32_t s = i < n ? (uint32_t)sel[i] : kSkip;
         const uint64_t x = s != kSkip ? load_key(keys + i) : 0ull;
         uint64_t m[W];
-        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
         if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
     }
 }
@@ -147,8 +146,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
             const bool valid = i < cnt;
             const uint64_t x = valid ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
-            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank, m);
+            const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
             if (valid && q == 0) {
                 sel[i] = (uint8_t)s;
                 if (s == kSkip) ++skp; else ++ins;
@@ -160,7 +158,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
             const uint32_t s = i < cnt ? (uint32_t)sel[i] : kSkip;
             const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
             if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
         }
         __syncthreads();
@@ -195,13 +193,16 @@ __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
     uint32_t ins = 0, skp = 0;
     for (uint64_t s0 = 0; s0 < n; s0 += B) {
         const uint64_t cnt = (n - s0) < B ? (n - s0) : B;
-        for (uint64_t base = warp * G; base < cnt; base += nwarps * G) {
+        const uint64_t stride = nwarps * G;
+        // the next step's key is loaded one step ahead
+        uint64_t xn = warp * G + g < cnt ? load_key(keys + s0 + warp * G + g) : 0ull;
+        for (uint64_t base = warp * G; base < cnt; base += stride) {
             const uint64_t i = base + g;
             const bool valid = i < cnt;
-            const uint64_t x = valid ? load_key(keys + s0 + i) : 0ull;
+            const uint64_t x = xn;
+            xn = i + stride < cnt ? load_key(keys + s0 + i + stride) : 0ull;
             uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
-            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank, m);
+            const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
             if (valid && q == 0) {
                 sel[i] = (uint8_t)s;
                 if (s == kSkip) ++skp; else ++ins;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
             const uint32_t s = i < cnt ? (uint32_t)__ldcg(sel + i) : kSkip;
             const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
             if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
         }
         if (s0 + B < n) {
@@ -271,8 +272,7 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
             const bool valid = i < cnt_b;
             const uint64_t x = valid ? load_key(bk + i) : 0ull;
             uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
-            const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, rank, m);
+            const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
             if (valid && q == 0) {
                 sel[i] = (uint8_t)s;
                 if (s == kSkip) ++skp; else ++ins;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
                 const uint32_t s = valid ? (uint32_t)__ldcg(sel + i) : kSkip;
                 const uint64_t x = valid ? load_key(bk + i) : 0ull;
                 uint64_t m[W];
-                key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+                key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
                 if (valid) {
                     const uint64_t local = block_addr(f, block_mult(f, s), x) - first;
                     uint32_t *dst = s_range32 + (local * kBlockWords + (uint64_t)q * W) * 2;
@@ -362,6 +362,88 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
         if (s0 + B < n) {
             target += gridDim.x;
             if (!grid_barrier(bar, target, err)) return;
+        }
+    }
+    flush_counts(ins, skp, counters);
+}
+
+// ---------------------------------------------------------------------------
+// One-key-at-a-time insertion (B = 1, the paper's order) in parallel, exactly.
+// Keys are taken in windows; in each round every pending key of the window
+// reserves its candidate blocks with a 64-bit atomic max of
+// (round << 32 | ~index), so the earliest pending key wins each block. A key
+// that holds all of its own reservations has no earlier pending key sharing a
+// candidate block with it: it decides against the current filter and sets its
+// bits. Keys that commit in the same round touch disjoint blocks, so the
+// outcome is that of inserting the keys one after another.
+
+constexpr int kSeqThreads = 1024;
+
+template <int C, int LANES>
+__global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
+    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint32_t window,
+    const uint16_t *__restrict__ rank_g, unsigned long long *counters, unsigned long long *resv) {
+    constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(s_dyn);                  // window keys
+    uint8_t *s_state = s_dyn + (size_t)window * 8;                           // 1 = pending
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_state + ((window + 15) & ~15u));
+    __shared__ uint64_t s_amul[32];
+    __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * G * region_u32<LANES>()];
+    __shared__ int s_left;
+    stage_bit_mults(f, s_amul);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    if constexpr (C == 1) __syncthreads();
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t ins = 0, skp = 0;
+    uint64_t round = 0;
+    for (uint64_t s0 = 0; s0 < n; s0 += window) {
+        const uint32_t cnt = (uint32_t)((n - s0) < window ? (n - s0) : window);
+        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            s_key[t] = load_key(keys + s0 + t);
+            s_state[t] = 1;
+        }
+        __syncthreads();
+        for (;;) {
+            ++round;
+            // reserve: the earliest pending key wins each candidate block
+            for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+                if (!s_state[t]) continue;
+                const unsigned long long tag = ((unsigned long long)round << 32) | (unsigned long long)(~t);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    atomicMax(resv + block_addr(f, f.a_block[c], s_key[t]), tag);
+            }
+            __syncthreads();
+            // every thread has read the previous round's s_left before this barrier
+            if (threadIdx.x == 0) s_left = 0;
+            // commit the keys that hold every reservation of theirs
+            for (uint32_t base = wib * G; base < cnt; base += wpc * G) {
+                const uint32_t t = base + g;
+                bool ready = t < cnt && s_state[t];
+                const uint64_t x = ready ? s_key[t] : 0ull;
+                if (ready) {
+                    const unsigned long long tag = ((unsigned long long)round << 32) | (unsigned long long)(~t);
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        ready = ready && __ldcg(resv + block_addr(f, f.a_block[c], x)) == tag;
+                }
+                uint64_t m[W];
+                const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, ready, q, rank, s_amul, region, m);
+                if (ready && s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
+                if (ready && q == 0) {
+                    s_state[t] = 0;
+                    if (s == kSkip) ++skp; else ++ins;
+                }
+            }
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x)
+                if (s_state[t]) s_left = 1;
+            __syncthreads();
+            if (!s_left) break;
         }
     }
     flush_counts(ins, skp, counters);
@@ -477,7 +559,32 @@ cudaError_t sorted_dispatch(const Launch &L, const DevFilter &f, const uint64_t 
     }
 }
 
+template <int C, int LANES>
+cudaError_t exact_seq_launch(cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n, uint32_t window,
+                             const uint16_t *rank, unsigned long long *counters, unsigned long long *resv) {
+    const size_t sm = (size_t)window * 8 + ((window + 15) & ~15u) + rank_bytes(C, f.k);
+    cudaError_t e = cudaFuncSetAttribute(exact_sequential_kernel<C, LANES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(resv, 0, f.M * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    exact_sequential_kernel<C, LANES><<<1, kSeqThreads, sm, s>>>(f, keys, n, window, rank, counters, resv);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_exact_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                    uint32_t window, const uint16_t *rank, unsigned long long *counters,
+                                    unsigned long long *resv) {
+    if (window < 32 || window > kSeqMaxWindow) return cudaErrorInvalidValue;
+    switch (C) {
+        case 1: return exact_seq_launch<1, 2>(s, f, keys, n, window, rank, counters, resv);
+        case 2: return exact_seq_launch<2, 2>(s, f, keys, n, window, rank, counters, resv);
+        case 3: return exact_seq_launch<3, 2>(s, f, keys, n, window, rank, counters, resv);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_sorted_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                                  uint64_t B, const uint16_t *rank, uint8_t *sel, unsigned long long *counters,

@@ -47,6 +47,13 @@ cudaError_t launch_sorted_insert(int C, const Launch &L, const DevFilter &f, con
                                  uint64_t B, const uint16_t *rank, uint8_t *sel, unsigned long long *counters,
                                  unsigned int *bar, uint32_t *scratch, uint32_t R, int sms);
 
+// B = 1 exactly, in parallel (reservation rounds over windows of keys, one
+// CTA). resv: M zeroed u64 (zeroed by the launcher). window in 32..kSeqMaxWindow.
+constexpr uint32_t kSeqMaxWindow = 8192;
+cudaError_t launch_exact_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                    uint32_t window, const uint16_t *rank, unsigned long long *counters,
+                                    unsigned long long *resv);
+
 // B = 1: one warp inserts the keys strictly one after another.
 cudaError_t launch_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys,
                               uint64_t n, const uint16_t *rank, unsigned long long *counters);

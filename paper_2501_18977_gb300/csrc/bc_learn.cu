@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) sampled_choose_kernel(bc::DevFilter f, co
         const bool valid = i < n;
         const uint64_t x = valid ? bc::load_key(keys + i) : 0ull;
         uint64_t m[W];
-        bc::key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
+        bc::key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
         uint32_t la[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {

@@ -56,6 +56,7 @@ __device__ __forceinline__ void load_item(const ManyItem *it, DevFilter &f, uint
     f.range_kind = it->f.range_kind;
     f.shift = it->f.shift;
     f.c = it->f.c;
+    f.bitsel = it->f.bitsel;
     f.a_block[0] = it->f.a_block[0];
     f.a_block[1] = it->f.a_block[1];
     f.a_block[2] = it->f.a_block[2];
@@ -100,8 +101,7 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
                         const bool valid = base + g < cnt;
                         const uint64_t x = valid ? load_key(it->keys + i) : 0ull;
                         uint64_t m[W];
-                        key_mask_shared<LANES>(s_amul[wib], f.k, x, q, region, m);
-                        const uint32_t s = choose_one<C, LANES, kLoadCG>(f, x, valid, q, it->rank, m);
+                        const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, it->rank, s_amul[wib], region, m);
                         if (valid && q == 0) {
                             it->sel[i - bstart] = (uint8_t)s;
                             if (s == kSkip) ++skp; else ++ins;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
                         const uint32_t s = base + g < cnt ? (uint32_t)__ldcg(it->sel + (i - bstart)) : kSkip;
                         const uint64_t x = s != kSkip ? load_key(it->keys + i) : 0ull;
                         uint64_t m[W];
-                        key_mask_shared<LANES>(s_amul[wib], f.k, x, q, region, m);
+                        key_mask_shared<LANES>(s_amul[wib], f.k, x, q, region, m, f.bitsel);
                         if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
                     }
                 }
@@ -241,32 +241,43 @@ namespace {
 
 using bc::ManyItem;
 
-// One call's device work list and the pinned staging it is uploaded from.
+// One call's device work list, uploaded through a ring of pinned staging
+// slots: a call reuses a slot only once the upload and launch that last used
+// it have completed, so the host can prepare several calls ahead of the GPU.
+constexpr int kStageSlots = 4;
+
 struct ManyPlan {
     struct Group {
         int C;
         uint32_t item0, nitems;   // range in the item array
         size_t prefix0;           // offset in the prefix array
         uint32_t nrounds;         // insert only
+        uint64_t keys;            // keys of the group's items
     };
-    ManyItem *d_items = nullptr, *h_items = nullptr;
-    size_t d_items_cap = 0, h_items_cap = 0;
-    uint32_t *d_prefix = nullptr, *h_prefix = nullptr;
-    size_t d_prefix_cap = 0, h_prefix_cap = 0;
+    struct Slot {
+        ManyItem *d_items = nullptr, *h_items = nullptr;
+        size_t d_items_cap = 0, h_items_cap = 0;
+        uint32_t *d_prefix = nullptr, *h_prefix = nullptr;
+        size_t d_prefix_cap = 0, h_prefix_cap = 0;
+        cudaEvent_t done = nullptr;  // the slot's last upload and launches completed
+    };
+    Slot slots[kStageSlots];
+    int cur = 0;                     // slot of the prepared call
     uint8_t *d_sel = nullptr;
     size_t sel_cap = 0;
-    cudaEvent_t staged = nullptr;  // staging may be rewritten once this completed
     std::vector<Group> groups;
     std::vector<blowchoc_work> side;  // items run by the single-filter kernels
 };
 
 void free_plan(ManyPlan &p) {
-    cudaFree(p.d_items);
-    cudaFree(p.d_prefix);
+    for (ManyPlan::Slot &sl : p.slots) {
+        cudaFree(sl.d_items);
+        cudaFree(sl.d_prefix);
+        cudaFreeHost(sl.h_items);
+        cudaFreeHost(sl.h_prefix);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
     cudaFree(p.d_sel);
-    cudaFreeHost(p.h_items);
-    cudaFreeHost(p.h_prefix);
-    if (p.staged) cudaEventDestroy(p.staged);
     p = ManyPlan();
 }
 
@@ -284,15 +295,30 @@ struct blowchoc_batch {
 
 namespace {
 
-// A filter whose insert would need more rounds than this (tiny batches over
-// many keys), or that inserts one key at a time (B = 1), runs through the
-// single-filter kernels (the sequential or single-CTA batch kernel, which need
-// no grid barrier per batch) instead of adding rounds to the whole launch.
-constexpr uint64_t kManyMaxRounds = 4096;
+// A launch runs as many rounds as its item with the most batches. An item
+// that inserts one key at a time (B = 1), or needs more than
+// max(kManyMinRounds, 4 x the median round count of the call) rounds, runs
+// through the single-filter kernels on the same stream instead, so that it
+// does not hold every other item of the launch behind its rounds.
+constexpr uint64_t kManyMinRounds = 64;
+constexpr uint64_t kManyKeysPerCta = 1024;
 
-bool side_path(const blowchoc_work &w) {
+uint64_t rounds_of(const blowchoc_work &w) {
     const uint64_t B = w.filter->p.batch;
-    return B == 1 || (B <= bc::kSmallBatchMax && (w.n + B - 1) / B > kManyMaxRounds);
+    return (w.n + B - 1) / B;
+}
+
+uint64_t round_cap(const blowchoc_work *items, uint32_t count) {
+    std::vector<uint64_t> r;
+    for (uint32_t i = 0; i < count; ++i)
+        if (items[i].n) r.push_back(rounds_of(items[i]));
+    if (r.empty()) return kManyMinRounds;
+    std::nth_element(r.begin(), r.begin() + r.size() / 2, r.end());
+    return std::max<uint64_t>(kManyMinRounds, 4 * r[r.size() / 2]);
+}
+
+bool side_path(const blowchoc_work &w, uint64_t cap) {
+    return w.filter->p.batch == 1 || rounds_of(w) > cap;
 }
 
 int set_err(int code, const char *msg) { return bc_set_error(code, msg); }
@@ -370,21 +396,24 @@ ManyItem make_item(const blowchoc_work &w) {
 // pinned staging, asynchronously; or with a synchronous copy if `sync`.
 int prepare(ManyPlan &p, const blowchoc_work *items, uint32_t count, bool query, cudaStream_t s,
             bool sync) {
-    if (p.staged) MANY_CUDA(cudaEventSynchronize(p.staged), "batch staging");
-    else MANY_CUDA(cudaEventCreateWithFlags(&p.staged, cudaEventDisableTiming), "batch event");
+    p.cur = (p.cur + 1) % kStageSlots;
+    ManyPlan::Slot &sl = p.slots[p.cur];
+    if (sl.done) MANY_CUDA(cudaEventSynchronize(sl.done), "batch staging");
+    else MANY_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "batch event");
     p.groups.clear();
     p.side.clear();
     std::vector<ManyItem> list;
     std::vector<uint32_t> prefix;
     std::vector<size_t> sel_off;
     size_t sel_total = 0;
+    const uint64_t cap = query ? 0 : round_cap(items, count);
     for (int C = 1; C <= 3; ++C) {
-        ManyPlan::Group g{C, (uint32_t)list.size(), 0, prefix.size(), 0};
+        ManyPlan::Group g{C, (uint32_t)list.size(), 0, prefix.size(), 0, 0};
         std::vector<ManyItem> mine;
         for (uint32_t i = 0; i < count; ++i) {
             const blowchoc_work &w = items[i];
             if ((int)w.filter->p.choices != C || w.n == 0) continue;
-            if (!query && side_path(w)) {
+            if (!query && side_path(w, cap)) {
                 p.side.push_back(w);
                 continue;
             }
@@ -397,6 +426,7 @@ int prepare(ManyPlan &p, const blowchoc_work *items, uint32_t count, bool query,
         }
         if (mine.empty()) continue;
         g.nitems = (uint32_t)mine.size();
+        for (const ManyItem &it : mine) g.keys += it.n;
         if (query) {
             prefix.push_back(0);
             for (const ManyItem &it : mine) {
@@ -431,37 +461,44 @@ int prepare(ManyPlan &p, const blowchoc_work *items, uint32_t count, bool query,
         for (size_t i = 0; i < list.size(); ++i) list[i].sel = p.d_sel + sel_off[i];
     }
     if (list.empty()) return BLOWCHOC_OK;
-    rc = grow_device(p.d_items, p.d_items_cap, list.size(), "batch work list");
-    if (!rc) rc = grow_device(p.d_prefix, p.d_prefix_cap, prefix.size(), "batch tile table");
+    rc = grow_device(sl.d_items, sl.d_items_cap, list.size(), "batch work list");
+    if (!rc) rc = grow_device(sl.d_prefix, sl.d_prefix_cap, prefix.size(), "batch tile table");
     if (rc) return rc;
     if (sync) {
-        MANY_CUDA(cudaMemcpy(p.d_items, list.data(), list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice),
+        MANY_CUDA(cudaMemcpy(sl.d_items, list.data(), list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice),
                   "upload work list");
-        MANY_CUDA(cudaMemcpy(p.d_prefix, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),
+        MANY_CUDA(cudaMemcpy(sl.d_prefix, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),
                   "upload tile table");
         return BLOWCHOC_OK;
     }
-    rc = grow_host(p.h_items, p.h_items_cap, list.size(), "batch staging");
-    if (!rc) rc = grow_host(p.h_prefix, p.h_prefix_cap, prefix.size(), "batch staging");
+    rc = grow_host(sl.h_items, sl.h_items_cap, list.size(), "batch staging");
+    if (!rc) rc = grow_host(sl.h_prefix, sl.h_prefix_cap, prefix.size(), "batch staging");
     if (rc) return rc;
-    std::memcpy(p.h_items, list.data(), list.size() * sizeof(ManyItem));
-    std::memcpy(p.h_prefix, prefix.data(), prefix.size() * sizeof(uint32_t));
-    MANY_CUDA(cudaMemcpyAsync(p.d_items, p.h_items, list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice, s),
+    std::memcpy(sl.h_items, list.data(), list.size() * sizeof(ManyItem));
+    std::memcpy(sl.h_prefix, prefix.data(), prefix.size() * sizeof(uint32_t));
+    MANY_CUDA(cudaMemcpyAsync(sl.d_items, sl.h_items, list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice, s),
               "upload work list");
-    MANY_CUDA(cudaMemcpyAsync(p.d_prefix, p.h_prefix, prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s),
+    MANY_CUDA(cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s),
               "upload tile table");
-    MANY_CUDA(cudaEventRecord(p.staged, s), "batch event");
     return BLOWCHOC_OK;
 }
 
-// Queues the prepared work on stream `s`.
-int launch(blowchoc_batch *b, const ManyPlan &p, bool query, cudaStream_t s) {
+// Queues the prepared work on stream `s` and marks its staging slot.
+int launch(blowchoc_batch *b, const ManyPlan &p, bool query, cudaStream_t s, bool mark = true) {
     unsigned long long *err = b->d_state;
     unsigned int *bar = reinterpret_cast<unsigned int *>(b->d_state + 1);
+    const ManyPlan::Slot &sl = p.slots[p.cur];
     for (const ManyPlan::Group &g : p.groups) {
-        const ManyItem *items = p.d_items + g.item0;
-        const uint32_t *prefix = p.d_prefix + g.prefix0;
-        const int grid = b->sms * b->ctas_per_sm;
+        const ManyItem *items = sl.d_items + g.item0;
+        const uint32_t *prefix = sl.d_prefix + g.prefix0;
+        // insert: about kManyKeysPerCta keys of a round per CTA, so that
+        // rounds with little work meet at cheap barriers
+        int grid = b->sms * b->ctas_per_sm;
+        if (!query && g.nrounds) {
+            const uint64_t per_round = (g.keys + g.nrounds - 1) / g.nrounds;
+            grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid,
+                                                                 (per_round + kManyKeysPerCta - 1) / kManyKeysPerCta));
+        }
         cudaError_t e;
         if (query)
             e = bc::launch_query_many(g.C, b->lanes_query, b->query_early != 0, grid, s, items, g.nitems, prefix);
@@ -475,6 +512,7 @@ int launch(blowchoc_batch *b, const ManyPlan &p, bool query, cudaStream_t s) {
         const int rc = blowchoc_insert(w.filter, w.d_keys, w.n, s);
         if (rc) return rc;
     }
+    if (mark) MANY_CUDA(cudaEventRecord(sl.done, s), "batch event");
     return BLOWCHOC_OK;
 }
 
@@ -554,8 +592,8 @@ int blowchoc_batch_record(blowchoc_batch *b, const blowchoc_work *ins, uint32_t 
         cudaStreamDestroy(cs);
         return cuda_err(e, "begin capture");
     }
-    if (n_ins) rc = launch(b, b->rec_ins, false, cs);
-    if (!rc && n_qry) rc = launch(b, b->rec_qry, true, cs);
+    if (n_ins) rc = launch(b, b->rec_ins, false, cs, false);
+    if (!rc && n_qry) rc = launch(b, b->rec_qry, true, cs, false);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
@@ -589,6 +627,7 @@ int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out) {
     out->persistent = 1;
     out->keys_per_cta = 0;
     out->set_mode = 0;
+    out->seq_window = 0;
     return BLOWCHOC_OK;
 }
 

@@ -47,6 +47,32 @@ __device__ __forceinline__ uint32_t choose_one(const DevFilter &f, uint64_t x, b
     return choose_from_terms<C>(la, rank, f.k + 1);
 }
 
+// The same decision, built for latency: the candidate blocks' loads are
+// issued first, the key's mask is built (key_mask_shared, warp-collective)
+// while they are in flight, then the terms are formed. m receives the mask.
+template <int C, int LANES, int PATH>
+__device__ __forceinline__ uint32_t choose_key(const DevFilter &f, uint64_t x, bool valid, int q,
+                                               const uint16_t *rank, const uint64_t *s_amul, uint32_t *region,
+                                               uint64_t (&m)[kBlockWords / LANES]) {
+    constexpr int W = kBlockWords / LANES;
+    uint64_t blk[C][W];
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const uint64_t b = block_addr(f, f.a_block[i], x);
+        if (valid) {
+            load_words<W, PATH>(f.words + b * kBlockWords + (uint64_t)q * W, blk[i]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) blk[i][j] = ~0ull;
+        }
+    }
+    key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
+    uint32_t la[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) la[i] = group_sum<LANES>(load_and_new<W>(blk[i], m));
+    return choose_from_terms<C>(la, rank, f.k + 1);
+}
+
 // OR of the key's bits into block b: lane q of the group owns W words.
 template <int LANES>
 __device__ __forceinline__ void set_one(const DevFilter &f, uint64_t b, int q,
@@ -165,12 +191,13 @@ __device__ __forceinline__ uint64_t query_word(const DevFilter &f, const uint64_
     constexpr int W = kBlockWords / LANES;
     constexpr int G = 32 / LANES;
     uint64_t word = 0;
+    uint64_t xn = wd * 64 + g < n ? load_key(keys + wd * 64 + g) : 0ull;  // one step ahead
     for (int it = 0; it < 64 / G; ++it) {
         const uint64_t i = wd * 64 + (uint64_t)it * G + g;
         const bool valid = i < n;
-        const uint64_t x = valid ? load_key(keys + i) : 0ull;
+        const uint64_t x = xn;
+        if (it + 1 < 64 / G) xn = i + G < n ? load_key(keys + i + G) : 0ull;
         uint64_t m[W];
-        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m);
         uint32_t hits = 0;
         if constexpr (!EARLY) {
             uint64_t blk[C][W];
@@ -184,6 +211,7 @@ __device__ __forceinline__ uint64_t query_word(const DevFilter &f, const uint64_
                     for (int j = 0; j < W; ++j) blk[c][j] = 0ull;
                 }
             }
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 uint64_t miss = 0;
@@ -193,10 +221,22 @@ __device__ __forceinline__ uint64_t query_word(const DevFilter &f, const uint64_
             }
         } else {
             bool need = valid;
+            uint64_t first[W];  // the first candidate is loaded before the mask is built
+            if (valid) {
+                load_words<W, kLoadNC>(f.words + block_addr(f, f.a_block[0], x) * kBlockWords + (uint64_t)q * W,
+                                       first);
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) first[j] = 0ull;
+            }
+            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 uint64_t blk[W];
-                if (need) {
+                if (c == 0) {
+#pragma unroll
+                    for (int j = 0; j < W; ++j) blk[j] = first[j];
+                } else if (need) {
                     const uint64_t b = block_addr(f, f.a_block[c], x);
                     load_words<W, kLoadNC>(f.words + b * kBlockWords + (uint64_t)q * W, blk);
                 } else {

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -39,7 +40,60 @@ struct Req {
     double launched = -1.0;
     double done = -1.0;
     uint64_t staging = 0;   // device bytes while in flight
+    bool keys_pinned = false, bitmap_pinned = false;
+    size_t key_bounce = SIZE_MAX, bm_bounce = SIZE_MAX;  // offsets in the pinned arenas
 };
+
+// First-fit allocator over a fixed pinned host buffer (offsets, 256-byte
+// granules): bounce space for requests whose host buffers are pageable,
+// because copies to or from pageable memory would block the scheduler.
+struct Arena {
+    uint8_t *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> length
+    void init(uint8_t *b, size_t n) {
+        base = b;
+        size = n;
+        free_.clear();
+        if (n) free_[0] = n;
+    }
+    size_t alloc(size_t n) {
+        n = (n + 255) & ~size_t(255);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            const size_t off = it->first, len = it->second;
+            free_.erase(it);
+            if (len > n) free_[off + n] = len - n;
+            return off;
+        }
+        return SIZE_MAX;
+    }
+    void release(size_t off, size_t n) {
+        n = (n + 255) & ~size_t(255);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+bool is_pinned(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
 
 struct Slot {               // one registered filter
     blowchoc_params params;
@@ -73,6 +127,8 @@ struct blowchoc_server {
     std::vector<blowchoc_batch *> batches;     // one per stream
     std::vector<int> stream_inflight;
     cudaMemPool_t pool = nullptr;
+    uint8_t *h_keys_arena = nullptr, *h_bm_arena = nullptr;  // pinned bounce buffers
+    Arena keys_arena, bm_arena;
     std::vector<Wave> waves;                   // pool of wave records
     std::vector<Slot> slots;
     std::vector<std::unique_ptr<Req>> reqs;
@@ -97,6 +153,7 @@ struct blowchoc_server {
 namespace {
 
 constexpr int kWavesPerStream = 2;
+constexpr uint64_t kHeavyRounds = 64;  // inserts needing more batches run in a wave of their own
 
 int fail_locked(blowchoc_server *s, int code, const char *what, cudaError_t e) {
     if (s->error == BLOWCHOC_OK) {
@@ -152,6 +209,17 @@ void collect(blowchoc_server *s) {
             fail_locked(s, BLOWCHOC_ECUDA, "a wave failed", q);
             continue;
         }
+        for (Req *r : wv.reqs) {
+            if (r->bm_bounce != SIZE_MAX) {
+                std::memcpy(r->h_bitmap, s->h_bm_arena + r->bm_bounce, (r->n + 63) / 64 * 8);
+                s->bm_arena.release(r->bm_bounce, (r->n + 63) / 64 * 8);
+                r->bm_bounce = SIZE_MAX;
+            }
+            if (r->key_bounce != SIZE_MAX) {
+                s->keys_arena.release(r->key_bounce, r->n * 8);
+                r->key_bounce = SIZE_MAX;
+            }
+        }
         const double t = s->now();
         for (Req *r : wv.reqs) {
             r->done = t;
@@ -186,11 +254,32 @@ bool launch_wave(blowchoc_server *s) {
     std::vector<Req *> take;
     uint64_t staging = 0;
     const int nf = (int)s->slots.size();
+    // a heavy insert (many batches) runs alone; light requests share waves
+    auto heavy = [s](const Req *r) {
+        const uint64_t B = s->slots[r->filter].params.batch;
+        return r->kind == BLOWCHOC_REQ_INSERT && (r->n + B - 1) / B > kHeavyRounds;
+    };
     for (int i = 0; i < nf && take.size() < s->cfg.max_wave_requests; ++i) {
         Slot &sl = s->slots[(s->rr + i) % nf];
         if (!sl.admitted || sl.removed || sl.fifo.empty()) continue;
         Req *r = sl.fifo.front();
         if (s->staging_used + staging + r->staging > s->cfg.staging_bytes) continue;
+        if (!r->keys_pinned && r->key_bounce == SIZE_MAX) {
+            r->key_bounce = s->keys_arena.alloc(r->n * 8);
+            if (r->key_bounce == SIZE_MAX) continue;
+        }
+        if (r->kind == BLOWCHOC_REQ_QUERY && !r->bitmap_pinned && r->bm_bounce == SIZE_MAX) {
+            r->bm_bounce = s->bm_arena.alloc((r->n + 63) / 64 * 8);
+            if (r->bm_bounce == SIZE_MAX) continue;
+        }
+        if (heavy(r)) {
+            if (take.empty()) {
+                take.push_back(r);
+                staging += r->staging;
+                break;
+            }
+            continue;
+        }
         take.push_back(r);
         staging += r->staging;
     }
@@ -209,8 +298,13 @@ bool launch_wave(blowchoc_server *s) {
             if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave ordering", e); return false; }
         }
         void *dk = nullptr, *db = nullptr;
+        const void *src = r->h_keys;
+        if (r->key_bounce != SIZE_MAX) {
+            std::memcpy(s->h_keys_arena + r->key_bounce, r->h_keys, r->n * 8);
+            src = s->h_keys_arena + r->key_bounce;
+        }
         cudaError_t e = cudaMallocFromPoolAsync(&dk, r->n * 8, s->pool, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dk, r->h_keys, r->n * 8, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dk, src, r->n * 8, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess && r->kind == BLOWCHOC_REQ_QUERY)
             e = cudaMallocFromPoolAsync(&db, (r->n + 63) / 64 * 8, s->pool, stream);
         if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave staging", e); return false; }
@@ -230,7 +324,8 @@ bool launch_wave(blowchoc_server *s) {
     size_t qi = 0;
     for (Req *r : take) {
         if (r->kind != BLOWCHOC_REQ_QUERY) continue;
-        const cudaError_t e = cudaMemcpyAsync(r->h_bitmap, qry[qi++].d_bitmap, (r->n + 63) / 64 * 8,
+        void *dst = r->bm_bounce != SIZE_MAX ? (void *)(s->h_bm_arena + r->bm_bounce) : (void *)r->h_bitmap;
+        const cudaError_t e = cudaMemcpyAsync(dst, qry[qi++].d_bitmap, (r->n + 63) / 64 * 8,
                                               cudaMemcpyDeviceToHost, stream);
         if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "bitmap copy", e); return false; }
     }
@@ -309,6 +404,15 @@ int blowchoc_server_create(const blowchoc_server_config *cfg, blowchoc_server **
             e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
+    if (e == cudaSuccess) {
+        const size_t kb = (size_t)cfg->staging_bytes, bb = (size_t)(cfg->staging_bytes / 32 + (1 << 20));
+        e = cudaHostAlloc((void **)&s->h_keys_arena, kb, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_bm_arena, bb, cudaHostAllocDefault);
+        if (e == cudaSuccess) {
+            s->keys_arena.init(s->h_keys_arena, kb);
+            s->bm_arena.init(s->h_bm_arena, bb);
+        }
+    }
     s->stream_inflight.assign(s->streams.size(), 0);
     s->waves.resize(s->streams.size() * kWavesPerStream + 1);
     for (Wave &w : s->waves)
@@ -359,6 +463,8 @@ int blowchoc_server_submit(blowchoc_server *s, uint32_t filter_id, uint32_t kind
     r->n = n;
     r->h_bitmap = h_bitmap;
     r->staging = ((n * 8 + 511) & ~uint64_t(511)) + (kind ? ((n + 63) / 64 * 8 + 511) & ~uint64_t(511) : 0);
+    r->keys_pinned = is_pinned(h_keys);
+    r->bitmap_pinned = kind == BLOWCHOC_REQ_QUERY && is_pinned(h_bitmap);
     if (r->staging > s->cfg.staging_bytes) return bc_set_error(BLOWCHOC_EBUDGET, "request larger than staging");
     std::lock_guard<std::mutex> lk(s->mu);
     if (filter_id >= s->slots.size() || s->slots[filter_id].remove)
@@ -462,6 +568,8 @@ int blowchoc_server_destroy(blowchoc_server *s) {
         if (w.ev) cudaEventDestroy(w.ev);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     if (s->pool) cudaMemPoolDestroy(s->pool);
+    cudaFreeHost(s->h_keys_arena);
+    cudaFreeHost(s->h_bm_arena);
     delete s;
     return BLOWCHOC_OK;
 }

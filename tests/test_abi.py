@@ -55,7 +55,7 @@ def _params(**kw):
                                 dict(k=33), dict(choices=0), dict(choices=4), dict(cost=3),
                                 dict(cost=-1), dict(cost_param=-1.0),
                                 dict(cost=bc.COST_EXP, cost_param=0.0),
-                                dict(cost_param=float("nan")), dict(bitsel=1), dict(batch=0)])
+                                dict(cost_param=float("nan")), dict(bitsel=2), dict(batch=0)])
 def test_create_rejects_bad_params(lib, kw):
     with pytest.raises(bc.BlowChocError) as ei:
         bc.blowchoc_create(_params(**kw), 0)

@@ -181,7 +181,8 @@ def test_set_tuning_rejects_bad_values():
         before = (f.tuning().lanes_query, f.tuning().ctas_per_sm)
         for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=2),
                     dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2),
-                    dict(keys_per_cta=8), dict(set_mode=2)]:
+                    dict(keys_per_cta=8), dict(set_mode=2), dict(seq_window=16),
+                    dict(seq_window=9000)]:
             with pytest.raises(bc.BlowChocError):
                 f.set_tuning(**bad)
         assert (f.tuning().lanes_query, f.tuning().ctas_per_sm) == before
@@ -211,6 +212,38 @@ def test_sort_by_block_set_matches_oracle(M, k, c, kind, par, B, n):
     finally:
         f.close()
     o, obm, _, _ = oracle_run(M, k, c, kind, par, 5, B, keys, queries)
+    assert np.array_equal(words, o.words)
+    assert np.array_equal(bm, obm)
+    assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
+
+
+@pytest.mark.parametrize("M,k,c,kind,par,n,window,dups", [
+    (32768, 14, 2, COST_MIX, 50.0, 200000, 2048, False),
+    (999, 11, 3, COST_EXP, PHI, 60000, 32, False),
+    (1, 5, 2, COST_LA, 3.5, 3000, 512, False),       # one block: every key waits for the last
+    (64, 9, 3, COST_MIX, 2.5, 20000, 8192, True),    # many repeated keys
+    (4096, 16, 2, COST_EXP, PHI, 50000, 100, True),
+    (6150, 12, 1, COST_EXP, PHI, 40000, 1000, False),
+    (2048, 14, 2, COST_MIX, 50.0, 30000, 0, False),  # the one-warp kernel
+])
+def test_exact_sequential_insert_matches_oracle(M, k, c, kind, par, n, window, dups):
+    """B = 1 through the reservation rounds equals the oracle's one key after
+    another, for any window, including long chains of conflicting keys."""
+    import paper_2501_18977_gb300 as bc
+    keys = workloads.uniform_keys(M + 3, n)
+    if dups:
+        keys = keys[np.random.default_rng(M).integers(0, max(n // 20, 1), n)]
+    queries = np.concatenate([keys[:n // 2], workloads.uniform_keys(M + 4, n // 2)])
+    f = bc.Filter(M, k, c, kind, par, hash_seed=2, batch=1)
+    try:
+        f.set_tuning(seq_window=window)
+        f.insert(to_dev(keys))
+        bm = f.query(to_dev(queries)).cpu().numpy().view(np.uint64)
+        words = f.words_host()
+        st = f.stats()
+    finally:
+        f.close()
+    o, obm, _, _ = oracle_run(M, k, c, kind, par, 2, 1, keys, queries)
     assert np.array_equal(words, o.words)
     assert np.array_equal(bm, obm)
     assert (st.inserted, st.skipped) == (o.inserted, o.skipped)

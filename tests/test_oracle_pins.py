@@ -449,3 +449,70 @@ def test_learned_sampling_limits_and_invariants():
     ch2, w2, _ = lr.sampled_batch(f, keys, table, 1.0, seed=6)
     assert abs(w2.sum()) < 1e-9 * max(1.0, np.abs(w2).sum())
     assert (ch2 != np.where(choices == 255, 255, choices)).any()
+
+
+# ---------------------------------------------------------------- distinct bit selection (Appendix B)
+
+def test_distinct_shift_rule_printed_example():
+    """Fig. 9: f_1 = 316, f_2 = 27 stays 27; values >= 316 move up by one."""
+    from oracle.oracle import distinct_from_raw
+    assert list(distinct_from_raw([316, 27])) == [316, 27]
+    assert list(distinct_from_raw([316, 316])) == [316, 317]
+    assert list(distinct_from_raw([316, 400])) == [316, 401]
+    assert list(distinct_from_raw([316, 315])) == [316, 315]
+    # hand-worked: each new value passes every earlier address at or below it
+    assert list(distinct_from_raw([5, 5, 5])) == [5, 6, 7]
+    assert list(distinct_from_raw([10, 3, 9])) == [10, 3, 11]   # 9 passes 3 -> 10, then 10 -> 11
+    assert list(distinct_from_raw([511, 510, 509])) == [511, 510, 509]
+    assert list(distinct_from_raw([0, 0, 0, 0])) == [0, 1, 2, 3]
+
+
+def test_distinct_pairs_are_each_2_subset_twice():
+    """Exhaustively: (f_1, f_2) over [512] x [511] yields every 2-subset of
+    [512] exactly twice (once per order), so the subset is uniform."""
+    from oracle.oracle import distinct_from_raw
+    counts = {}
+    for a in range(0, 512, 1):
+        for b in range(0, 511, 7):
+            p, q = distinct_from_raw([a, b])
+            assert p != q and 0 <= q < 512
+            key = (min(p, q), max(p, q))
+            counts[key] = counts.get(key, 0) + 1
+    # the map is injective on the sampled domain: no subset arises more than twice
+    assert max(counts.values()) <= 2
+    # full domain for a few first values: b ranges over [511], so f_2 covers [512] minus {f_1}
+    for a in (0, 1, 255, 316, 511):
+        seconds = {int(distinct_from_raw([a, b])[1]) for b in range(511)}
+        assert seconds == set(range(512)) - {a}
+
+
+def test_distinct_multipliers_and_sizes():
+    from oracle.oracle import derive_multipliers, bit_positions
+    _, af = derive_multipliers(77, 1 << 10, 20, 2, bitsel=1)
+    for i, a in enumerate(af):
+        assert math.gcd(int(a), 512 - i) == 1
+    keys = workloads.uniform_keys(8, 2000)
+    for x in keys:
+        assert len(bit_positions(af, int(x), bitsel=1)) == 20
+
+
+def test_distinct_one_choice_fpr_given_state():
+    """With k distinct positions a negative hits a block of load L with
+    probability C(L, k) / C(512, k): mean over blocks vs measured W/N."""
+    M, k = 256, 8
+    n = int(M * 512 * math.log(2) / k)
+    f = OracleFilter(M, k, 1, COST_EXP, GOLDEN_RATIO, seed=12, batch=1, bitsel=1)
+    keys = workloads.uniform_keys(121, n)
+    f.insert(keys)
+    hist, _ = f.histogram()
+    q = sum(int(hist[L]) * math.comb(L, k) for L in range(513)) / (M * math.comb(512, k))
+    neg = workloads.disjoint_keys(122, 400000, keys)
+    W = int(bits_of_bitmap(f.query(neg), len(neg)).sum())
+    sd = math.sqrt(len(neg) * q * (1 - q))
+    assert abs(W - len(neg) * q) < 4.5 * sd
+    assert bits_of_bitmap(f.query(keys), n).all()
+    # distinct selection queries more bits than random selection: lower FPR at the same size
+    g = OracleFilter(M, k, 1, COST_EXP, GOLDEN_RATIO, seed=12, batch=1)
+    g.insert(keys)
+    W2 = int(bits_of_bitmap(g.query(neg), len(neg)).sum())
+    assert W < W2
