@@ -389,7 +389,10 @@ def run_serve(args):
            "closed_loop": {"p50_ms": round(closed_st.p50_latency_s * 1e3, 3),
                            "p99_ms": round(closed_st.p99_latency_s * 1e3, 3),
                            "waves": int(closed_st.waves),
-                           "mean_wave_requests": round(closed_st.mean_wave_requests, 2)},
+                           "mean_wave_requests": round(closed_st.mean_wave_requests, 2),
+                           "mean_wave_gpu_ms": round(closed_st.mean_wave_gpu_ms, 3),
+                           "launch_host_s": round(closed_st.launch_host_s, 3),
+                           "span_s": round(closed_span, 3)},
            "poisson": loads, "identical_to_plain_results": bool(same),
            "timing": "host steady clock (server) and wall clock (plain); keys from pinned host memory"}
     print(json.dumps(out))

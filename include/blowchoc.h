@@ -192,6 +192,17 @@ int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit)
 int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs);
 
 /*
+ * blowchoc_l2_residency -- keep part of the filter's words resident in L2
+ * for the kernels later queued on `stream` (a created stream, not NULL):
+ * sets aside fraction x the device's maximum persisting L2 for this process
+ * (a limit of the CUDA context, which ends with it) and gives `stream` an
+ * access-policy window over the words with persisting hits. fraction = 0
+ * removes the window and releases persisting lines. Never changes results.
+ * Errors: EINVAL (fraction outside [0, 1], NULL stream), ECUDA.
+ */
+int blowchoc_l2_residency(blowchoc_filter *f, double fraction, void *stream);
+
+/*
  * blowchoc_read_words / blowchoc_write_words -- copy filter words
  * [first, first + count) to or from HOST memory (checkpoint and restore: a
  * filter is fully determined by its parameters and its words). Both run on
@@ -312,6 +323,8 @@ typedef struct {
     double mean_wave_requests;
     uint64_t max_filter_bytes_used;  /* high-water mark of admitted filter memory */
     uint32_t filters_admitted, filters_pending;
+    double mean_wave_gpu_ms;     /* stream time from a wave's first copy to its completion */
+    double launch_host_s;        /* scheduler time spent building and queueing waves */
 } blowchoc_server_summary;
 
 /* Create a server on the current device (its thread starts at
@@ -417,7 +430,9 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *   lanes_choose, lanes_set, lanes_query: lanes of a warp that share one key
  *       (1, 2, 4 or 8); each lane owns 8/lanes words of every 512-bit block.
  *   query_early: 1 = load candidate i+1 only if the key was not found in
- *       candidates 1..i (fewer block reads for members); 0 = load all first.
+ *       candidates 1..i (fewer block reads for members); 0 = load all first;
+ *       2 = load the first two up front, later ones only while not found
+ *       (three choices; two choices treat 2 as 1).
  *   ctas_per_sm: grid size of the grid-wide kernels, in CTAs per SM (1..16;
  *       the persistent insert caps it at what is co-resident).
  *   persistent: 1 = an insert of batches above 2048 keys runs as one

@@ -66,7 +66,8 @@ class blowchoc_server_summary(ctypes.Structure):
                 ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
                 ("max_latency_s", ctypes.c_double), ("mean_wave_requests", ctypes.c_double),
                 ("max_filter_bytes_used", ctypes.c_uint64), ("filters_admitted", ctypes.c_uint32),
-                ("filters_pending", ctypes.c_uint32)]
+                ("filters_pending", ctypes.c_uint32), ("mean_wave_gpu_ms", ctypes.c_double),
+                ("launch_host_s", ctypes.c_double)]
 
 
 REQ_INSERT, REQ_QUERY = 0, 1
@@ -86,6 +87,7 @@ _SIGS = {
     "blowchoc_write_words": ([_VP, _U64, _U64, _VP], _I),
     "blowchoc_clear": ([_VP, _VP], _I),
     "blowchoc_set_cost_table": ([_VP, _VP], _I),
+    "blowchoc_l2_residency": ([_VP, ctypes.c_double, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
     "blowchoc_batch_create": ([ctypes.POINTER(_VP)], _I),
@@ -236,6 +238,10 @@ def blowchoc_set_cost_table(f, costs):
     import numpy as np
     c = np.ascontiguousarray(costs, dtype=np.float64)
     _check(load_library().blowchoc_set_cost_table(f, c.ctypes.data))
+
+
+def blowchoc_l2_residency(f, fraction, stream):
+    _check(load_library().blowchoc_l2_residency(f, float(fraction), _stream(stream)))
 
 
 def blowchoc_clear(f, stream=None):
@@ -584,6 +590,9 @@ class Filter:
 
     def set_cost_table(self, costs):
         blowchoc_set_cost_table(self.handle, costs)
+
+    def l2_residency(self, fraction, stream):
+        blowchoc_l2_residency(self.handle, fraction, stream)
 
     def tuning(self):
         return blowchoc_get_tuning(self.handle)

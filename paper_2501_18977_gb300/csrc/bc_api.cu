@@ -398,6 +398,37 @@ int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs) {
     return BLOWCHOC_OK;
 }
 
+int blowchoc_l2_residency(blowchoc_filter *f, double fraction, void *stream) {
+    if (!f || !(fraction >= 0.0) || fraction > 1.0) return fail(BLOWCHOC_EINVAL, "fraction must be in [0, 1]");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) return fail(BLOWCHOC_EINVAL, "a created stream is required (not the legacy default stream)");
+    int max_persist = 0, max_window = 0;
+    BC_CUDA(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, f->device), "L2 attribute");
+    BC_CUDA(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, f->device), "L2 attribute");
+    cudaStreamAttrValue attr;
+    std::memset(&attr, 0, sizeof attr);
+    const size_t bytes = (size_t)f->dev.M * bc::kBlockWords * sizeof(uint64_t);
+    if (fraction > 0.0 && max_persist > 0 && max_window > 0) {
+        const size_t set_aside = (size_t)(fraction * (double)max_persist);
+        BC_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, set_aside), "persisting L2 limit");
+        const size_t window = std::min(bytes, (size_t)max_window);
+        attr.accessPolicyWindow.base_ptr = f->dev.words;
+        attr.accessPolicyWindow.num_bytes = window;
+        attr.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)set_aside / (double)window);
+        attr.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    } else {
+        attr.accessPolicyWindow.base_ptr = f->dev.words;
+        attr.accessPolicyWindow.num_bytes = 0;
+        attr.accessPolicyWindow.hitRatio = 0.0f;
+        attr.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+        attr.accessPolicyWindow.missProp = cudaAccessPropertyNormal;
+    }
+    BC_CUDA(cudaStreamSetAttribute(s, cudaStreamAttributeAccessPolicyWindow, &attr), "access policy window");
+    if (fraction == 0.0) BC_CUDA(cudaCtxResetPersistingL2Cache(), "reset persisting L2");
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     if (!f || !out) return fail(BLOWCHOC_EINVAL, "NULL argument");
     out->lanes_choose = (uint32_t)f->lanes_choose;
@@ -417,7 +448,7 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     auto lanes_ok = [](uint32_t l) { return l == 1 || l == 2 || l == 4 || l == 8; };
     if (!lanes_ok(t->lanes_choose) || !lanes_ok(t->lanes_set) || !lanes_ok(t->lanes_query))
         return fail(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
-    if (t->query_early > 1) return fail(BLOWCHOC_EINVAL, "query_early must be 0 or 1");
+    if (t->query_early > 2) return fail(BLOWCHOC_EINVAL, "query_early must be 0, 1 or 2");
     if (t->ctas_per_sm < 1 || t->ctas_per_sm > 16) return fail(BLOWCHOC_EINVAL, "ctas_per_sm must be in 1..16");
     if (t->persistent > 1) return fail(BLOWCHOC_EINVAL, "persistent must be 0 or 1");
     if (t->keys_per_cta < 32 || t->keys_per_cta > (1u << 24))

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
     }
 }
 
-template <int C, int LANES, bool EARLY>
+template <int C, int LANES, int MODE>
 __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__restrict__ items, uint32_t nitems,
                                                               const uint32_t *__restrict__ prefix) {
     constexpr int G = 32 / LANES;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__
             cur = fi;
         }
         const uint64_t wd = t - __ldg(prefix + fi);
-        const uint64_t word = query_word<C, LANES, EARLY>(f, it->keys, it->n, wd, s_amul[wib], region, q, g);
+        const uint64_t word = query_word<C, LANES, MODE>(f, it->keys, it->n, wd, s_amul[wib], region, q, g);
         if (lane == 0) it->bitmap[wd] = word;
     }
 }
@@ -192,14 +192,14 @@ cudaError_t insert_many_dispatch(int lanes, int grid, cudaStream_t s, const Many
     }
 }
 
-template <int C, bool EARLY>
+template <int C, int MODE>
 cudaError_t query_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
                                 const uint32_t *prefix) {
     switch (lanes) {
-        case 1: query_many_kernel<C, 1, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
-        case 2: query_many_kernel<C, 2, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
-        case 4: query_many_kernel<C, 4, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
-        case 8: query_many_kernel<C, 8, EARLY><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 1: query_many_kernel<C, 1, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 2: query_many_kernel<C, 2, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 4: query_many_kernel<C, 4, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 8: query_many_kernel<C, 8, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -221,11 +221,11 @@ cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const
 cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
                               uint32_t nitems, const uint32_t *prefix) {
     switch (C) {
-        case 1: return query_many_dispatch<1, false>(lanes, grid, s, items, nitems, prefix);
-        case 2: return early ? query_many_dispatch<2, true>(lanes, grid, s, items, nitems, prefix)
-                             : query_many_dispatch<2, false>(lanes, grid, s, items, nitems, prefix);
-        case 3: return early ? query_many_dispatch<3, true>(lanes, grid, s, items, nitems, prefix)
-                             : query_many_dispatch<3, false>(lanes, grid, s, items, nitems, prefix);
+        case 1: return query_many_dispatch<1, 0>(lanes, grid, s, items, nitems, prefix);
+        case 2: return early ? query_many_dispatch<2, 1>(lanes, grid, s, items, nitems, prefix)
+                             : query_many_dispatch<2, 0>(lanes, grid, s, items, nitems, prefix);
+        case 3: return early ? query_many_dispatch<3, 1>(lanes, grid, s, items, nitems, prefix)
+                             : query_many_dispatch<3, 0>(lanes, grid, s, items, nitems, prefix);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -260,11 +260,13 @@ struct ManyPlan {
         uint32_t *d_prefix = nullptr, *h_prefix = nullptr;
         size_t d_prefix_cap = 0, h_prefix_cap = 0;
         cudaEvent_t done = nullptr;  // the slot's last upload and launches completed
+        cudaStream_t last = nullptr;  // stream of the slot's last use
     };
     Slot slots[kStageSlots];
     int cur = 0;                     // slot of the prepared call
     uint8_t *d_sel = nullptr;
     size_t sel_cap = 0;
+    cudaStream_t sel_last = nullptr;
     std::vector<Group> groups;
     std::vector<blowchoc_work> side;  // items run by the single-filter kernels
 };
@@ -335,16 +337,32 @@ int cuda_err(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_err(e_, what);    \
     } while (0)
 
+// Grows a device buffer with stream-ordered allocation: the old buffer is
+// released after the work already queued on `last` (its last user), the new
+// one is allocated on `s`. No device-wide synchronisation.
 template <typename T>
-int grow_device(T *&ptr, size_t &cap, size_t need, const char *what) {
-    if (need <= cap) return BLOWCHOC_OK;
-    MANY_CUDA(cudaDeviceSynchronize(), what);  // earlier launches may still read the old buffer
-    cudaFree(ptr);
+int grow_device(T *&ptr, size_t &cap, size_t need, cudaStream_t s, cudaStream_t &last, const char *what) {
+    if (need <= cap) {
+        last = s;
+        return BLOWCHOC_OK;
+    }
+    if (ptr) {
+        if (last != s) {
+            // order the release after the last user's work, seen from `s`
+            cudaEvent_t ev;
+            MANY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), what);
+            MANY_CUDA(cudaEventRecord(ev, last), what);
+            MANY_CUDA(cudaStreamWaitEvent(s, ev, 0), what);
+            cudaEventDestroy(ev);
+        }
+        MANY_CUDA(cudaFreeAsync(ptr, s), what);
+    }
     ptr = nullptr;
     const size_t n = std::max(need, cap * 2);
     cap = 0;
-    MANY_CUDA(cudaMalloc((void **)&ptr, n * sizeof(T)), what);
+    MANY_CUDA(cudaMallocAsync((void **)&ptr, n * sizeof(T), s), what);
     cap = n;
+    last = s;
     return BLOWCHOC_OK;
 }
 
@@ -456,15 +474,18 @@ int prepare(ManyPlan &p, const blowchoc_work *items, uint32_t count, bool query,
     }
     int rc = BLOWCHOC_OK;
     if (!query && sel_total) {
-        rc = grow_device(p.d_sel, p.sel_cap, sel_total, "batch choice scratch");
+        rc = grow_device(p.d_sel, p.sel_cap, sel_total, s, p.sel_last, "batch choice scratch");
         if (rc) return rc;
         for (size_t i = 0; i < list.size(); ++i) list[i].sel = p.d_sel + sel_off[i];
     }
     if (list.empty()) return BLOWCHOC_OK;
-    rc = grow_device(sl.d_items, sl.d_items_cap, list.size(), "batch work list");
-    if (!rc) rc = grow_device(sl.d_prefix, sl.d_prefix_cap, prefix.size(), "batch tile table");
+    cudaStream_t last_items = sl.last, last_prefix = sl.last;
+    rc = grow_device(sl.d_items, sl.d_items_cap, list.size(), s, last_items, "batch work list");
+    if (!rc) rc = grow_device(sl.d_prefix, sl.d_prefix_cap, prefix.size(), s, last_prefix, "batch tile table");
+    sl.last = s;
     if (rc) return rc;
     if (sync) {
+        MANY_CUDA(cudaStreamSynchronize(s), "batch work list");
         MANY_CUDA(cudaMemcpy(sl.d_items, list.data(), list.size() * sizeof(ManyItem), cudaMemcpyHostToDevice),
                   "upload work list");
         MANY_CUDA(cudaMemcpy(sl.d_prefix, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),

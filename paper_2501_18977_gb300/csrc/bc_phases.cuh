@@ -181,15 +181,18 @@ __device__ __forceinline__ uint32_t compress_groups(uint32_t v) {
 // returns their bitmap word. Per key, a group of LANES lanes builds the key's
 // mask once (key_mask_shared), then tests the candidate blocks: each lane
 // checks its W words for F(x) & ~block == 0, a ballot per candidate ANDs the
-// lanes of each group, and the candidates OR. EARLY = false issues all C
-// block loads before any test; EARLY = true loads candidate i+1 only for
-// groups whose key was not found in candidates 1..i. Warp-collective.
-template <int C, int LANES, bool EARLY>
+// lanes of each group, and the candidates OR. MODE 0 issues all C block
+// loads before any test; MODE 1 loads candidate i+1 only for groups whose key
+// was not found in candidates 1..i; MODE 2 loads the first two candidates up
+// front and the others only while not found. The first loads are issued
+// before the mask is built. Warp-collective.
+template <int C, int LANES, int MODE>
 __device__ __forceinline__ uint64_t query_word(const DevFilter &f, const uint64_t *__restrict__ keys,
                                                uint64_t n, uint64_t wd, const uint64_t *s_amul,
                                                uint32_t *region, int q, int g) {
     constexpr int W = kBlockWords / LANES;
     constexpr int G = 32 / LANES;
+    constexpr int U = MODE == 0 ? C : (MODE == 2 && C >= 2 ? 2 : 1);  // candidates loaded up front
     uint64_t word = 0;
     uint64_t xn = wd * 64 + g < n ? load_key(keys + wd * 64 + g) : 0ull;  // one step ahead
     for (int it = 0; it < 64 / G; ++it) {
@@ -197,59 +200,40 @@ __device__ __forceinline__ uint64_t query_word(const DevFilter &f, const uint64_
         const bool valid = i < n;
         const uint64_t x = xn;
         if (it + 1 < 64 / G) xn = i + G < n ? load_key(keys + i + G) : 0ull;
-        uint64_t m[W];
-        uint32_t hits = 0;
-        if constexpr (!EARLY) {
-            uint64_t blk[C][W];
+        uint64_t up[U][W];
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const uint64_t b = block_addr(f, f.a_block[c], x);
-                if (valid) {
-                    load_words<W, kLoadNC>(f.words + b * kBlockWords + (uint64_t)q * W, blk[c]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < W; ++j) blk[c][j] = 0ull;
-                }
-            }
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                uint64_t miss = 0;
-#pragma unroll
-                for (int j = 0; j < W; ++j) miss |= m[j] & ~blk[c][j];
-                hits |= fold_groups<LANES>(__ballot_sync(kFull, valid && miss == 0));
-            }
-        } else {
-            bool need = valid;
-            uint64_t first[W];  // the first candidate is loaded before the mask is built
+        for (int c = 0; c < U; ++c) {
             if (valid) {
-                load_words<W, kLoadNC>(f.words + block_addr(f, f.a_block[0], x) * kBlockWords + (uint64_t)q * W,
-                                       first);
+                load_words<W, kLoadNC>(f.words + block_addr(f, f.a_block[c], x) * kBlockWords + (uint64_t)q * W,
+                                       up[c]);
             } else {
 #pragma unroll
-                for (int j = 0; j < W; ++j) first[j] = 0ull;
+                for (int j = 0; j < W; ++j) up[c][j] = 0ull;
             }
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
+        }
+        uint64_t m[W];
+        key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
+        uint32_t hits = 0;
+        bool need = valid;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                uint64_t blk[W];
-                if (c == 0) {
+        for (int c = 0; c < C; ++c) {
+            uint64_t blk[W];
+            if (c < U) {
 #pragma unroll
-                    for (int j = 0; j < W; ++j) blk[j] = first[j];
-                } else if (need) {
-                    const uint64_t b = block_addr(f, f.a_block[c], x);
-                    load_words<W, kLoadNC>(f.words + b * kBlockWords + (uint64_t)q * W, blk);
-                } else {
+                for (int j = 0; j < W; ++j) blk[j] = up[c < U ? c : 0][j];
+            } else if (need) {
+                load_words<W, kLoadNC>(f.words + block_addr(f, f.a_block[c], x) * kBlockWords + (uint64_t)q * W,
+                                       blk);
+            } else {
 #pragma unroll
-                    for (int j = 0; j < W; ++j) blk[j] = 0ull;
-                }
-                uint64_t miss = 0;
-#pragma unroll
-                for (int j = 0; j < W; ++j) miss |= m[j] & ~blk[j];
-                const uint32_t got = fold_groups<LANES>(__ballot_sync(kFull, need && miss == 0));
-                hits |= got;
-                need = need && !((got >> (g * LANES)) & 1u);
+                for (int j = 0; j < W; ++j) blk[j] = 0ull;
             }
+            uint64_t miss = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) miss |= m[j] & ~blk[j];
+            const uint32_t got = fold_groups<LANES>(__ballot_sync(kFull, need && miss == 0));
+            hits |= got;
+            if (MODE != 0) need = need && !((got >> (g * LANES)) & 1u);
         }
         word |= (uint64_t)compress_groups<LANES>(hits) << (it * G);
     }

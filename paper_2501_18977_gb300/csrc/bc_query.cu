@@ -9,7 +9,7 @@ constexpr int kThreads = 256;
 
 // One warp answers 64 consecutive keys per step (query_word) and writes one
 // bitmap word; warps stride over the words of the bitmap.
-template <int C, int LANES, bool EARLY>
+template <int C, int LANES, int MODE>
 __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint64_t *__restrict__ keys,
                                                          uint64_t n, uint64_t *__restrict__ bitmap) {
     constexpr int G = 32 / LANES;
@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nwords = (n + 63) / 64;
     for (uint64_t wd = warp; wd < nwords; wd += nwarps) {
-        const uint64_t word = query_word<C, LANES, EARLY>(f, keys, n, wd, s_amul, region, q, g);
+        const uint64_t word = query_word<C, LANES, MODE>(f, keys, n, wd, s_amul, region, q, g);
         if (lane == 0) bitmap[wd] = word;
     }
 }
@@ -55,14 +55,14 @@ __global__ void __launch_bounds__(256) stats_kernel(const uint64_t *__restrict__
         if (s_hist[t]) atomicAdd(&hist[t], (unsigned long long)s_hist[t]);
 }
 
-template <int C, bool EARLY>
+template <int C, int MODE>
 cudaError_t query_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                            uint64_t *bitmap) {
     switch (L.lanes) {
-        case 1: query_kernel<C, 1, EARLY><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
-        case 2: query_kernel<C, 2, EARLY><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
-        case 4: query_kernel<C, 4, EARLY><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
-        case 8: query_kernel<C, 8, EARLY><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
+        case 1: query_kernel<C, 1, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
+        case 2: query_kernel<C, 2, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
+        case 4: query_kernel<C, 4, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
+        case 8: query_kernel<C, 8, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -72,13 +72,13 @@ cudaError_t query_dispatch(const Launch &L, const DevFilter &f, const uint64_t *
 
 cudaError_t launch_query(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                          uint64_t n, uint64_t *bitmap) {
-    const bool early = L.early != 0;
     switch (C) {
-        case 1: return query_dispatch<1, false>(L, f, keys, n, bitmap);
-        case 2: return early ? query_dispatch<2, true>(L, f, keys, n, bitmap)
-                             : query_dispatch<2, false>(L, f, keys, n, bitmap);
-        case 3: return early ? query_dispatch<3, true>(L, f, keys, n, bitmap)
-                             : query_dispatch<3, false>(L, f, keys, n, bitmap);
+        case 1: return query_dispatch<1, 0>(L, f, keys, n, bitmap);
+        case 2: return L.early == 0 ? query_dispatch<2, 0>(L, f, keys, n, bitmap)
+                                    : query_dispatch<2, 1>(L, f, keys, n, bitmap);
+        case 3: return L.early == 0 ? query_dispatch<3, 0>(L, f, keys, n, bitmap)
+                     : L.early == 1 ? query_dispatch<3, 1>(L, f, keys, n, bitmap)
+                                    : query_dispatch<3, 2>(L, f, keys, n, bitmap);
         default: return cudaErrorInvalidValue;
     }
 }

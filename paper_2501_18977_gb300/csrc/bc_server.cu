@@ -109,6 +109,7 @@ struct Slot {               // one registered filter
 struct Wave {
     int stream = 0;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t start = nullptr;  // timing: recorded before the wave's first copy
     std::vector<Req *> reqs;
     uint64_t staging = 0;
     bool active = false;
@@ -136,6 +137,7 @@ struct blowchoc_server {
     uint64_t used_bytes = 0, max_used = 0, staging_used = 0;
     uint64_t outstanding = 0;                  // submitted, not completed
     uint64_t completed = 0, keys_done = 0, nwaves = 0, wave_reqs = 0;
+    double wave_gpu_ms = 0.0, launch_host_s = 0.0;
     int error = BLOWCHOC_OK;
     char error_msg[256] = {0};
     std::mutex mu;
@@ -230,6 +232,8 @@ void collect(blowchoc_server *s) {
             s->keys_done += r->n;
             s->outstanding--;
         }
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, wv.start, wv.ev) == cudaSuccess) s->wave_gpu_ms += ms;
         s->staging_used -= wv.staging;
         s->stream_inflight[wv.stream]--;
         wv.active = false;
@@ -262,6 +266,9 @@ bool launch_wave(blowchoc_server *s) {
     for (int i = 0; i < nf && take.size() < s->cfg.max_wave_requests; ++i) {
         Slot &sl = s->slots[(s->rr + i) % nf];
         if (!sl.admitted || sl.removed || sl.fifo.empty()) continue;
+        // a filter with work in flight on another stream waits for it here,
+        // on the host: a device-side wait would hold the whole wave behind it
+        if (sl.last_wave >= 0 && s->waves[sl.last_wave].stream != st) continue;
         Req *r = sl.fifo.front();
         if (s->staging_used + staging + r->staging > s->cfg.staging_bytes) continue;
         if (!r->keys_pinned && r->key_bounce == SIZE_MAX) {
@@ -290,12 +297,15 @@ bool launch_wave(blowchoc_server *s) {
     std::vector<blowchoc_work> ins, qry;
     std::vector<void *> bufs;
     const double t = s->now();
+    const auto h0 = Clock::now();
     for (Req *r : take) {
         Slot &sl = s->slots[r->filter];
         sl.fifo.pop_front();
-        if (sl.last_wave >= 0) {
-            const cudaError_t e = cudaStreamWaitEvent(stream, s->waves[sl.last_wave].ev, 0);
-            if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave ordering", e); return false; }
+        // the filter's earlier work, if still in flight, is on this stream
+        // (selection above): stream order keeps its requests in FIFO order
+        if (r == take.front()) {
+            const cudaError_t e0 = cudaEventRecord(wv.start, stream);
+            if (e0 != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave event", e0); return false; }
         }
         void *dk = nullptr, *db = nullptr;
         const void *src = r->h_keys;
@@ -340,6 +350,7 @@ bool launch_wave(blowchoc_server *s) {
     s->stream_inflight[st]++;
     s->nwaves++;
     s->wave_reqs += take.size();
+    s->launch_host_s += std::chrono::duration<double>(Clock::now() - h0).count();
     return true;
 }
 
@@ -415,8 +426,10 @@ int blowchoc_server_create(const blowchoc_server_config *cfg, blowchoc_server **
     }
     s->stream_inflight.assign(s->streams.size(), 0);
     s->waves.resize(s->streams.size() * kWavesPerStream + 1);
-    for (Wave &w : s->waves)
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming);
+    for (Wave &w : s->waves) {
+        if (e == cudaSuccess) e = cudaEventCreate(&w.ev);
+        if (e == cudaSuccess) e = cudaEventCreate(&w.start);
+    }
     if (e != cudaSuccess) {
         blowchoc_server_destroy(s);
         return bc_set_error(BLOWCHOC_ECUDA, "blowchoc_server_create failed");
@@ -531,6 +544,8 @@ int blowchoc_server_stats(blowchoc_server *s, blowchoc_server_summary *out) {
     out->waves = s->nwaves;
     out->mean_wave_requests = s->nwaves ? (double)s->wave_reqs / (double)s->nwaves : 0.0;
     out->max_filter_bytes_used = s->max_used;
+    out->mean_wave_gpu_ms = s->nwaves ? s->wave_gpu_ms / (double)s->nwaves : 0.0;
+    out->launch_host_s = s->launch_host_s;
     for (const Slot &sl : s->slots) {
         if (sl.admitted && !sl.removed) out->filters_admitted++;
         if (!sl.admitted && !sl.removed) out->filters_pending++;
@@ -564,8 +579,10 @@ int blowchoc_server_destroy(blowchoc_server *s) {
     for (Slot &sl : s->slots)
         if (sl.f) blowchoc_destroy(sl.f);
     for (blowchoc_batch *b : s->batches) blowchoc_batch_destroy(b);
-    for (Wave &w : s->waves)
+    for (Wave &w : s->waves) {
         if (w.ev) cudaEventDestroy(w.ev);
+        if (w.start) cudaEventDestroy(w.start);
+    }
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     if (s->pool) cudaMemPoolDestroy(s->pool);
     cudaFreeHost(s->h_keys_arena);

@@ -151,6 +151,8 @@ def test_config_small_uniform_full():
          keys_per_cta=64, set_mode=1),
     dict(lanes_choose=8, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=16, persistent=1,
          set_mode=1),
+    dict(lanes_choose=2, lanes_set=4, lanes_query=1, query_early=2, ctas_per_sm=8, persistent=1),
+    dict(lanes_choose=2, lanes_set=4, lanes_query=2, query_early=2, ctas_per_sm=8, persistent=1),
 ])
 def test_results_independent_of_launch_configuration(tune):
     """Every launch configuration gives the oracle's words and bitmap."""
@@ -179,7 +181,7 @@ def test_set_tuning_rejects_bad_values():
     f = bc.Filter(64, 8, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=1)
     try:
         before = (f.tuning().lanes_query, f.tuning().ctas_per_sm)
-        for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=2),
+        for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=3),
                     dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2),
                     dict(keys_per_cta=8), dict(set_mode=2), dict(seq_window=16),
                     dict(seq_window=9000)]:
