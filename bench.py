@@ -62,7 +62,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
-                                           "learn"], default="dna")
+                                           "learn", "fig4", "fig8", "fig10"], default="dna")
+    ap.add_argument("--keys", type=float, default=2e9, help="fig4/fig8/fig10: keys inserted and negatives")
+    ap.add_argument("--ks", type=str, default="4,7,10,14,17,20", help="fig4/fig10: k values")
+    ap.add_argument("--runs", type=int, default=1, help="fig10: repetitions with other seeds")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--requests", type=int, default=10000)
     return ap.parse_args()
@@ -412,7 +415,7 @@ def run_sweep(args):
     estimate, and insert / query rates."""
     import torch
     import paper_2501_18977_gb300 as bc
-    from oracle import closed_forms as cf
+    from paper_2501_18977_gb300 import sweeps
     M, k, B = 1 << 23, 12, 1 << 20
     phi = (1.0 + math.sqrt(5.0)) / 2.0
     kinds = {"MIX": bc.COST_MIX, "LA": bc.COST_LA, "EXP": bc.COST_EXP}
@@ -443,8 +446,8 @@ def run_sweep(args):
             W = int(np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")[: neg.numel()].sum())
             rows.append({"c": c, "cost": cname, "bits_per_key": b, "n": n, "fpr": W / neg.numel(),
                          "false_positives": W, "fpr_est_hist": st.fpr_est,
-                         "blocked_bloom_formula": cf.blocked_bloom_fpr(n, M, k),
-                         "bloom_formula": cf.bloom_fpr(n, M * 512, k),
+                         "blocked_bloom_formula": sweeps.blocked_bloom_fpr(n, M, k),
+                         "bloom_formula": sweeps.bloom_fpr(n, M * 512, k),
                          "inserted": st.inserted, "skipped": st.skipped, "set_bits": st.set_bits,
                          "insert_mkeys_s": round((n - n_prev) / (e[0].elapsed_time(e[1]) / 1e3) / 1e6, 1),
                          "query_mkeys_s": round(neg.numel() / (e[1].elapsed_time(e[2]) / 1e3) / 1e6, 1)})
@@ -647,8 +650,46 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_figures(args):
+    """Paper-scale FPR and load sweeps on the device (keys generated there):
+    fig4 = log2 FPR vs relative size for c = 1, 2, 3 and random/distinct bits
+    (Section 4.1, Fig. 4); fig10 = log2 FPR vs the parameter of each cost at
+    the standard Bloom size (Appendix C, Fig. 10); fig8 = load histograms
+    (Appendix C, Fig. 8). One JSON line per point, then a summary line."""
+    import torch
+    from paper_2501_18977_gb300 import sweeps
+    n = int(args.keys)
+    ks = tuple(int(v) for v in args.ks.split(","))
+    t0 = time.perf_counter()
+    keys_done = [0]
+
+    def log(r):
+        r = dict(r)
+        hist = r.pop("hist", None)
+        if hist is not None:
+            r["hist_nonzero"] = {str(L): h for L, h in enumerate(hist) if h}
+        keys_done[0] += r["n"] + r["N"]
+        print(json.dumps(r), flush=True)
+
+    if args.workload == "fig4":
+        rows = sweeps.fig4(n=n, ks=ks, log=log)
+    elif args.workload == "fig10":
+        rows = sweeps.fig10(n=n, ks=ks, runs=tuple(range(1, args.runs + 1)), log=log)
+    else:
+        rows = sweeps.fig8(n=n, log=log)
+    wall = time.perf_counter() - t0
+    dev_s = sum(r["insert_ms"] + r["query_ms"] for r in rows) / 1e3
+    print(json.dumps({"workload": args.workload, "points": len(rows), "keys_per_point": n,
+                      "device_s": round(dev_s, 3), "wall_s": round(wall, 3),
+                      "gkeys_per_s_device": round(keys_done[0] / dev_s / 1e9, 3),
+                      "gpu": torch.cuda.get_device_name()}))
+
+
 def main():
     args = parse()
+    if args.workload in ("fig4", "fig8", "fig10"):
+        run_figures(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

@@ -71,7 +71,7 @@ typedef struct {
     uint64_t skipped;   /* keys already contained in a candidate block (Section 3.2) */
     uint64_t set_bits;  /* total 1-bits of the filter */
     uint64_t hist[BLOWCHOC_BLOCK_BITS + 1]; /* hist[L] = blocks with L set bits (Fig. 8) */
-    double fpr_est;     /* 1 - (1 - mean_b (L_b/512)^k)^c, see blowchoc_stats */
+    double fpr_est;     /* 1 - (1 - q)^c, q from the histogram, see blowchoc_stats */
 } blowchoc_filter_stats;
 
 /*
@@ -153,8 +153,9 @@ int blowchoc_query(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n,
  * set bits per block, the total, and the insert/skip counters. Runs on the
  * filter's home stream and synchronises it before returning (host result).
  * fpr_est is the false-positive rate implied by the histogram for ideal
- * hashing, q = mean_b (L_b/512)^k (exact in expectation for c = 1), combined
- * over c candidates as if independent: 1 - (1 - q)^c.
+ * hashing, q = mean_b (L_b/512)^k (exact in expectation for c = 1; with
+ * distinct bit selection mean_b C(L_b, k) / C(512, k)), combined over c
+ * candidates as if independent: 1 - (1 - q)^c.
  * Errors: EINVAL (NULL pointers), ECUDA, ETIMEOUT (an earlier bounded
  * device wait of this filter gave up; its result is not trustworthy).
  */
@@ -218,6 +219,35 @@ int blowchoc_write_words(blowchoc_filter *f, uint64_t first, uint64_t count, con
  * zero), queued on `stream`. Errors: EINVAL, ECUDA.
  */
 int blowchoc_clear(blowchoc_filter *f, void *stream);
+
+/*
+ * blowchoc_query_count -- the query of blowchoc_query, counted instead of
+ * written out: adds to *d_count the number of keys of d_keys[0..n) that are
+ * reported present. For false-positive rates over large negative sets.
+ *   d_count   device, in/out, one uint64 (the caller zeroes it).
+ * Errors: EINVAL (NULL filter, NULL pointers with n > 0), ECUDA.
+ */
+int blowchoc_query_count(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, unsigned long long *d_count,
+                         void *stream);
+
+/*
+ * blowchoc_generate_keys -- input generation, not part of the filter:
+ * d_out[i] = output (start + i) of splitmix64 seeded with `seed`
+ * (z = seed + (start + i + 1) * 0x9E3779B97F4A7C15, then the generator's two
+ * xor-shift-multiply steps and a final xor-shift), i.e. the stream the
+ * Python input generators give on the host.
+ *   d_out     device, out, n uint64.
+ * Errors: EINVAL (NULL d_out with n > 0), ECUDA.
+ */
+int blowchoc_generate_keys(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t start, void *stream);
+
+/*
+ * blowchoc_cluster_ctas -- CTAs per cluster that an insert of n keys into f
+ * would run cluster-resident with (see blowchoc_tuning.cluster_max), or 0
+ * when it would take the global-memory kernels. Needs the device (queries
+ * its cluster limits once). Errors: EINVAL (NULL pointers).
+ */
+int blowchoc_cluster_ctas(blowchoc_filter *f, uint64_t n, uint32_t *ctas);
 
 /*
  * blowchoc_launch_count -- number of kernels this library has launched in
@@ -455,6 +485,17 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       earliest key wins each block) and the keys that won all of theirs
  *       decide and set their bits; such keys share no candidate block with
  *       any earlier pending key. 0 = one warp inserting key after key.
+ *   cluster_max: an insert of at least 4 batches (B >= 2) into a filter
+ *       that fits in the shared memory of one thread-block cluster runs
+ *       cluster-resident: the cluster's CTAs hold the filter's words (a
+ *       contiguous slice each), every batch reads and ORs them there over
+ *       distributed shared memory with a cluster barrier between phases,
+ *       and the words are written back at the end. cluster_max caps the
+ *       CTAs per cluster (1..16, further capped by the device); 0 = never.
+ *   lanes_cluster: lanes per key of the cluster-resident insert (4 or 8).
+ *   cluster_keys: keys of a batch per CTA that the cluster-resident insert
+ *       aims for: a cluster takes more CTAs than the filter needs (up to
+ *       cluster_max) while a batch has more keys per CTA (16..2^20).
  */
 typedef struct {
     uint32_t lanes_choose;
@@ -466,6 +507,9 @@ typedef struct {
     uint32_t keys_per_cta;
     uint32_t set_mode;
     uint32_t seq_window;
+    uint32_t cluster_max;
+    uint32_t lanes_cluster;
+    uint32_t cluster_keys;
 } blowchoc_tuning;
 
 /* Read / replace a filter's launch configuration. set_tuning checks every
@@ -474,7 +518,9 @@ int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out);
 int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t);
 
 /* The same for a batch object's many-filter kernels (lanes_choose applies to
- * both insert phases; lanes_query, query_early, ctas_per_sm as above). */
+ * both insert phases; lanes_query, query_early, ctas_per_sm, cluster_max,
+ * lanes_cluster, cluster_keys as above; cluster_max > 0 gives each eligible
+ * filter of a call a cluster of its own, default 0). */
 int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out);
 int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t);
 

@@ -47,7 +47,8 @@ class blowchoc_tuning(ctypes.Structure):
                 ("lanes_query", ctypes.c_uint32), ("query_early", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
                 ("keys_per_cta", ctypes.c_uint32), ("set_mode", ctypes.c_uint32),
-                ("seq_window", ctypes.c_uint32)]
+                ("seq_window", ctypes.c_uint32), ("cluster_max", ctypes.c_uint32),
+                ("lanes_cluster", ctypes.c_uint32), ("cluster_keys", ctypes.c_uint32)]
 
 
 class blowchoc_work(ctypes.Structure):
@@ -90,6 +91,9 @@ _SIGS = {
     "blowchoc_l2_residency": ([_VP, ctypes.c_double, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
+    "blowchoc_cluster_ctas": ([_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)], _I),
+    "blowchoc_query_count": ([_VP, _VP, ctypes.c_uint64, _VP, _VP], _I),
+    "blowchoc_generate_keys": ([_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _VP], _I),
     "blowchoc_batch_create": ([ctypes.POINTER(_VP)], _I),
     "blowchoc_batch_destroy": ([_VP], _I),
     "blowchoc_insert_many": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32, _VP], _I),
@@ -246,6 +250,32 @@ def blowchoc_l2_residency(f, fraction, stream):
 
 def blowchoc_clear(f, stream=None):
     _check(load_library().blowchoc_clear(f, _stream(stream)))
+
+
+def blowchoc_query_count(f, d_keys, n: int, d_count, stream=None):
+    _check(load_library().blowchoc_query_count(f, d_keys, int(n), d_count, _stream(stream)))
+
+
+def blowchoc_generate_keys(d_out, n: int, seed: int, start: int = 0, stream=None):
+    _check(load_library().blowchoc_generate_keys(d_out, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF, int(start),
+                                                 _stream(stream)))
+
+
+def generate_keys(n: int, seed: int, start: int = 0, out=None, stream=None):
+    """n splitmix64 keys of `seed` from stream position `start`, generated on
+    the current CUDA device into `out` (an int64 tensor) or a new tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(int(n), dtype=torch.int64, device="cuda")
+    assert out.dtype == torch.int64 and out.is_cuda and out.is_contiguous() and out.numel() >= n
+    blowchoc_generate_keys(out.data_ptr(), n, seed, start, stream)
+    return out
+
+
+def blowchoc_cluster_ctas(f, n: int) -> int:
+    out = ctypes.c_uint32()
+    _check(load_library().blowchoc_cluster_ctas(f, int(n), ctypes.byref(out)))
+    return int(out.value)
 
 
 def blowchoc_get_tuning(f) -> blowchoc_tuning:
@@ -593,6 +623,23 @@ class Filter:
 
     def l2_residency(self, fraction, stream):
         blowchoc_l2_residency(self.handle, fraction, stream)
+
+    def cluster_ctas(self, n):
+        return blowchoc_cluster_ctas(self.handle, n)
+
+    def query_count(self, keys, count=None, stream=None):
+        """Number of `keys` (int64 CUDA tensor) reported present. With a
+        one-element int64 CUDA tensor `count`, adds to it asynchronously and
+        returns it; otherwise synchronises and returns an int."""
+        import torch
+        assert keys.dtype == torch.int64 and keys.is_cuda and keys.is_contiguous()
+        own = count is None
+        if own:
+            count = torch.zeros(1, dtype=torch.int64, device=keys.device)
+        blowchoc_query_count(self.handle, keys.data_ptr(), keys.numel(), count.data_ptr(), stream)
+        if own:
+            return int(count.item())
+        return count
 
     def tuning(self):
         return blowchoc_get_tuning(self.handle)

@@ -205,6 +205,7 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
     } else {
         d.range_kind = (d.M & 1) ? bc::kRangeOdd : bc::kRangeEven;
         d.shift = 0;
+        d.mod_mul = bc::mod_mul_for(d.M);
     }
     d.bitsel = params->bitsel;
     derive_multipliers(params->hash_seed, d.M, d.k, d.c, d.bitsel, d.a_block, d.a_bit);
@@ -232,6 +233,24 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
     return BLOWCHOC_OK;
 }
 
+namespace {
+
+// Shape of the cluster-resident insert for n keys, S = 0 if not taken.
+bc::ClusterShape cluster_plan(const blowchoc_filter *f, uint64_t n) {
+    const uint64_t B = f->p.batch;
+    if (f->cluster_max == 0 || B < 2 || n == 0 || (n + B - 1) / B < bc::kClusterMinRounds) return bc::ClusterShape();
+    return bc::cluster_shape((int)f->p.choices, f->lanes_cluster, f->dev.M, f->dev.k, std::min(B, n),
+                             f->cluster_max, (uint64_t)f->cluster_keys);
+}
+
+}  // namespace
+
+int blowchoc_cluster_ctas(blowchoc_filter *f, uint64_t n, uint32_t *ctas) {
+    if (!f || !ctas) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    *ctas = (uint32_t)cluster_plan(f, n).S;
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream) {
     if (!f) return fail(BLOWCHOC_EINVAL, "filter is NULL");
     if (n == 0) return BLOWCHOC_OK;
@@ -251,6 +270,22 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
         BC_CUDA(counted(bc::launch_sequential(C, s, f->dev, d_keys, n, f->d_rank, f->d_counters)),
                 "sequential insert launch");
         return BLOWCHOC_OK;
+    }
+    {
+        const bc::ClusterShape sh = cluster_plan(f, n);
+        if (sh.S) {
+            bc::ManyItem one;
+            std::memset(&one, 0, sizeof one);
+            one.f = f->dev;
+            one.rank = f->d_rank;
+            one.keys = d_keys;
+            one.n = n;
+            one.B = B;
+            one.counters = f->d_counters;
+            BC_CUDA(counted(bc::launch_cluster_insert(C, f->lanes_cluster, sh, 1, s, nullptr, one)),
+                    "cluster insert launch");
+            return BLOWCHOC_OK;
+        }
     }
     if (B <= bc::kSingleCtaBatch || (!f->persistent && B <= bc::kSmallBatchMax)) {
         bc::Launch L{1, f->lanes_choose, s};
@@ -309,6 +344,29 @@ int blowchoc_query(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, uint6
     return BLOWCHOC_OK;
 }
 
+int blowchoc_query_count(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, unsigned long long *d_count,
+                         void *stream) {
+    if (!f) return fail(BLOWCHOC_EINVAL, "filter is NULL");
+    if (n == 0) return BLOWCHOC_OK;
+    if (!d_keys || !d_count) return fail(BLOWCHOC_EINVAL, "keys or count is NULL");
+    const uint64_t nwords = (n + 63) / 64;
+    bc::Launch L{grid_for(f, nwords * 32, 256, f->ctas_per_sm), f->lanes_query, (cudaStream_t)stream, f->query_early};
+    BC_CUDA(counted(bc::launch_query((int)f->p.choices, L, f->dev, d_keys, n, nullptr, d_count)),
+            "query count launch");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_generate_keys(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t start, void *stream) {
+    if (n == 0) return BLOWCHOC_OK;
+    if (!d_out) return fail(BLOWCHOC_EINVAL, "out is NULL");
+    int dev = 0, sms = 0;
+    BC_CUDA(cudaGetDevice(&dev), "device");
+    BC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    BC_CUDA(counted(bc::launch_generate_keys((cudaStream_t)stream, sms, d_out, n, seed, start)),
+            "key generation launch");
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
     if (!f || !out) return fail(BLOWCHOC_EINVAL, "filter or out is NULL");
     unsigned long long *d_hist = f->d_counters + 3;
@@ -321,11 +379,21 @@ int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
     std::memset(out, 0, sizeof *out);
     out->inserted = h[0];
     out->skipped = h[1];
+    // probability that a negative finds all its bits set in a block of load
+    // L: (L / 512)^k for independent bit addresses, C(L, k) / C(512, k) for
+    // k distinct ones (Appendix B)
     double q = 0.0;
     for (int L = 0; L <= 512; ++L) {
         out->hist[L] = h[3 + L];
         out->set_bits += (uint64_t)L * h[3 + L];
-        q += (double)h[3 + L] * std::pow((double)L / 512.0, (double)f->p.k);
+        double pL = 1.0;
+        if (f->p.bitsel) {
+            for (uint32_t i = 0; i < f->p.k; ++i) pL *= (double)((int)L - (int)i) / (double)(512 - i);
+            if (pL < 0.0) pL = 0.0;
+        } else {
+            pL = std::pow((double)L / 512.0, (double)f->p.k);
+        }
+        q += (double)h[3 + L] * pL;
     }
     q /= (double)f->dev.M;
     out->fpr_est = 1.0 - std::pow(1.0 - q, (double)f->p.choices);
@@ -440,6 +508,9 @@ int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     out->keys_per_cta = (uint32_t)f->keys_per_cta;
     out->set_mode = (uint32_t)f->set_mode;
     out->seq_window = (uint32_t)f->seq_window;
+    out->cluster_max = (uint32_t)f->cluster_max;
+    out->lanes_cluster = (uint32_t)f->lanes_cluster;
+    out->cluster_keys = (uint32_t)f->cluster_keys;
     return BLOWCHOC_OK;
 }
 
@@ -456,6 +527,10 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     if (t->set_mode > 1) return fail(BLOWCHOC_EINVAL, "set_mode must be 0 or 1");
     if (t->seq_window != 0 && (t->seq_window < 32 || t->seq_window > bc::kSeqMaxWindow))
         return fail(BLOWCHOC_EINVAL, "seq_window must be 0 or in 32..8192");
+    if (t->cluster_max > 16) return fail(BLOWCHOC_EINVAL, "cluster_max must be in 0..16");
+    if (t->lanes_cluster != 4 && t->lanes_cluster != 8) return fail(BLOWCHOC_EINVAL, "lanes_cluster must be 4 or 8");
+    if (t->cluster_keys < 16 || t->cluster_keys > (1u << 20))
+        return fail(BLOWCHOC_EINVAL, "cluster_keys must be in 16..2^20");
     f->lanes_choose = (int)t->lanes_choose;
     f->lanes_set = (int)t->lanes_set;
     f->lanes_query = (int)t->lanes_query;
@@ -465,6 +540,9 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     f->keys_per_cta = (int)t->keys_per_cta;
     f->set_mode = (int)t->set_mode;
     f->seq_window = (int)t->seq_window;
+    f->cluster_max = (int)t->cluster_max;
+    f->lanes_cluster = (int)t->lanes_cluster;
+    f->cluster_keys = (int)t->cluster_keys;
     return BLOWCHOC_OK;
 }
 

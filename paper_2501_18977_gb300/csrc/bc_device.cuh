@@ -29,17 +29,41 @@ struct DevFilter {
     uint32_t c;            // choices (for dispatch checks)
     uint32_t bitsel;       // 0 = random bit selection, 1 = distinct (Appendix B)
     uint32_t pad;
+    uint64_t mod_mul;      // floor(2^64 / M) for M not a power of two (mod_fast)
     uint64_t a_block[3];   // h_1..h_c multipliers
     uint64_t a_bit[32];    // f_1..f_k multipliers
 };
+
+// y mod d for d >= 2 with mul = floor(2^64 / d): q = floor(y mul / 2^64) is
+// floor(y / d) or one less (mul > 2^64 / d - 1 and y < 2^64), so y - q d
+// lies in [0, 2d) and one conditional subtraction finishes it. Exact for
+// every 64-bit y; replaces the library's 64-bit division.
+__host__ __device__ constexpr uint64_t mod_mul_for(uint64_t d) {
+    return ~0ull / d + (~0ull % d == d - 1 ? 1ull : 0ull);
+}
+__device__ __forceinline__ uint64_t mod_fast(uint64_t y, uint64_t d, uint64_t mul) {
+    const uint64_t q = __umul64hi(y, mul);
+    const uint64_t r = y - q * d;
+    return r >= d ? r - d : r;
+}
 
 // h_i(x): linear hash into [M] (Section 3.4) with u = 64.
 __device__ __forceinline__ uint64_t block_addr(const DevFilter &f, uint64_t a, uint64_t x) {
     uint64_t y = a * x;
     if (f.range_kind == kRangePow2) return f.shift >= 64 ? 0ull : (y >> f.shift);
     if (f.range_kind == kRangeEven) y ^= (y >> 32);
-    return y % f.M;
+    return mod_fast(y, f.M, f.mod_mul);
 }
+
+// mod_mul_for(512 - i) for the ranges of distinct bit selection (i >= 1).
+__constant__ const uint64_t kBitRangeMul[32] = {
+    0, mod_mul_for(511), mod_mul_for(510), mod_mul_for(509), mod_mul_for(508), mod_mul_for(507),
+    mod_mul_for(506), mod_mul_for(505), mod_mul_for(504), mod_mul_for(503), mod_mul_for(502),
+    mod_mul_for(501), mod_mul_for(500), mod_mul_for(499), mod_mul_for(498), mod_mul_for(497),
+    mod_mul_for(496), mod_mul_for(495), mod_mul_for(494), mod_mul_for(493), mod_mul_for(492),
+    mod_mul_for(491), mod_mul_for(490), mod_mul_for(489), mod_mul_for(488), mod_mul_for(487),
+    mod_mul_for(486), mod_mul_for(485), mod_mul_for(484), mod_mul_for(483), mod_mul_for(482),
+    mod_mul_for(481)};
 
 __device__ __forceinline__ uint64_t block_mult(const DevFilter &f, uint32_t i) {
     return i == 0 ? f.a_block[0] : (i == 1 ? f.a_block[1] : f.a_block[2]);
@@ -52,7 +76,7 @@ __device__ __forceinline__ uint32_t bit_hash_range(uint64_t a, uint64_t x, uint3
     uint64_t y = a * x;
     if (range == 512u) return (uint32_t)(y >> 55);
     if ((range & 1u) == 0) y ^= (y >> 32);
-    return (uint32_t)(y % range);
+    return (uint32_t)mod_fast(y, range, kBitRangeMul[512u - range]);
 }
 
 // Index of the r-th (0-based) zero bit of a 64-bit word that has more than

@@ -28,6 +28,9 @@ struct blowchoc_filter {
     uint64_t sorted_cap = 0;
     int seq_window = 2048;         // B = 1: keys per reservation window (0: one-warp kernel)
     unsigned long long *d_resv = nullptr;  // B = 1 reservations, M words
+    int cluster_max = 16;          // cluster-resident insert: CTAs per cluster at most (0: off)
+    int lanes_cluster = 8;
+    int cluster_keys = 128;        // keys of a batch per CTA the cluster size aims for
 };
 
 // Adds one to the library's launch counter (blowchoc_launch_count).

@@ -63,19 +63,60 @@ cudaError_t launch_small_batch(int C, const Launch &L, const DevFilter &f, const
                                uint64_t n, uint64_t B, const uint16_t *rank,
                                unsigned long long *counters);
 
-// Membership query into an LSB-first bitmap of ceil(n/64) words.
+// Membership query into an LSB-first bitmap of ceil(n/64) words (bitmap may
+// be null); with count, the number of present keys is added to *count.
 cudaError_t launch_query(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
-                         uint64_t n, uint64_t *bitmap);
+                         uint64_t n, uint64_t *bitmap, unsigned long long *count = nullptr);
+
+// d_out[i] = output start + i of splitmix64 seeded with `seed`.
+cudaError_t launch_generate_keys(cudaStream_t s, int sms, uint64_t *d_out, uint64_t n, uint64_t seed,
+                                 uint64_t start);
+
+// Device work-list entry of one filter (many-filter and cluster launches).
+struct ManyItem {
+    DevFilter f;
+    const uint16_t *rank;
+    const uint64_t *keys;
+    uint64_t n;
+    uint64_t B;
+    uint8_t *sel;                  // min(B, n) choice bytes (insert)
+    unsigned long long *counters;  // the filter's counters (inserted, skipped)
+    uint64_t *bitmap;              // query output
+};
 
 // Many-filter execution (bc_many.cu): one cooperative insert launch over the
 // rounds of a work list, and one query launch over its bitmap words.
-struct ManyItem;
 uint64_t many_tile();
 cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
                                uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
                                unsigned long long *err, int sms);
 cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
                               uint32_t nitems, const uint32_t *prefix);
+
+// Cluster-resident insert (bc_cluster.cu): one thread-block cluster holds a
+// whole filter in the distributed shared memory of its CTAs and runs every
+// batch of the insert there (choose, cluster barrier, set, cluster barrier).
+// Cluster i of the launch takes items[i]; with items == nullptr the launch
+// has one cluster and takes `one`.
+constexpr uint64_t kClusterMinRounds = 4;  // fewer batches take the global-memory kernels
+constexpr uint64_t kClusterMaxPasses = 4;  // so do batches of more than 4 keys per lane group of a cluster
+struct ClusterShape {
+    int S = 0;              // CTAs per cluster (0: the filters do not fit)
+    uint32_t slice = 0;     // blocks per CTA (the largest filter's)
+    uint32_t rank_u16 = 0;  // rank-table entries per CTA (the largest k's)
+    uint32_t kpc = 0;       // keys of one batch per CTA (key buffers and choice bytes)
+    size_t smem = 0;        // dynamic shared memory per CTA
+};
+// Shape for filters of at most M blocks, k bit hashes and batches of at most
+// Beff keys: the fewest CTAs per cluster (at most max_S, capped by the device)
+// that hold the filter; with keys_per_cta > 0, more CTAs while a batch has
+// more than keys_per_cta keys per CTA (fewer passes per batch).
+// cluster_shape_at: the shape at exactly S CTAs (S = 0: no fit).
+ClusterShape cluster_shape(int C, int lanes, uint64_t M, uint32_t k, uint64_t Beff, int max_S,
+                           uint64_t keys_per_cta);
+ClusterShape cluster_shape_at(int C, int lanes, int S, uint64_t M, uint32_t k, uint64_t Beff);
+cudaError_t launch_cluster_insert(int C, int lanes, const ClusterShape &sh, int nclusters, cudaStream_t s,
+                                  const ManyItem *items, const ManyItem &one);
 
 // Load histogram: hist[L] += blocks with L set bits (hist has 513 entries).
 cudaError_t launch_stats(const Launch &L, const uint64_t *words, uint64_t M,

@@ -8,10 +8,12 @@ namespace {
 constexpr int kThreads = 256;
 
 // One warp answers 64 consecutive keys per step (query_word) and writes one
-// bitmap word; warps stride over the words of the bitmap.
+// bitmap word; warps stride over the words of the bitmap. With `count`, the
+// warp also adds its number of present keys to *count (bitmap may be null).
 template <int C, int LANES, int MODE>
 __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint64_t *__restrict__ keys,
-                                                         uint64_t n, uint64_t *__restrict__ bitmap) {
+                                                         uint64_t n, uint64_t *__restrict__ bitmap,
+                                                         unsigned long long *__restrict__ count) {
     constexpr int G = 32 / LANES;
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
@@ -22,10 +24,15 @@ __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nwords = (n + 63) / 64;
+    uint32_t present = 0;
     for (uint64_t wd = warp; wd < nwords; wd += nwarps) {
         const uint64_t word = query_word<C, LANES, MODE>(f, keys, n, wd, s_amul, region, q, g);
-        if (lane == 0) bitmap[wd] = word;
+        if (lane == 0) {
+            if (bitmap) bitmap[wd] = word;
+            present += (uint32_t)__popcll(word);
+        }
     }
+    if (count && lane == 0 && present) atomicAdd(count, (unsigned long long)present);
 }
 
 // Histogram of set bits per block. Four lanes read one 64-byte block as
@@ -57,12 +64,12 @@ __global__ void __launch_bounds__(256) stats_kernel(const uint64_t *__restrict__
 
 template <int C, int MODE>
 cudaError_t query_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
-                           uint64_t *bitmap) {
+                           uint64_t *bitmap, unsigned long long *count) {
     switch (L.lanes) {
-        case 1: query_kernel<C, 1, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
-        case 2: query_kernel<C, 2, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
-        case 4: query_kernel<C, 4, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
-        case 8: query_kernel<C, 8, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap); break;
+        case 1: query_kernel<C, 1, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap, count); break;
+        case 2: query_kernel<C, 2, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap, count); break;
+        case 4: query_kernel<C, 4, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap, count); break;
+        case 8: query_kernel<C, 8, MODE><<<L.grid, kThreads, 0, L.stream>>>(f, keys, n, bitmap, count); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -71,14 +78,14 @@ cudaError_t query_dispatch(const Launch &L, const DevFilter &f, const uint64_t *
 }  // namespace
 
 cudaError_t launch_query(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
-                         uint64_t n, uint64_t *bitmap) {
+                         uint64_t n, uint64_t *bitmap, unsigned long long *count) {
     switch (C) {
-        case 1: return query_dispatch<1, 0>(L, f, keys, n, bitmap);
-        case 2: return L.early == 0 ? query_dispatch<2, 0>(L, f, keys, n, bitmap)
-                                    : query_dispatch<2, 1>(L, f, keys, n, bitmap);
-        case 3: return L.early == 0 ? query_dispatch<3, 0>(L, f, keys, n, bitmap)
-                     : L.early == 1 ? query_dispatch<3, 1>(L, f, keys, n, bitmap)
-                                    : query_dispatch<3, 2>(L, f, keys, n, bitmap);
+        case 1: return query_dispatch<1, 0>(L, f, keys, n, bitmap, count);
+        case 2: return L.early == 0 ? query_dispatch<2, 0>(L, f, keys, n, bitmap, count)
+                                    : query_dispatch<2, 1>(L, f, keys, n, bitmap, count);
+        case 3: return L.early == 0 ? query_dispatch<3, 0>(L, f, keys, n, bitmap, count)
+                     : L.early == 1 ? query_dispatch<3, 1>(L, f, keys, n, bitmap, count)
+                                    : query_dispatch<3, 2>(L, f, keys, n, bitmap, count);
         default: return cudaErrorInvalidValue;
     }
 }

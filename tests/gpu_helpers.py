@@ -10,12 +10,15 @@ def to_dev(keys):
     return torch.from_numpy(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)).cuda()
 
 
-def gpu_run(M, k, c, kind, par, seed, B, keys, queries, chunks=None):
+def gpu_run(M, k, c, kind, par, seed, B, keys, queries, chunks=None, tune=None):
     """Insert `keys` (optionally in several insert calls, split at `chunks`),
-    query `queries`; returns (words, bitmap, stats) as host values."""
+    query `queries`; returns (words, bitmap, stats) as host values. `tune`
+    holds launch-configuration fields to set first."""
     import paper_2501_18977_gb300 as bc
     f = bc.Filter(M, k, c, kind, par, hash_seed=seed, batch=B)
     try:
+        if tune:
+            f.set_tuning(**tune)
         dk = to_dev(keys)
         if chunks:
             edges = [0] + list(chunks) + [len(keys)]

@@ -52,7 +52,13 @@ def _check_against_oracle(cases, filters, keys, queries, bitmaps, seed0):
         assert (st.inserted, st.skipped) == (o.inserted, o.skipped), j
 
 
-def test_insert_and_query_many_match_the_oracle():
+@pytest.mark.parametrize("tune", [dict(cluster_max=16, lanes_cluster=4), dict(cluster_max=16, lanes_cluster=8),
+                                  dict(cluster_max=2, lanes_cluster=4), dict(cluster_max=0)],
+                         ids=["cluster16", "cluster16-lanes8", "cluster2", "worklist-only"])
+def test_insert_and_query_many_match_the_oracle(tune):
+    """The mix runs partly cluster-resident (small filters with at least four
+    batches, one cluster per filter) and partly over the work list; with
+    cluster_max = 0 all of it over the work list."""
     import torch
     import paper_2501_18977_gb300 as bc
     seed0 = 11
@@ -62,6 +68,7 @@ def test_insert_and_query_many_match_the_oracle():
     bms = [torch.zeros(max(1, (len(q) + 63) // 64), dtype=torch.int64, device="cuda") for q in queries]
     batch = bc.Batch()
     try:
+        batch.set_tuning(**tune)
         batch.insert_many([(f, d, len(k), None) for f, d, k in zip(filters, dk, keys)])
         batch.query_many([(f, d, len(q), b) for f, d, q, b in zip(filters, dq, queries, bms)])
         torch.cuda.synchronize()

@@ -46,13 +46,16 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("cluster", [16, 0], ids=["cluster", "global"])
 @pytest.mark.parametrize("M,k,c,kind,par,B,n", CASES)
-def test_parity_small(M, k, c, kind, par, B, n):
+def test_parity_small(M, k, c, kind, par, B, n, cluster):
+    """Every case with the cluster-resident insert allowed (taken wherever the
+    filter fits and there are at least four batches) and with it off."""
     seed = 1000 + M + k
     keys = workloads.uniform_keys(M * 7 + k, n)
     neg = workloads.disjoint_keys(M * 7 + k + 1, n // 2 + 13, keys)
     queries = np.concatenate([keys[: n // 2 + 7], neg])
-    words, bm, st = gpu_run(M, k, c, kind, par, seed, B, keys, queries)
+    words, bm, st = gpu_run(M, k, c, kind, par, seed, B, keys, queries, tune=dict(cluster_max=cluster))
     o, obm, hist, total = oracle_run(M, k, c, kind, par, seed, B, keys, queries)
     assert np.array_equal(words, o.words)
     assert np.array_equal(bm, obm)
@@ -134,25 +137,30 @@ def test_config_small_uniform_full():
 
 
 @pytest.mark.parametrize("tune", [
-    dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=0, ctas_per_sm=1, persistent=0),
-    dict(lanes_choose=8, lanes_set=4, lanes_query=8, query_early=1, ctas_per_sm=3, persistent=0),
-    dict(lanes_choose=4, lanes_set=8, lanes_query=4, query_early=0, ctas_per_sm=16, persistent=0),
-    dict(lanes_choose=1, lanes_set=1, lanes_query=1, query_early=1, ctas_per_sm=2, persistent=0),
-    dict(lanes_choose=1, lanes_set=2, lanes_query=1, query_early=0, ctas_per_sm=8, persistent=1),
-    dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=1, ctas_per_sm=1, persistent=1),
-    dict(lanes_choose=8, lanes_set=2, lanes_query=4, query_early=1, ctas_per_sm=16, persistent=1),
+    dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=0, ctas_per_sm=1, persistent=0, cluster_max=0),
+    dict(lanes_choose=8, lanes_set=4, lanes_query=8, query_early=1, ctas_per_sm=3, persistent=0, cluster_max=0),
+    dict(lanes_choose=4, lanes_set=8, lanes_query=4, query_early=0, ctas_per_sm=16, persistent=0, cluster_max=0),
+    dict(lanes_choose=1, lanes_set=1, lanes_query=1, query_early=1, ctas_per_sm=2, persistent=0, cluster_max=0),
+    dict(lanes_choose=1, lanes_set=2, lanes_query=1, query_early=0, ctas_per_sm=8, persistent=1, cluster_max=0),
+    dict(lanes_choose=2, lanes_set=2, lanes_query=2, query_early=1, ctas_per_sm=1, persistent=1, cluster_max=0),
+    dict(lanes_choose=8, lanes_set=2, lanes_query=4, query_early=1, ctas_per_sm=16, persistent=1, cluster_max=0),
     dict(lanes_choose=2, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=8, persistent=1,
-         keys_per_cta=32),
+         keys_per_cta=32, cluster_max=0),
     dict(lanes_choose=4, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=4, persistent=1,
-         keys_per_cta=1 << 20),
+         keys_per_cta=1 << 20, cluster_max=0),
     dict(lanes_choose=2, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=8, persistent=1,
-         set_mode=1),
+         set_mode=1, cluster_max=0),
     dict(lanes_choose=4, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=2, persistent=1,
-         keys_per_cta=64, set_mode=1),
+         keys_per_cta=64, set_mode=1, cluster_max=0),
     dict(lanes_choose=8, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=16, persistent=1,
-         set_mode=1),
-    dict(lanes_choose=2, lanes_set=4, lanes_query=1, query_early=2, ctas_per_sm=8, persistent=1),
-    dict(lanes_choose=2, lanes_set=4, lanes_query=2, query_early=2, ctas_per_sm=8, persistent=1),
+         set_mode=1, cluster_max=0),
+    dict(lanes_choose=2, lanes_set=4, lanes_query=1, query_early=2, ctas_per_sm=8, persistent=1, cluster_max=0),
+    dict(lanes_choose=2, lanes_set=4, lanes_query=2, query_early=2, ctas_per_sm=8, persistent=1, cluster_max=0),
+    dict(cluster_max=16, lanes_cluster=4),
+    dict(cluster_max=16, lanes_cluster=8),
+    dict(cluster_max=2, lanes_cluster=8),
+    dict(cluster_max=3, lanes_cluster=4),
+    dict(cluster_max=1, lanes_cluster=4),   # does not fit one CTA: global-memory kernels
 ])
 def test_results_independent_of_launch_configuration(tune):
     """Every launch configuration gives the oracle's words and bitmap."""
@@ -184,7 +192,8 @@ def test_set_tuning_rejects_bad_values():
         for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=3),
                     dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2),
                     dict(keys_per_cta=8), dict(set_mode=2), dict(seq_window=16),
-                    dict(seq_window=9000)]:
+                    dict(seq_window=9000), dict(cluster_max=17), dict(lanes_cluster=2),
+                    dict(lanes_cluster=16), dict(cluster_keys=8), dict(cluster_keys=(1 << 20) + 1)]:
             with pytest.raises(bc.BlowChocError):
                 f.set_tuning(**bad)
         assert (f.tuning().lanes_query, f.tuning().ctas_per_sm) == before
@@ -206,7 +215,7 @@ def test_sort_by_block_set_matches_oracle(M, k, c, kind, par, B, n):
     queries = np.concatenate([keys[:50000], neg])
     f = bc.Filter(M, k, c, kind, par, hash_seed=5, batch=B)
     try:
-        f.set_tuning(set_mode=1, persistent=1)
+        f.set_tuning(set_mode=1, persistent=1, cluster_max=0)
         f.insert(to_dev(keys))
         bm = f.query(to_dev(queries)).cpu().numpy().view(np.uint64)
         words = f.words_host()
