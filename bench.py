@@ -679,10 +679,25 @@ def run_figures(args):
         rows = sweeps.fig8(n=n, log=log)
     wall = time.perf_counter() - t0
     dev_s = sum(r["insert_ms"] + r["query_ms"] for r in rows) / 1e3
+
+    def l2(r):
+        return round(r["log2_fpr"], 3) if r["log2_fpr"] is not None else None
+
+    if args.workload == "fig4":
+        cols = ["k", "rel_size", "bitsel", "c", "log2_fpr", "log2_bloom_formula"]
+        table = [[r["k"], r["rel_size"], r["bitsel"], r["c"], l2(r), round(math.log2(r["bloom_fpr"]), 3)]
+                 for r in rows]
+    elif args.workload == "fig10":
+        cols = ["k", "cost", "param", "c", "bitsel", "run", "log2_fpr"]
+        table = [[r["k"], r["cost"], round(r["param"], 4), r["c"], r["bitsel"], r["run"], l2(r)] for r in rows]
+    else:
+        cols = ["k", "cost", "param", "c", "load_mean", "load_sd", "log2_fpr"]
+        table = [[r["k"], r["cost"], round(r["param"], 4), r["c"], round(r["load_mean"], 2),
+                  round(r["load_sd"], 2), l2(r)] for r in rows]
     print(json.dumps({"workload": args.workload, "points": len(rows), "keys_per_point": n,
                       "device_s": round(dev_s, 3), "wall_s": round(wall, 3),
                       "gkeys_per_s_device": round(keys_done[0] / dev_s / 1e9, 3),
-                      "gpu": torch.cuda.get_device_name()}))
+                      "gpu": torch.cuda.get_device_name(), "columns": cols, "table": table}))
 
 
 def main():

@@ -524,6 +524,15 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t);
 int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out);
 int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t);
 
+/* Launch configuration of a server's filters (applied as each is admitted,
+ * like blowchoc_set_tuning) and of its many-filter calls (like
+ * blowchoc_batch_set_tuning). Before blowchoc_server_start only; results
+ * never change. Without it, a server's filters keep their defaults except
+ * cluster_max = 16, lanes_cluster = 4, cluster_keys = 512, and its
+ * many-filter calls use the same cluster fields.
+ * Errors: EINVAL (bad fields, NULL, already started). */
+int blowchoc_server_set_tuning(blowchoc_server *s, const blowchoc_tuning *t);
+
 /*
  * blowchoc_batch_autotune -- time insert_many + query_many of `ins` / `qry`
  * on scratch copies of the filters (same parameters, empty; the callers'

@@ -112,6 +112,7 @@ _SIGS = {
     "blowchoc_server_submit": ([_VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _U64, _VP, ctypes.c_double,
                                 ctypes.POINTER(_U64)], _I),
     "blowchoc_server_start": ([_VP], _I),
+    "blowchoc_server_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
     "blowchoc_server_wait": ([_VP, ctypes.c_double], _I),
     "blowchoc_server_request_times": ([_VP, _U64, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], _I),
@@ -430,6 +431,18 @@ class Server:
             self.handle, int(fid), int(kind), h_keys.ctypes.data, len(h_keys),
             h_bitmap.ctypes.data if h_bitmap is not None else None, float(arrival_s), ctypes.byref(rid)))
         return rid.value
+
+    def set_tuning(self, **kw):
+        """Launch configuration for the server's filters and many-filter
+        calls (before start): the filter defaults with the given fields."""
+        probe = Filter(1, 1, 1)
+        try:
+            t = blowchoc_get_tuning(probe.handle)
+        finally:
+            probe.close()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(load_library().blowchoc_server_set_tuning(self.handle, ctypes.byref(t)))
 
     def start(self):
         _check(load_library().blowchoc_server_start(self.handle))

@@ -188,10 +188,17 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
     f->home = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&f->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device);
+    int l2 = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, f->device);
     if (e != cudaSuccess) {
         delete f;
         return cuda_fail(e, "no usable CUDA device");
     }
+    // measured defaults: one lane per key decides and queries fastest while
+    // the filter fits in L2 (latency dominates), two lanes beyond (HBM sectors)
+    const bool in_l2 = params->nblocks * 64ull <= (uint64_t)l2;
+    f->lanes_choose = in_l2 ? 1 : 2;
+    f->lanes_query = in_l2 ? 1 : 2;
     bc::DevFilter &d = f->dev;
     std::memset(&d, 0, sizeof d);
     d.M = params->nblocks;
@@ -514,8 +521,8 @@ int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     return BLOWCHOC_OK;
 }
 
-int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
-    if (!f || !t) return fail(BLOWCHOC_EINVAL, "NULL argument");
+// Field checks of a filter's launch configuration (blowchoc_set_tuning).
+int bc_check_tuning(const blowchoc_tuning *t) {
     auto lanes_ok = [](uint32_t l) { return l == 1 || l == 2 || l == 4 || l == 8; };
     if (!lanes_ok(t->lanes_choose) || !lanes_ok(t->lanes_set) || !lanes_ok(t->lanes_query))
         return fail(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
@@ -531,6 +538,13 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     if (t->lanes_cluster != 4 && t->lanes_cluster != 8) return fail(BLOWCHOC_EINVAL, "lanes_cluster must be 4 or 8");
     if (t->cluster_keys < 16 || t->cluster_keys > (1u << 20))
         return fail(BLOWCHOC_EINVAL, "cluster_keys must be in 16..2^20");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
+    if (!f || !t) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    const int rc = bc_check_tuning(t);
+    if (rc) return rc;
     f->lanes_choose = (int)t->lanes_choose;
     f->lanes_set = (int)t->lanes_set;
     f->lanes_query = (int)t->lanes_query;

@@ -105,20 +105,21 @@ __device__ __forceinline__ void distinct_mask(const uint64_t *amul, uint32_t k, 
     for (int j = 0; j < 8; ++j) w[j] = 0;
     for (uint32_t i = 0; i < k; ++i) {
         uint32_t r = bit_hash_range(amul[i], x, 512u - i);
-        uint32_t p = 0;
+        // word holding the r-th free position, and r's rank inside it: a
+        // branch-free scan of the words' free counts, then one select
+        uint32_t jw = 7;
+        uint64_t word = w[7];
         bool found = false;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 7; ++j) {
             const uint32_t z = 64u - (uint32_t)__popcll(w[j]);
-            if (!found) {
-                if (r < z) {
-                    p = 64u * j + select_zero64(w[j], r);
-                    found = true;
-                } else {
-                    r -= z;
-                }
-            }
+            const bool here = !found && r < z;
+            jw = here ? (uint32_t)j : jw;
+            word = here ? w[j] : word;
+            r -= (!found && !here) ? z : 0u;
+            found = found || here;
         }
+        const uint32_t p = 64u * jw + select_zero64(word, r);
 #pragma unroll
         for (int j = 0; j < 8; ++j) w[j] |= ((p >> 6) == (uint32_t)j) ? (1ull << (p & 63)) : 0ull;
     }

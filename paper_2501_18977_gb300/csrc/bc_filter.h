@@ -18,7 +18,7 @@ struct blowchoc_filter {
     cudaStream_t home = nullptr;
     int device = 0;
     int sms = 0;
-    int lanes_choose = 2, lanes_set = 4, lanes_query = 1;
+    int lanes_choose = 2, lanes_set = 4, lanes_query = 2;
     int query_early = 1;
     int ctas_per_sm = 8;
     int persistent = 1;            // insert: one cooperative launch for all batches
@@ -38,3 +38,6 @@ void bc_note_launch();
 
 // Records msg as the calling thread's last error (blowchoc_last_error); returns code.
 int bc_set_error(int code, const char *msg);
+
+// Checks the fields of a filter launch configuration; EINVAL with a message.
+extern "C" int bc_check_tuning(const blowchoc_tuning *t);

@@ -451,18 +451,34 @@ __global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
 
 inline size_t rank_bytes(int C, uint32_t k) { return C > 1 ? 513u * (k + 1) * sizeof(uint16_t) : 0; }
 
+// Lets `fn` take `sm` bytes of dynamic shared memory (the default cap is
+// 48 KB including static: the rank table of k = 32 next to a large static
+// mask region exceeds it).
+template <typename F>
+cudaError_t allow_smem(F fn, size_t sm) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+template <int C, int LANES>
+cudaError_t choose_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                          const uint16_t *rank, uint8_t *sel, unsigned long long *counters) {
+    const size_t sm = rank_bytes(C, f.k);
+    const cudaError_t e = allow_smem(choose_kernel<C, LANES>, sm);
+    if (e != cudaSuccess) return e;
+    choose_kernel<C, LANES><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters);
+    return cudaGetLastError();
+}
+
 template <int C>
 cudaError_t choose_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                             const uint16_t *rank, uint8_t *sel, unsigned long long *counters) {
-    const size_t sm = rank_bytes(C, f.k);
     switch (L.lanes) {
-        case 1: choose_kernel<C, 1><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
-        case 2: choose_kernel<C, 2><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
-        case 4: choose_kernel<C, 4><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
-        case 8: choose_kernel<C, 8><<<L.grid, kThreads, sm, L.stream>>>(f, keys, n, rank, sel, counters); break;
+        case 1: return choose_launch<C, 1>(L, f, keys, n, rank, sel, counters);
+        case 2: return choose_launch<C, 2>(L, f, keys, n, rank, sel, counters);
+        case 4: return choose_launch<C, 4>(L, f, keys, n, rank, sel, counters);
+        case 8: return choose_launch<C, 8>(L, f, keys, n, rank, sel, counters);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <int C, int LANES>
@@ -493,9 +509,10 @@ cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_
                               uint64_t B, const uint16_t *rank, uint8_t *sel,
                               unsigned long long *counters, unsigned int *bar, int sms) {
     const size_t sm = rank_bytes(C, f.k);
+    cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES>, sm);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, persistent_insert_kernel<C, LANES>, kThreads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES>, kThreads, sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int want = L.grid > 0 ? L.grid : 1;

@@ -124,6 +124,8 @@ uint64_t filter_bytes(const blowchoc_params &p) {
 struct blowchoc_server {
     blowchoc_server_config cfg;
     int device = 0;
+    bool tuned = false;                        // apply `tuning` to admitted filters
+    blowchoc_tuning tuning;
     std::vector<cudaStream_t> streams;
     std::vector<blowchoc_batch *> batches;     // one per stream
     std::vector<int> stream_inflight;
@@ -157,6 +159,19 @@ namespace {
 constexpr int kWavesPerStream = 2;
 constexpr uint64_t kHeavyRounds = 64;  // inserts needing more batches run in a wave of their own
 
+// Cluster-resident inserts in the server: moderate clusters (4 lanes per key,
+// 512 keys of a batch per CTA) for its filters and many-filter calls. Under
+// concurrent waves, smaller clusters schedule more easily than the largest
+// ones, and cluster launches keep waves clear of cooperative grid-wide
+// kernels (64 filters, 10^4 requests: 2.2 G keys/s against 0.6 with the
+// work list).
+blowchoc_tuning *server_cluster_defaults(blowchoc_tuning *t) {
+    t->cluster_max = 16;
+    t->lanes_cluster = 4;
+    t->cluster_keys = 512;
+    return t;
+}
+
 int fail_locked(blowchoc_server *s, int code, const char *what, cudaError_t e) {
     if (s->error == BLOWCHOC_OK) {
         s->error = code;
@@ -172,8 +187,16 @@ void admit(blowchoc_server *s) {
         if (sl.admitted || sl.removed) continue;
         if (s->used_bytes + sl.bytes > s->cfg.hbm_budget_bytes) break;
         blowchoc_filter *f = nullptr;
-        const int rc = blowchoc_create(&sl.params, nullptr, &f);
+        int rc = blowchoc_create(&sl.params, nullptr, &f);
+        if (!rc && s->tuned) {
+            rc = blowchoc_set_tuning(f, &s->tuning);
+        } else if (!rc) {
+            blowchoc_tuning t;
+            rc = blowchoc_get_tuning(f, &t);
+            if (!rc) rc = blowchoc_set_tuning(f, server_cluster_defaults(&t));
+        }
         if (rc) {
+            if (f) blowchoc_destroy(f);
             fail_locked(s, rc, "admitting a filter", cudaSuccess);
             return;
         }
@@ -401,7 +424,12 @@ int blowchoc_server_create(const blowchoc_server_config *cfg, blowchoc_server **
         if (e == cudaSuccess) s->streams.push_back(st);
         blowchoc_batch *b = nullptr;
         if (e == cudaSuccess && blowchoc_batch_create(&b)) e = cudaErrorMemoryAllocation;
-        if (e == cudaSuccess) s->batches.push_back(b);
+        if (e == cudaSuccess) {
+            s->batches.push_back(b);
+            blowchoc_tuning t;
+            if (blowchoc_batch_get_tuning(b, &t) || blowchoc_batch_set_tuning(b, server_cluster_defaults(&t)))
+                e = cudaErrorInvalidValue;
+        }
     }
     if (e == cudaSuccess) {
         cudaMemPoolProps props;
@@ -490,6 +518,21 @@ int blowchoc_server_submit(blowchoc_server *s, uint32_t filter_id, uint32_t kind
     s->reqs.push_back(std::move(r));
     s->outstanding++;
     s->cv_work.notify_one();
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_server_set_tuning(blowchoc_server *s, const blowchoc_tuning *t) {
+    if (!s || !t) return bc_set_error(BLOWCHOC_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->started) return bc_set_error(BLOWCHOC_EINVAL, "server already started");
+    int rc0 = bc_check_tuning(t);
+    if (rc0) return rc0;
+    for (blowchoc_batch *b : s->batches) {
+        const int rc = blowchoc_batch_set_tuning(b, t);
+        if (rc) return rc;
+    }
+    s->tuning = *t;
+    s->tuned = true;
     return BLOWCHOC_OK;
 }
 

@@ -41,8 +41,10 @@ def _alone(bc, filters, reqs, keys):
 
 
 def _serve(bc, filters, reqs, keys, budget=1 << 30, streams=3, wave=8, time_scale=1e-4,
-           remove=()):
+           remove=(), tune=None):
     srv = bc.Server(budget, staging_bytes=64 << 20, streams=streams, max_wave_requests=wave)
+    if tune:
+        srv.set_tuning(**tune)
     ids = [srv.add_filter(f["M"], 14, 2, bc.COST_MIX, 50.0, f["key_seed"], f["B"]) for f in filters]
     bms = {}
     for r in reqs:
@@ -75,6 +77,33 @@ def test_served_results_equal_alone_results():
         assert np.array_equal(served[j], bm), j
     for a, b in zip(alone_words, served_words):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tune", [dict(cluster_max=0, lanes_choose=4, lanes_query=1),
+                                  dict(cluster_max=16, lanes_cluster=4, cluster_keys=16, lanes_query=4),
+                                  dict(cluster_max=2, lanes_cluster=8, query_early=0, ctas_per_sm=3)])
+def test_server_launch_configuration_keeps_results(tune):
+    """A server-wide launch configuration (filters and many-filter calls)
+    changes no result; it is refused once the server runs."""
+    import paper_2501_18977_gb300 as bc
+    filters, reqs = _small_trace(n_filters=8, n_requests=150, seed=10)
+    keys = {r["index"]: workloads.serving_keys(filters, r, seed=10) for r in reqs}
+    alone, alone_words = _alone(bc, filters, reqs, keys)
+    served, served_words, st, _ = _serve(bc, filters, reqs, keys, time_scale=0.0, tune=tune)
+    assert st.completed == len(reqs)
+    for j, bm in alone.items():
+        assert np.array_equal(served[j], bm), j
+    for a, b in zip(alone_words, served_words):
+        assert np.array_equal(a, b)
+    srv = bc.Server(1 << 24, staging_bytes=1 << 20, streams=1, max_wave_requests=1)
+    try:
+        with pytest.raises(bc.BlowChocError):
+            srv.set_tuning(lanes_cluster=2)
+        srv.start()
+        with pytest.raises(bc.BlowChocError):
+            srv.set_tuning(**tune)
+    finally:
+        srv.close()
 
 
 def test_concurrent_waves_share_launches():
