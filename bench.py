@@ -27,7 +27,10 @@ each cost) from 20 to 6 bits per key against 10^8 negatives per point;
 one-key-at-a-time insertion; `small` times the small uniform configuration
 (10^6 keys into 2^24 bits, k = 14, two choices, cost^MIX, B = 65536 and 1);
 `learn` trains the learned cost on the small configuration's shape and
-compares its greedy filter with cost^EXP and cost^MIX on held-out keys.
+compares its greedy filter with cost^EXP and cost^MIX on held-out keys;
+`fig4`, `fig8` and `fig10` run the paper's FPR-against-size, load-histogram
+and cost-parameter sweeps at 2*10^9 keys per point (`--keys` scales them),
+with keys generated on the device.
 """
 import argparse
 import json
