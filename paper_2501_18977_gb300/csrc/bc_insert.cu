@@ -171,23 +171,14 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
 // choose phase and the set phase of a batch, and between batches, the whole
 // grid meets at a barrier, which gives exactly the batch rule above.
 
-// With `slots` > 0 each CTA keeps its keys and choices of a batch in shared
-// memory between the phases (slot t * groups-per-CTA + group for the t-th
-// key a group takes), so the set phase reads neither keys nor choices from
-// global memory; with 0 the choices go through `sel` and keys are re-read.
 template <int C, int LANES>
 __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
     DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
     const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters,
-    unsigned int *bar, uint32_t slots) {
+    unsigned int *bar) {
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
-    constexpr uint32_t GC = kThreads / LANES;  // groups per CTA
-    extern __shared__ __align__(16) uint8_t s_dyn[];
-    const size_t rank_b = C > 1 ? ((size_t)513 * (f.k + 1) * 2 + 15) & ~size_t(15) : 0;
-    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_dyn);
-    uint64_t *s_x = reinterpret_cast<uint64_t *>(s_dyn + rank_b);
-    uint8_t *s_s = reinterpret_cast<uint8_t *>(s_x + slots);
+    extern __shared__ uint16_t s_rank[];
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
     stage_bit_mults(f, s_amul);
@@ -197,7 +188,6 @@ __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
     uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t gl = threadIdx.x / LANES;
     unsigned long long *err = counters + 2;
     unsigned int target = 0;
     uint32_t ins = 0, skp = 0;
@@ -206,8 +196,7 @@ __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
         const uint64_t stride = nwarps * G;
         // the next step's key is loaded one step ahead
         uint64_t xn = warp * G + g < cnt ? load_key(keys + s0 + warp * G + g) : 0ull;
-        uint32_t slot = gl;
-        for (uint64_t base = warp * G; base < cnt; base += stride, slot += GC) {
+        for (uint64_t base = warp * G; base < cnt; base += stride) {
             const uint64_t i = base + g;
             const bool valid = i < cnt;
             const uint64_t x = xn;
@@ -215,30 +204,17 @@ __global__ void __launch_bounds__(kThreads) persistent_insert_kernel(
             uint64_t m[W];
             const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
             if (valid && q == 0) {
-                if (slots) {
-                    s_x[slot] = x;
-                    s_s[slot] = (uint8_t)s;
-                } else {
-                    sel[i] = (uint8_t)s;
-                }
+                sel[i] = (uint8_t)s;
                 if (s == kSkip) ++skp; else ++ins;
             }
         }
         target += gridDim.x;
-        if (!grid_barrier(bar, target, err)) return;  // also a CTA barrier: the staged slots are visible
-        slot = gl;
-        for (uint64_t base = warp * G; base < cnt; base += nwarps * G, slot += GC) {
+        if (!grid_barrier(bar, target, err)) return;
+        for (uint64_t base = warp * G; base < cnt; base += nwarps * G) {
             const uint64_t i = base + g;
-            uint32_t s;
-            uint64_t x;
-            if (slots) {
-                s = i < cnt ? (uint32_t)s_s[slot] : kSkip;
-                x = s != kSkip ? s_x[slot] : 0ull;
-            } else {
-                // written by other CTAs in this launch: read through L2
-                s = i < cnt ? (uint32_t)__ldcg(sel + i) : kSkip;
-                x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
-            }
+            // written by other CTAs in this launch: read through L2
+            const uint32_t s = i < cnt ? (uint32_t)__ldcg(sel + i) : kSkip;
+            const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
             key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
             if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
@@ -532,39 +508,21 @@ template <int C, int LANES>
 cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                               uint64_t B, const uint16_t *rank, uint8_t *sel,
                               unsigned long long *counters, unsigned int *bar, int sms) {
-    auto fn = persistent_insert_kernel<C, LANES>;
-    const size_t rank_b = C > 1 ? (rank_bytes(C, f.k) + 15) & ~size_t(15) : 0;
-    cudaError_t e = allow_smem(fn, rank_b);
+    const size_t sm = rank_bytes(C, f.k);
+    cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES>, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, rank_b);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES>, kThreads, sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int want = L.grid > 0 ? L.grid : 1;
     const int grid = want < per_sm * sms ? want : per_sm * sms;
-    // stage each CTA's keys and choices of a batch in shared memory when that
-    // keeps the grid co-resident
-    const uint64_t groups = (uint64_t)grid * (kThreads / LANES);
-    const uint64_t cnt = B < n ? B : n;
-    uint32_t slots = (uint32_t)(((cnt + groups - 1) / groups) * (kThreads / LANES));
-    size_t sm = rank_b + (size_t)slots * 9;
-    bool staged = sm <= 160 * 1024;
-    if (staged) {
-        e = allow_smem(fn, sm);
-        int per_sm2 = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, fn, kThreads, sm);
-        if (e != cudaSuccess) return e;
-        staged = (int64_t)per_sm2 * sms >= grid;
-    }
-    if (!staged) {
-        slots = 0;
-        sm = rank_b;
-    }
     e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), L.stream);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&f, (void *)&keys, (void *)&n, (void *)&B, (void *)&rank,
-                    (void *)&sel, (void *)&counters, (void *)&bar, (void *)&slots};
-    return cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kThreads), args, sm, L.stream);
+                    (void *)&sel, (void *)&counters, (void *)&bar};
+    return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES>, dim3(grid),
+                                       dim3(kThreads), args, sm, L.stream);
 }
 
 template <int C>
