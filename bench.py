@@ -30,7 +30,8 @@ one-key-at-a-time insertion; `small` times the small uniform configuration
 compares its greedy filter with cost^EXP and cost^MIX on held-out keys;
 `fig4`, `fig8` and `fig10` run the paper's FPR-against-size, load-histogram
 and cost-parameter sweeps at 2*10^9 keys per point (`--keys` scales them),
-with keys generated on the device.
+with keys generated on the device; `cluster` compares cluster-resident with
+global-memory inserts on serving-sized filters.
 """
 import argparse
 import json
@@ -65,7 +66,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
-                                           "learn", "fig4", "fig8", "fig10"], default="dna")
+                                           "learn", "fig4", "fig8", "fig10", "cluster"], default="dna")
     ap.add_argument("--keys", type=float, default=2e9, help="fig4/fig8/fig10: keys inserted and negatives")
     ap.add_argument("--ks", type=str, default="4,7,10,14,17,20", help="fig4/fig10: k values")
     ap.add_argument("--runs", type=int, default=1, help="fig10: repetitions with other seeds")
@@ -653,6 +654,48 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_cluster(args):
+    """Cluster-resident against global-memory insertion on serving-sized
+    filters (k = 14, c = 2, cost^MIX sigma = 50, B = 2^floor(log2(M/2)),
+    ~10^6 uniform keys each): per shape the insert time with cluster_max = 0
+    and with the defaults, and the CTAs per cluster the defaults take.
+    Results are checked equal."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    shapes = [(2075, 1024, 939473), (5808, 2048, 950901), (9022, 4096, 978426), (6250, 2048, 200000)]
+    s = torch.cuda.current_stream()
+    rows = []
+    for M, B, n in shapes:
+        keys = torch.from_numpy(workloads.uniform_keys(M, n).view(np.int64)).cuda()
+        f = bc.Filter(M, 14, 2, bc.COST_MIX, 50.0, hash_seed=3, batch=B, stream=s)
+        row = {"M": M, "B": B, "n": n, "batches": (n + B - 1) // B}
+        words = {}
+        for name, cmax in (("global", 0), ("cluster", 16)):
+            f.set_tuning(cluster_max=cmax)
+            times = []
+            for rep in range(args.warmup + args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                f.clear(s)
+                a.record(s)
+                f.insert(keys, s)
+                b.record(s)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    times.append(a.elapsed_time(b))
+            ms = statistics.median(times)
+            words[name] = f.words_host()
+            row[name + "_ms"] = round(ms, 4)
+            row[name + "_us_per_batch"] = round(ms * 1e3 / row["batches"], 2)
+        f.set_tuning(cluster_max=16)
+        row["ctas_per_cluster"] = f.cluster_ctas(n)
+        row["identical"] = bool(np.array_equal(words["global"], words["cluster"]))
+        f.close()
+        rows.append(row)
+    print(json.dumps({"workload": "cluster_resident_insert", "rows": rows,
+                      "timing": "CUDA events, median of --steps after --warmup"}))
+
+
 def run_figures(args):
     """Paper-scale FPR and load sweeps on the device (keys generated there):
     fig4 = log2 FPR vs relative size for c = 1, 2, 3 and random/distinct bits
@@ -707,6 +750,9 @@ def main():
     args = parse()
     if args.workload in ("fig4", "fig8", "fig10"):
         run_figures(args)
+        return
+    if args.workload == "cluster":
+        run_cluster(args)
         return
     if args.impl == "reference":
         run_reference(args)
