@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(kClThreads, 1)
     const int lane = threadIdx.x & 31, q = lane % LANES;
     uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + lane / LANES) * region_u32<LANES>();
     const uint32_t gl = threadIdx.x / LANES;  // group within the CTA
+    const int lead = lane & ~(LANES - 1);     // the group's first lane
+    static_assert(LANES >= C, "a group locates its candidates one per lane");
     const uint32_t T = S * TC;                // groups in the cluster
     const uint32_t gid = me * TC + gl;
     uint32_t ins = 0, skp = 0;
@@ -182,13 +184,19 @@ __global__ void __launch_bounds__(kClThreads, 1)
             const uint32_t j = p * T + gid;
             const bool valid = j < cnt;
             const uint64_t x = valid ? kb[p * TC + gl] : 0ull;
+            // lane i of the group locates candidate i once; the group shares it
+            uint32_t mine = 0;
+            if (valid && q < C) {
+                uint32_t owner, off;
+                locate((uint32_t)block_addr(f, block_mult(f, (uint32_t)q), x), owner, off);
+                mine = cluster_addr(s_words + (size_t)off * kBlockWords, owner);
+            }
             uint64_t blk[C][W];
 #pragma unroll
             for (int i = 0; i < C; ++i) {
+                const uint32_t base = __shfl_sync(kFull, mine, lead + i);
                 if (valid) {
-                    uint32_t owner, off;
-                    locate((uint32_t)block_addr(f, f.a_block[i], x), owner, off);
-                    dsmem_load<W>(cluster_addr(s_words + (size_t)off * kBlockWords + q * W, owner), blk[i]);
+                    dsmem_load<W>(base + 8u * W * q, blk[i]);
                 } else {
 #pragma unroll
                     for (int w = 0; w < W; ++w) blk[i][w] = ~0ull;
@@ -213,10 +221,14 @@ __global__ void __launch_bounds__(kClThreads, 1)
             const uint64_t x = s != kSkip ? kb[p * TC + gl] : 0ull;
             uint64_t m[W];
             key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
-            if (s != kSkip) {
+            uint32_t mine = 0;
+            if (s != kSkip && q == 0) {
                 uint32_t owner, off;
                 locate((uint32_t)block_addr(f, block_mult(f, s), x), owner, off);
-                const uint32_t a = cluster_addr(s_words + (size_t)off * kBlockWords + q * W, owner);
+                mine = cluster_addr(s_words + (size_t)off * kBlockWords, owner);
+            }
+            const uint32_t a = __shfl_sync(kFull, mine, lead) + 8u * W * q;
+            if (s != kSkip) {
 #pragma unroll
                 for (int w = 0; w < W; ++w)
                     if (m[w]) dsmem_or(a + 8u * w, m[w]);
