@@ -138,6 +138,28 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
 int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream);
 
 /*
+ * blowchoc_insert_host / blowchoc_query_host -- blowchoc_insert and
+ * blowchoc_query on HOST buffers. Keys move to the device in chunks through
+ * two device staging slots on the filter's own copy stream, so the copy of
+ * one chunk overlaps the kernels of the previous one on `stream`. Insert
+ * chunks are whole multiples of the batch size B, so the words and counters
+ * equal those of one blowchoc_insert over all n keys. Query chunks are
+ * multiples of 64 keys, and the bitmap layout is that of blowchoc_query.
+ *   h_keys    host, in, n uint64. Pinned (page-locked) memory lets copies run
+ *             asynchronously; pageable memory works but copies synchronously.
+ *   h_bitmap  host, out, ceil(n/64) uint64 words.
+ * Both calls are ordered on `stream` and return once the work is queued. The
+ * caller keeps both buffers alive and unchanged until `stream` completes;
+ * the bitmap is complete when it does. The staging (two slots of up to 2^22
+ * keys, or of one batch if B is larger) is owned by the filter and grows on
+ * demand. Growing synchronises the device.
+ * Errors: EINVAL (NULL filter, NULL buffers with n > 0), ENOMEM, ECUDA.
+ */
+int blowchoc_insert_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, void *stream);
+int blowchoc_query_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, uint64_t *h_bitmap,
+                        void *stream);
+
+/*
  * blowchoc_query -- membership of d_keys[0..n) (Section 3.1): key t is
  * reported present iff all bits of F(x) are set in at least one of its c
  * candidate blocks. No false negatives for inserted keys.

@@ -93,6 +93,8 @@ _SIGS = {
     "blowchoc_launch_count": ([], ctypes.c_uint64),
     "blowchoc_cluster_ctas": ([_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)], _I),
     "blowchoc_query_count": ([_VP, _VP, ctypes.c_uint64, _VP, _VP], _I),
+    "blowchoc_insert_host": ([_VP, _VP, ctypes.c_uint64, _VP], _I),
+    "blowchoc_query_host": ([_VP, _VP, ctypes.c_uint64, _VP, _VP], _I),
     "blowchoc_generate_keys": ([_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _VP], _I),
     "blowchoc_batch_create": ([ctypes.POINTER(_VP)], _I),
     "blowchoc_batch_destroy": ([_VP], _I),
@@ -251,6 +253,25 @@ def blowchoc_l2_residency(f, fraction, stream):
 
 def blowchoc_clear(f, stream=None):
     _check(load_library().blowchoc_clear(f, _stream(stream)))
+
+
+def _host_ptr(a):
+    """Address of a host uint64 buffer: a numpy array or a CPU torch tensor."""
+    if hasattr(a, "data_ptr"):
+        assert not a.is_cuda and a.is_contiguous() and a.element_size() == 8
+        return a.data_ptr()
+    import numpy as np
+    assert isinstance(a, np.ndarray) and a.dtype.itemsize == 8 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def blowchoc_insert_host(f, h_keys, n: int, stream=None):
+    _check(load_library().blowchoc_insert_host(f, _host_ptr(h_keys), int(n), _stream(stream)))
+
+
+def blowchoc_query_host(f, h_keys, n: int, h_bitmap, stream=None):
+    _check(load_library().blowchoc_query_host(f, _host_ptr(h_keys), int(n), _host_ptr(h_bitmap),
+                                              _stream(stream)))
 
 
 def blowchoc_query_count(f, d_keys, n: int, d_count, stream=None):
@@ -639,6 +660,23 @@ class Filter:
 
     def cluster_ctas(self, n):
         return blowchoc_cluster_ctas(self.handle, n)
+
+    def insert_host(self, keys, stream=None):
+        """Insert host keys (numpy uint64/int64 array or CPU tensor; pinned
+        memory overlaps the copies with the kernels). Ordered on `stream`:
+        keep `keys` unchanged until the stream completes."""
+        n = keys.numel() if hasattr(keys, "numel") else len(keys)
+        blowchoc_insert_host(self.handle, keys, n, stream)
+
+    def query_host(self, keys, bitmap=None, stream=None):
+        """Query host keys into a host bitmap (numpy uint64, ceil(n/64)
+        words; allocated if None). Complete once `stream` completes."""
+        import numpy as np
+        n = keys.numel() if hasattr(keys, "numel") else len(keys)
+        if bitmap is None:
+            bitmap = np.zeros(max(1, (n + 63) // 64), dtype=np.uint64)
+        blowchoc_query_host(self.handle, keys, n, bitmap, stream)
+        return bitmap
 
     def query_count(self, keys, count=None, stream=None):
         """Number of `keys` (int64 CUDA tensor) reported present. With a

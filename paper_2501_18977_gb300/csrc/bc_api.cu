@@ -194,11 +194,15 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
         delete f;
         return cuda_fail(e, "no usable CUDA device");
     }
-    // measured defaults: one lane per key decides and queries fastest while
-    // the filter fits in L2 (latency dominates), two lanes beyond (HBM sectors)
-    const bool in_l2 = params->nblocks * 64ull <= (uint64_t)l2;
-    f->lanes_choose = in_l2 ? 1 : 2;
-    f->lanes_query = in_l2 ? 1 : 2;
+    // measured defaults (one GB300, one process): inserts decide fastest with
+    // one lane per key while the filter is well inside L2 (2 MiB: 0.33 ms
+    // against 0.38 with two), with two lanes near the L2 size (128 MiB:
+    // 4.44 ms against 5.10 with one) and four beyond (512 MiB: 17.0 ms against
+    // 18.7 with two); queries with one lane while the filter fits in L2 and
+    // two beyond
+    const uint64_t bytes = params->nblocks * 64ull;
+    f->lanes_choose = bytes <= (uint64_t)l2 / 4 ? 1 : bytes <= 2ull * (uint64_t)l2 ? 2 : 4;
+    f->lanes_query = bytes <= (uint64_t)l2 ? 1 : 2;
     bc::DevFilter &d = f->dev;
     std::memset(&d, 0, sizeof d);
     d.M = params->nblocks;
@@ -417,6 +421,7 @@ int blowchoc_destroy(blowchoc_filter *f) {
     cudaFree(f->d_sel);
     cudaFree(f->d_sorted);
     cudaFree(f->d_resv);
+    bc_free_host_stage(f);
     delete f;
     if (e != cudaSuccess) return cuda_fail(e, "blowchoc_destroy");
     return BLOWCHOC_OK;

@@ -1,0 +1,139 @@
+// Insert and query from host buffers: the keys move to the device in chunks
+// through two staging slots on a copy stream, so that the copy of chunk i + 1
+// overlaps the kernels of chunk i on the caller's stream. Insert chunks are
+// whole multiples of the filter's batch size B, so that the batch sequence is
+// exactly that of one blowchoc_insert over all keys (each call starts its
+// batches at its first key, and every chunk edge is a batch edge). Query
+// chunks are multiples of 64 keys, so that each chunk's bitmap is a run of
+// whole words of the caller's bitmap.
+#include <cstdio>
+#include <cstring>
+
+#include "bc_filter.h"
+
+namespace {
+
+constexpr uint64_t kHostChunkKeys = 1ull << 22;  // about 32 MB of keys per slot
+
+int cuda_fail(cudaError_t e, const char *what) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    return bc_set_error(e == cudaErrorMemoryAllocation ? BLOWCHOC_ENOMEM : BLOWCHOC_ECUDA, msg);
+}
+
+#define HOST_CUDA(call, what)                              \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Staging of at least `chunk` keys per slot (and chunk / 64 bitmap words).
+int ensure_stage(blowchoc_filter *f, uint64_t chunk) {
+    blowchoc_filter::HostStage &h = f->host;
+    if (!h.copy) {
+        HOST_CUDA(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking), "copy stream");
+        for (int i = 0; i < 2; ++i) {
+            HOST_CUDA(cudaEventCreateWithFlags(&h.copied[i], cudaEventDisableTiming), "staging events");
+            HOST_CUDA(cudaEventCreateWithFlags(&h.used[i], cudaEventDisableTiming), "staging events");
+            HOST_CUDA(cudaEventCreateWithFlags(&h.drained[i], cudaEventDisableTiming), "staging events");
+        }
+        HOST_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming), "staging events");
+    }
+    if (h.chunk >= chunk) return BLOWCHOC_OK;
+    HOST_CUDA(cudaStreamSynchronize(h.copy), "staging resize");
+    HOST_CUDA(cudaDeviceSynchronize(), "staging resize");  // earlier kernels may still read the old slots
+    cudaFree(h.d_keys);
+    cudaFree(h.d_bitmap);
+    h.d_keys = nullptr;
+    h.d_bitmap = nullptr;
+    h.chunk = 0;
+    HOST_CUDA(cudaMalloc(&h.d_keys, 2 * chunk * sizeof(uint64_t)), "staging keys");
+    HOST_CUDA(cudaMalloc(&h.d_bitmap, 2 * (chunk / 64) * sizeof(uint64_t)), "staging bitmap");
+    h.chunk = chunk;
+    return BLOWCHOC_OK;
+}
+
+}  // namespace
+
+void bc_free_host_stage(blowchoc_filter *f) {
+    blowchoc_filter::HostStage &h = f->host;
+    if (h.copy) cudaStreamSynchronize(h.copy);
+    cudaFree(h.d_keys);
+    cudaFree(h.d_bitmap);
+    for (int i = 0; i < 2; ++i) {
+        if (h.copied[i]) cudaEventDestroy(h.copied[i]);
+        if (h.used[i]) cudaEventDestroy(h.used[i]);
+        if (h.drained[i]) cudaEventDestroy(h.drained[i]);
+    }
+    if (h.done) cudaEventDestroy(h.done);
+    if (h.copy) cudaStreamDestroy(h.copy);
+    h = blowchoc_filter::HostStage();
+}
+
+extern "C" {
+
+int blowchoc_insert_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, void *stream) {
+    if (!f) return bc_set_error(BLOWCHOC_EINVAL, "filter is NULL");
+    if (n == 0) return BLOWCHOC_OK;
+    if (!h_keys) return bc_set_error(BLOWCHOC_EINVAL, "keys are NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t B = f->p.batch;
+    // whole batches per chunk; a batch larger than the chunk is one chunk
+    uint64_t chunk = B >= kHostChunkKeys ? B : (kHostChunkKeys / B) * B;
+    if (chunk > n) chunk = n;
+    int rc = ensure_stage(f, chunk);
+    if (rc) return rc;
+    blowchoc_filter::HostStage &h = f->host;
+    for (uint64_t off = 0, i = 0; off < n; off += chunk, ++i) {
+        const int slot = (int)(i & 1);
+        const uint64_t cnt = n - off < chunk ? n - off : chunk;
+        uint64_t *dst = h.d_keys + (uint64_t)slot * h.chunk;
+        HOST_CUDA(cudaStreamWaitEvent(h.copy, h.used[slot], 0), "staging order");
+        HOST_CUDA(cudaMemcpyAsync(dst, h_keys + off, cnt * sizeof(uint64_t), cudaMemcpyHostToDevice, h.copy),
+                  "keys to the device");
+        HOST_CUDA(cudaEventRecord(h.copied[slot], h.copy), "staging order");
+        HOST_CUDA(cudaStreamWaitEvent(s, h.copied[slot], 0), "staging order");
+        rc = blowchoc_insert(f, dst, cnt, s);
+        if (rc) return rc;
+        HOST_CUDA(cudaEventRecord(h.used[slot], s), "staging order");
+    }
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_query_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, uint64_t *h_bitmap, void *stream) {
+    if (!f) return bc_set_error(BLOWCHOC_EINVAL, "filter is NULL");
+    if (n == 0) return BLOWCHOC_OK;
+    if (!h_keys || !h_bitmap) return bc_set_error(BLOWCHOC_EINVAL, "keys or bitmap is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t chunk = kHostChunkKeys;  // a multiple of 64
+    int rc = ensure_stage(f, chunk < n ? chunk : ((n + 63) / 64) * 64);
+    if (rc) return rc;
+    blowchoc_filter::HostStage &h = f->host;
+    chunk = h.chunk / 64 * 64;  // a slot may be larger (an insert sized it to whole batches)
+    for (uint64_t off = 0, i = 0; off < n; off += chunk, ++i) {
+        const int slot = (int)(i & 1);
+        const uint64_t cnt = n - off < chunk ? n - off : chunk;
+        uint64_t *dk = h.d_keys + (uint64_t)slot * h.chunk;
+        uint64_t *db = h.d_bitmap + (uint64_t)slot * (h.chunk / 64);
+        HOST_CUDA(cudaStreamWaitEvent(h.copy, h.used[slot], 0), "staging order");
+        HOST_CUDA(cudaMemcpyAsync(dk, h_keys + off, cnt * sizeof(uint64_t), cudaMemcpyHostToDevice, h.copy),
+                  "keys to the device");
+        HOST_CUDA(cudaEventRecord(h.copied[slot], h.copy), "staging order");
+        HOST_CUDA(cudaStreamWaitEvent(s, h.copied[slot], 0), "staging order");
+        HOST_CUDA(cudaStreamWaitEvent(s, h.drained[slot], 0), "staging order");  // the slot's last bitmap is out
+        rc = blowchoc_query(f, dk, cnt, db, s);
+        if (rc) return rc;
+        HOST_CUDA(cudaEventRecord(h.used[slot], s), "staging order");
+        HOST_CUDA(cudaStreamWaitEvent(h.copy, h.used[slot], 0), "staging order");
+        HOST_CUDA(cudaMemcpyAsync(h_bitmap + off / 64, db, (cnt + 63) / 64 * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, h.copy),
+                  "bitmap to the host");
+        HOST_CUDA(cudaEventRecord(h.drained[slot], h.copy), "staging order");
+    }
+    // the caller's stream completes only after the last bitmap reached the host
+    HOST_CUDA(cudaEventRecord(h.done, h.copy), "staging order");
+    HOST_CUDA(cudaStreamWaitEvent(s, h.done, 0), "staging order");
+    return BLOWCHOC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+"""Insert and query from host buffers (blowchoc_insert_host /
+blowchoc_query_host) give exactly what the device-buffer calls give: the
+chunked copies through staging slots keep every batch edge, and the bitmap
+layout is the same, for pinned and pageable memory, ragged lengths, batch
+sizes that do not divide the chunk and a batch larger than the chunk. The
+results are also the oracle's."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import COST_MIX, COST_EXP, OracleFilter
+from oracle.oracle import GOLDEN_RATIO
+from tests.gpu_helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _host(a, pinned):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
+    return t.pin_memory() if pinned else a
+
+
+@pytest.mark.parametrize("M,k,c,B,n,pinned", [
+    (4096, 14, 2, 65536, 1000003, True),      # several chunks of whole batches
+    (3000, 12, 3, 1000, 5000001, True),       # B not dividing 2^22: chunks of 4,194,000 keys
+    (777, 9, 2, 1, 200001, False),            # one key at a time, pageable memory
+    (8192, 16, 3, 5 << 20, 12 << 20, True),   # one batch larger than a chunk
+    (100, 7, 1, 64, 63, False),               # fewer keys than a bitmap word
+])
+def test_host_buffers_equal_device_buffers(M, k, c, B, n, pinned):
+    import torch
+    import paper_2501_18977_gb300 as bc
+    keys = workloads.uniform_keys(M + n, n)
+    queries = np.concatenate([keys[: n // 2], workloads.uniform_keys(M + n + 1, n // 2 + 7)])
+    a = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=5, batch=B)
+    b = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=5, batch=B)
+    try:
+        s = torch.cuda.current_stream()
+        hk, hq = _host(keys, pinned), _host(queries, pinned)
+        a.insert_host(hk, s)
+        bm_host = a.query_host(hq, stream=s)
+        s.synchronize()
+        b.insert(to_dev(keys))
+        bm_dev = b.query(to_dev(queries)).cpu().numpy().view(np.uint64)
+        assert np.array_equal(a.words_host(), b.words_host())
+        assert np.array_equal(bm_host[: len(bm_dev)], bm_dev)
+        sa, sb = a.stats(), b.stats()
+        assert (sa.inserted, sa.skipped) == (sb.inserted, sb.skipped)
+    finally:
+        a.close()
+        b.close()
+    if n <= 300000:
+        o = OracleFilter(M, k, c, COST_EXP, GOLDEN_RATIO, seed=5, batch=B)
+        o.insert(keys)
+        assert np.array_equal(bm_host[: (len(queries) + 63) // 64], o.query(queries))
+
+
+def test_host_calls_reuse_staging_across_calls_and_streams():
+    """Back-to-back host calls on two streams of one filter, with the caller
+    ordering the streams, build the same filter as one device call."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    M, k, c, B = 2048, 14, 2, 4096
+    keys = workloads.uniform_keys(99, 3000000)
+    f = bc.Filter(M, k, c, COST_MIX, 50.0, hash_seed=1, batch=B)
+    g = bc.Filter(M, k, c, COST_MIX, 50.0, hash_seed=1, batch=B)
+    try:
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        h = _host(keys, True)
+        f.insert_host(h[:1000000], s1)
+        s2.wait_stream(s1)
+        f.insert_host(h[1000000:], s2)
+        s2.synchronize()
+        g.insert(to_dev(keys[:1000000]))
+        g.insert(to_dev(keys[1000000:]))
+        assert np.array_equal(f.words_host(), g.words_host())
+    finally:
+        f.close()
+        g.close()
