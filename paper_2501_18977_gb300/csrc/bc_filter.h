@@ -31,18 +31,7 @@ struct blowchoc_filter {
     int cluster_max = 16;          // cluster-resident insert: CTAs per cluster at most (0: off)
     int lanes_cluster = 8;
     int cluster_keys = 128;        // keys of a batch per CTA the cluster size aims for
-    // host-buffer entry points: two device staging slots, a copy stream and
-    // the events that order the slots between it and the caller's stream
-    struct HostStage {
-        uint64_t *d_keys = nullptr;    // 2 x chunk keys
-        uint64_t *d_bitmap = nullptr;  // 2 x chunk / 64 words
-        uint64_t chunk = 0;            // keys per slot
-        cudaStream_t copy = nullptr;
-        cudaEvent_t copied[2] = {nullptr, nullptr};   // keys of the slot are on the device
-        cudaEvent_t used[2] = {nullptr, nullptr};     // the slot's keys were consumed
-        cudaEvent_t drained[2] = {nullptr, nullptr};  // the slot's bitmap was copied out
-        cudaEvent_t done = nullptr;                   // the copy stream's last work
-    } host;
+    struct HostStage *host = nullptr;  // host-buffer calls' staging (bc_host.cu), made on first use
 };
 
 // Frees the host-buffer staging of f (synchronises its copy stream).

@@ -1,6 +1,7 @@
 // Insert and query from host buffers: the keys move to the device in chunks
 // through two staging slots on a copy stream, so that the copy of chunk i + 1
-// overlaps the kernels of chunk i on the caller's stream. Insert chunks are
+// overlaps the kernels of chunk i on the caller's stream; query bitmaps come
+// back on a second stream, so that they never queue in front of keys. Insert chunks are
 // whole multiples of the filter's batch size B, so that the batch sequence is
 // exactly that of one blowchoc_insert over all keys (each call starts its
 // batches at its first key, and every chunk edge is a batch edge). Query
@@ -10,6 +11,21 @@
 #include <cstring>
 
 #include "bc_filter.h"
+
+// Staging of the host-buffer calls: two device slots, a stream for keys to
+// the device, one for bitmaps back, and the events that order the slots
+// between those streams and the caller's stream.
+struct HostStage {
+    uint64_t *d_keys = nullptr;    // 2 x chunk keys
+    uint64_t *d_bitmap = nullptr;  // 2 x chunk / 64 words
+    uint64_t chunk = 0;            // keys per slot
+    cudaStream_t copy = nullptr;   // keys to the device
+    cudaStream_t back = nullptr;   // bitmaps to the host (its own queue, so that it never holds up keys)
+    cudaEvent_t copied[2] = {nullptr, nullptr};   // keys of the slot are on the device
+    cudaEvent_t used[2] = {nullptr, nullptr};     // the slot's keys were consumed
+    cudaEvent_t drained[2] = {nullptr, nullptr};  // the slot's bitmap was copied out
+    cudaEvent_t done = nullptr;                   // the bitmap stream's last work
+};
 
 namespace {
 
@@ -29,9 +45,11 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // Staging of at least `chunk` keys per slot (and chunk / 64 bitmap words).
 int ensure_stage(blowchoc_filter *f, uint64_t chunk) {
-    blowchoc_filter::HostStage &h = f->host;
+    if (!f->host) f->host = new HostStage();
+    HostStage &h = *f->host;
     if (!h.copy) {
         HOST_CUDA(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking), "copy stream");
+        HOST_CUDA(cudaStreamCreateWithFlags(&h.back, cudaStreamNonBlocking), "copy stream");
         for (int i = 0; i < 2; ++i) {
             HOST_CUDA(cudaEventCreateWithFlags(&h.copied[i], cudaEventDisableTiming), "staging events");
             HOST_CUDA(cudaEventCreateWithFlags(&h.used[i], cudaEventDisableTiming), "staging events");
@@ -41,6 +59,7 @@ int ensure_stage(blowchoc_filter *f, uint64_t chunk) {
     }
     if (h.chunk >= chunk) return BLOWCHOC_OK;
     HOST_CUDA(cudaStreamSynchronize(h.copy), "staging resize");
+    HOST_CUDA(cudaStreamSynchronize(h.back), "staging resize");
     HOST_CUDA(cudaDeviceSynchronize(), "staging resize");  // earlier kernels may still read the old slots
     cudaFree(h.d_keys);
     cudaFree(h.d_bitmap);
@@ -56,8 +75,10 @@ int ensure_stage(blowchoc_filter *f, uint64_t chunk) {
 }  // namespace
 
 void bc_free_host_stage(blowchoc_filter *f) {
-    blowchoc_filter::HostStage &h = f->host;
+    if (!f->host) return;
+    HostStage &h = *f->host;
     if (h.copy) cudaStreamSynchronize(h.copy);
+    if (h.back) cudaStreamSynchronize(h.back);
     cudaFree(h.d_keys);
     cudaFree(h.d_bitmap);
     for (int i = 0; i < 2; ++i) {
@@ -67,7 +88,9 @@ void bc_free_host_stage(blowchoc_filter *f) {
     }
     if (h.done) cudaEventDestroy(h.done);
     if (h.copy) cudaStreamDestroy(h.copy);
-    h = blowchoc_filter::HostStage();
+    if (h.back) cudaStreamDestroy(h.back);
+    delete f->host;
+    f->host = nullptr;
 }
 
 extern "C" {
@@ -83,7 +106,7 @@ int blowchoc_insert_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n,
     if (chunk > n) chunk = n;
     int rc = ensure_stage(f, chunk);
     if (rc) return rc;
-    blowchoc_filter::HostStage &h = f->host;
+    HostStage &h = *f->host;
     for (uint64_t off = 0, i = 0; off < n; off += chunk, ++i) {
         const int slot = (int)(i & 1);
         const uint64_t cnt = n - off < chunk ? n - off : chunk;
@@ -108,7 +131,7 @@ int blowchoc_query_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, 
     uint64_t chunk = kHostChunkKeys;  // a multiple of 64
     int rc = ensure_stage(f, chunk < n ? chunk : ((n + 63) / 64) * 64);
     if (rc) return rc;
-    blowchoc_filter::HostStage &h = f->host;
+    HostStage &h = *f->host;
     chunk = h.chunk / 64 * 64;  // a slot may be larger (an insert sized it to whole batches)
     for (uint64_t off = 0, i = 0; off < n; off += chunk, ++i) {
         const int slot = (int)(i & 1);
@@ -124,14 +147,14 @@ int blowchoc_query_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, 
         rc = blowchoc_query(f, dk, cnt, db, s);
         if (rc) return rc;
         HOST_CUDA(cudaEventRecord(h.used[slot], s), "staging order");
-        HOST_CUDA(cudaStreamWaitEvent(h.copy, h.used[slot], 0), "staging order");
+        HOST_CUDA(cudaStreamWaitEvent(h.back, h.used[slot], 0), "staging order");
         HOST_CUDA(cudaMemcpyAsync(h_bitmap + off / 64, db, (cnt + 63) / 64 * sizeof(uint64_t),
-                                  cudaMemcpyDeviceToHost, h.copy),
+                                  cudaMemcpyDeviceToHost, h.back),
                   "bitmap to the host");
-        HOST_CUDA(cudaEventRecord(h.drained[slot], h.copy), "staging order");
+        HOST_CUDA(cudaEventRecord(h.drained[slot], h.back), "staging order");
     }
     // the caller's stream completes only after the last bitmap reached the host
-    HOST_CUDA(cudaEventRecord(h.done, h.copy), "staging order");
+    HOST_CUDA(cudaEventRecord(h.done, h.back), "staging order");
     HOST_CUDA(cudaStreamWaitEvent(s, h.done, 0), "staging order");
     return BLOWCHOC_OK;
 }
