@@ -507,6 +507,10 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       earliest key wins each block) and the keys that won all of theirs
  *       decide and set their bits; such keys share no candidate block with
  *       any earlier pending key. 0 = one warp inserting key after key.
+ *       Batches of 2..16 keys (of a filter that does not run
+ *       cluster-resident) use the same rounds with whole batches in place
+ *       of keys, over windows of seq_window keys rounded to whole batches
+ *       (at least four); 0 = one CTA running the batches one after another.
  *   cluster_max: an insert of at least 4 batches (B >= 2) into a filter
  *       that fits in the shared memory of one thread-block cluster runs
  *       cluster-resident: the cluster's CTAs hold the filter's words (a

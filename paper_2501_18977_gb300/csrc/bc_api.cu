@@ -298,6 +298,19 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
             return BLOWCHOC_OK;
         }
     }
+    if (B <= bc::kSeqMaxBatch && f->seq_window > 0 && n > B) {
+        // small batches of a filter beyond one cluster: reservation rounds
+        // over windows of whole batches
+        uint64_t window = (uint64_t)f->seq_window / B * B;
+        if (window < 4 * B) window = 4 * B;
+        if (window > bc::kSeqMaxWindow) window = bc::kSeqMaxWindow / B * B;
+        if (!f->d_resv)
+            BC_CUDA(cudaMalloc(&f->d_resv, f->dev.M * sizeof(unsigned long long)), "cudaMalloc(reservations)");
+        BC_CUDA(counted(bc::launch_exact_batched(C, s, f->dev, d_keys, n, B, (uint32_t)window, f->d_rank,
+                                                 f->d_counters, f->d_resv)),
+                "batched insert launch");
+        return BLOWCHOC_OK;
+    }
     if (B <= bc::kSingleCtaBatch || (!f->persistent && B <= bc::kSmallBatchMax)) {
         bc::Launch L{1, f->lanes_choose, s};
         BC_CUDA(counted(bc::launch_small_batch(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_counters)),

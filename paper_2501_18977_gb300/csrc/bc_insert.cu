@@ -456,6 +456,106 @@ __global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
     flush_counts(ins, skp, counters);
 }
 
+// Batches of B > 1 keys (batch-synchronous: a batch decides against the
+// state at its start, then sets) with the same reservation rounds, a batch
+// taking the place of a key: every key of a pending batch reserves its
+// candidate blocks with (round << 32 | ~batch), and a batch commits when all
+// its keys hold all of their reservations. Then no earlier pending batch
+// shares a candidate block with it, its keys decide against the current
+// filter, and only after all of them decided do they set their bits. Batches
+// that commit in the same round touch disjoint blocks. The outcome is that of
+// inserting the batches one after another. The window holds whole batches.
+template <int C, int LANES>
+__global__ void __launch_bounds__(kSeqThreads) exact_batched_kernel(
+    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint32_t B, uint32_t window,
+    const uint16_t *__restrict__ rank_g, unsigned long long *counters, unsigned long long *resv) {
+    constexpr int G = 32 / LANES;
+    constexpr int W = kBlockWords / LANES;
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    const uint32_t wpad = (window + 15) & ~15u;
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(s_dyn);  // window keys
+    uint8_t *s_state = s_dyn + (size_t)window * 8;           // 1 = pending (per key)
+    uint8_t *s_sel = s_state + wpad;                         // choices of a committing batch
+    uint8_t *s_ok = s_sel + wpad;                            // per batch: every key holds its reservations
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_ok + wpad);
+    __shared__ uint64_t s_amul[32];
+    __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * G * region_u32<LANES>()];
+    __shared__ int s_left;
+    stage_bit_mults(f, s_amul);
+    const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
+    if constexpr (C == 1) __syncthreads();
+    const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
+    const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t ins = 0, skp = 0;
+    uint64_t round = 0;
+    for (uint64_t s0 = 0; s0 < n; s0 += window) {
+        const uint32_t cnt = (uint32_t)((n - s0) < window ? (n - s0) : window);
+        const uint32_t nb = (cnt + B - 1) / B;
+        for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+            s_key[t] = load_key(keys + s0 + t);
+            s_state[t] = 1;
+        }
+        __syncthreads();
+        for (;;) {
+            ++round;
+            for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) s_ok[b] = 1;
+            // reserve: the earliest pending batch wins each candidate block
+            for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+                if (!s_state[t]) continue;
+                const unsigned long long tag = ((unsigned long long)round << 32) | (unsigned long long)(~(t / B));
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    atomicMax(resv + block_addr(f, f.a_block[c], s_key[t]), tag);
+            }
+            __syncthreads();
+            // every thread has read the previous round's s_left before this barrier
+            if (threadIdx.x == 0) s_left = 0;
+            // a batch with a key that lost one of its blocks waits for a later round
+            for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+                if (!s_state[t]) continue;
+                const unsigned long long tag = ((unsigned long long)round << 32) | (unsigned long long)(~(t / B));
+                bool won = true;
+#pragma unroll
+                for (int c = 0; c < C; ++c) won = won && __ldcg(resv + block_addr(f, f.a_block[c], s_key[t])) == tag;
+                if (!won) s_ok[t / B] = 0;
+            }
+            __syncthreads();
+            // the committing batches decide against the current filter ...
+            for (uint32_t base = wib * G; base < cnt; base += wpc * G) {
+                const uint32_t t = base + g;
+                const bool ready = t < cnt && s_state[t] && s_ok[t / B];
+                const uint64_t x = ready ? s_key[t] : 0ull;
+                uint64_t m[W];
+                const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, ready, q, rank, s_amul, region, m);
+                if (ready && q == 0) s_sel[t] = (uint8_t)s;
+            }
+            __syncthreads();
+            // ... and set their bits only after all of them decided
+            for (uint32_t base = wib * G; base < cnt; base += wpc * G) {
+                const uint32_t t = base + g;
+                const bool ready = t < cnt && s_state[t] && s_ok[t / B];
+                const uint32_t s = ready ? (uint32_t)s_sel[t] : kSkip;
+                const uint64_t x = ready ? s_key[t] : 0ull;
+                uint64_t m[W];
+                key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
+                if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
+                if (ready && q == 0) {
+                    if (s == kSkip) ++skp; else ++ins;
+                }
+            }
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+                if (s_state[t] && s_ok[t / B]) s_state[t] = 0;
+                else if (s_state[t]) s_left = 1;
+            }
+            __syncthreads();
+            if (!s_left) break;
+        }
+    }
+    flush_counts(ins, skp, counters);
+}
+
 inline size_t rank_bytes(int C, uint32_t k) { return C > 1 ? 513u * (k + 1) * sizeof(uint16_t) : 0; }
 
 // Lets `fn` take `sm` bytes of dynamic shared memory (the default cap is
@@ -596,7 +696,33 @@ cudaError_t exact_seq_launch(cudaStream_t s, const DevFilter &f, const uint64_t 
     return cudaGetLastError();
 }
 
+template <int C, int LANES>
+cudaError_t exact_batched_launch(cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n, uint32_t B,
+                                 uint32_t window, const uint16_t *rank, unsigned long long *counters,
+                                 unsigned long long *resv) {
+    const size_t wpad = (window + 15) & ~15u;
+    const size_t sm = (size_t)window * 8 + 3 * wpad + rank_bytes(C, f.k);
+    cudaError_t e = allow_smem(exact_batched_kernel<C, LANES>, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(resv, 0, f.M * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    exact_batched_kernel<C, LANES><<<1, kSeqThreads, sm, s>>>(f, keys, n, B, window, rank, counters, resv);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_exact_batched(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                 uint64_t B, uint32_t window, const uint16_t *rank, unsigned long long *counters,
+                                 unsigned long long *resv) {
+    if (B < 2 || B > kSeqMaxBatch || window < B || window > kSeqMaxWindow || window % B) return cudaErrorInvalidValue;
+    switch (C) {
+        case 1: return exact_batched_launch<1, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
+        case 2: return exact_batched_launch<2, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
+        case 3: return exact_batched_launch<3, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_exact_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n,
                                     uint32_t window, const uint16_t *rank, unsigned long long *counters,

@@ -54,6 +54,13 @@ cudaError_t launch_exact_sequential(int C, cudaStream_t s, const DevFilter &f, c
                                     uint32_t window, const uint16_t *rank, unsigned long long *counters,
                                     unsigned long long *resv);
 
+// 2 <= B <= kSeqMaxBatch, exactly, by the same reservation rounds with a
+// batch in place of a key; window is a multiple of B in B..kSeqMaxWindow.
+constexpr uint64_t kSeqMaxBatch = 16;  // measured: beyond, the one-CTA batch loop is faster
+cudaError_t launch_exact_batched(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                                 uint64_t B, uint32_t window, const uint16_t *rank, unsigned long long *counters,
+                                 unsigned long long *resv);
+
 // B = 1: one warp inserts the keys strictly one after another.
 cudaError_t launch_sequential(int C, cudaStream_t s, const DevFilter &f, const uint64_t *keys,
                               uint64_t n, const uint16_t *rank, unsigned long long *counters);

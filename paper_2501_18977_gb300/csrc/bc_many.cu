@@ -287,7 +287,7 @@ struct blowchoc_batch {
     ManyPlan live_ins, live_qry, rec_ins, rec_qry;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int lanes_choose = 2, lanes_query = 1, query_early = 1, ctas_per_sm = 8;
+    int lanes_choose = 1, lanes_query = 1, query_early = 1, ctas_per_sm = 8;  // one lane per key: 14.3 ms against 18.7 (256 filters)
     // cluster-resident items are off by default here: a work list of many
     // filters spreads every round over all SMs, which measured faster than one
     // cluster per filter (256 lognormal filters: 18.3 ms against 20.8-33 ms)

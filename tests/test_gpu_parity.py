@@ -258,3 +258,34 @@ def test_exact_sequential_insert_matches_oracle(M, k, c, kind, par, n, window, d
     assert np.array_equal(words, o.words)
     assert np.array_equal(bm, obm)
     assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
+
+
+@pytest.mark.parametrize("M,k,c,kind,par,B,n,window,dups", [
+    (65536, 12, 2, COST_EXP, PHI, 16, 60000, 2048, False),
+    (70001, 14, 3, COST_MIX, 50.0, 7, 30001, 2048, True),     # odd B, repeated keys, ragged end
+    (4096, 16, 2, COST_LA, 3.5, 16, 40000, 64, False),        # windows of four batches
+    (1, 5, 2, COST_MIX, 50.0, 2, 3000, 64, False),            # one block: every batch waits for the last
+    (9000, 11, 1, COST_EXP, PHI, 3, 50000, 2048, False),
+    (300, 20, 3, COST_EXP, PHI, 13, 20000, 8192, True),
+])
+def test_exact_batched_insert_matches_oracle(M, k, c, kind, par, B, n, window, dups):
+    """Small batches through reservation rounds over whole batches equal the
+    oracle's batch-after-batch insertion (cluster-resident path off)."""
+    import paper_2501_18977_gb300 as bc
+    keys = workloads.uniform_keys(M + 11, n)
+    if dups:
+        keys = keys[np.random.default_rng(M).integers(0, max(n // 20, 1), n)]
+    queries = np.concatenate([keys[:n // 2], workloads.uniform_keys(M + 12, n // 2)])
+    f = bc.Filter(M, k, c, kind, par, hash_seed=4, batch=B)
+    try:
+        f.set_tuning(seq_window=window, cluster_max=0)
+        f.insert(to_dev(keys))
+        bm = f.query(to_dev(queries)).cpu().numpy().view(np.uint64)
+        words = f.words_host()
+        st = f.stats()
+    finally:
+        f.close()
+    o, obm, _, _ = oracle_run(M, k, c, kind, par, 4, B, keys, queries)
+    assert np.array_equal(words, o.words)
+    assert np.array_equal(bm, obm)
+    assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
