@@ -317,7 +317,7 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
                 "small-batch insert launch");
         return BLOWCHOC_OK;
     }
-    int rc = ensure_sel(f, std::min(B, n));
+    int rc = ensure_sel(f, 2 * std::min(B, n));  // the persistent insert keeps two bytes per key
     if (rc) return rc;
     if (f->persistent) {
         const uint64_t per = std::min(B, n);

@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kThreads, persistent_min_ctas<LANES>()) persis
     uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint16_t *sel16 = reinterpret_cast<uint16_t *>(sel);  // choice | words with new bits << 8
     unsigned long long *err = counters + 2;
     unsigned int target = 0;
     uint32_t ins = 0, skp = 0;
@@ -209,9 +210,17 @@ __global__ void __launch_bounds__(kThreads, persistent_min_ctas<LANES>()) persis
             const uint64_t x = xn;
             xn = i + stride < cnt ? load_key(keys + s0 + i + stride) : 0ull;
             uint64_t m[W];
-            const uint32_t s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
+            // with 1 or 2 lanes per key, only words with new bits are OR-ed in
+            // later (measured 1.4-4% faster); wider groups OR every word, which
+            // measured faster for them (the flags cost registers)
+            uint32_t words = 0xFFu;
+            uint32_t s;
+            if constexpr (LANES <= 2)
+                s = choose_key_words<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m, words);
+            else
+                s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
             if (valid && q == 0) {
-                sel[i] = (uint8_t)s;
+                sel16[i] = (uint16_t)(s | (words << 8));
                 if (s == kSkip) ++skp; else ++ins;
             }
         }
@@ -220,11 +229,12 @@ __global__ void __launch_bounds__(kThreads, persistent_min_ctas<LANES>()) persis
         for (uint64_t base = warp * G; base < cnt; base += nwarps * G) {
             const uint64_t i = base + g;
             // written by other CTAs in this launch: read through L2
-            const uint32_t s = i < cnt ? (uint32_t)__ldcg(sel + i) : kSkip;
+            const uint32_t sw = i < cnt ? (uint32_t)__ldcg(sel16 + i) : kSkip;
+            const uint32_t s = sw & 0xFFu;
             const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
             key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
-            if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
+            if (s != kSkip) set_words<LANES>(f, block_addr(f, block_mult(f, s), x), q, m, sw >> 8);
         }
         if (s0 + B < n) {
             target += gridDim.x;

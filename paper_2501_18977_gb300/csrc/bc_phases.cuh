@@ -73,6 +73,57 @@ __device__ __forceinline__ uint32_t choose_key(const DevFilter &f, uint64_t x, b
     return choose_from_terms<C>(la, rank, f.k + 1);
 }
 
+// choose_key that also reports which of the chosen block's eight words get
+// new bits (bit w of *words: word w of the key's mask has bits the block
+// lacked at the batch start). Bits set then stay set, so a word without new
+// bits needs no OR in the set phase.
+template <int C, int LANES, int PATH>
+__device__ __forceinline__ uint32_t choose_key_words(const DevFilter &f, uint64_t x, bool valid, int q,
+                                                     const uint16_t *rank, const uint64_t *s_amul, uint32_t *region,
+                                                     uint64_t (&m)[kBlockWords / LANES], uint32_t &words) {
+    constexpr int W = kBlockWords / LANES;
+    uint64_t blk[C][W];
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const uint64_t b = block_addr(f, f.a_block[i], x);
+        if (valid) {
+            load_words<W, PATH>(f.words + b * kBlockWords + (uint64_t)q * W, blk[i]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) blk[i][j] = ~0ull;
+        }
+    }
+    key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
+    uint32_t la[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) la[i] = group_sum<LANES>(load_and_new<W>(blk[i], m));
+    const uint32_t s = choose_from_terms<C>(la, rank, f.k + 1);
+    uint32_t v = 0;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        if ((uint32_t)i == s) {
+#pragma unroll
+            for (int j = 0; j < W; ++j) v |= (m[j] & ~blk[i][j]) ? (1u << (q * W + j)) : 0u;
+        }
+    }
+#pragma unroll
+    for (int sh = LANES / 2; sh > 0; sh >>= 1) v |= __shfl_xor_sync(kFull, v, sh, LANES);
+    words = v;
+    return s;
+}
+
+// set_one restricted to the words flagged in `words` (bit w = word w).
+template <int LANES>
+__device__ __forceinline__ void set_words(const DevFilter &f, uint64_t b, int q, const uint64_t (&m)[kBlockWords / LANES],
+                                          uint32_t words) {
+    constexpr int W = kBlockWords / LANES;
+    unsigned long long *dst =
+        reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + (uint64_t)q * W);
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if ((words >> (q * W + j)) & 1u) atomicOr(dst + j, (unsigned long long)m[j]);
+}
+
 // OR of the key's bits into block b: lane q of the group owns W words.
 template <int LANES>
 __device__ __forceinline__ void set_one(const DevFilter &f, uint64_t b, int q,
