@@ -154,12 +154,20 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# sources that define each profiled kernel and its launch configuration
+# sources that define each profiled kernel, and the launch-configuration
+# fields that select its instance and grid
 KERNEL_SOURCES = {
-    "persistent_insert_kernel": ["bc_insert.cu", "bc_phases.cuh", "bc_device.cuh", "bc_launch.h", "bc_api.cu",
-                                 "bc_filter.h"],
-    "query_kernel": ["bc_query.cu", "bc_phases.cuh", "bc_device.cuh", "bc_launch.h", "bc_api.cu", "bc_filter.h"],
+    "persistent_insert_kernel": ["bc_insert.cu", "bc_phases.cuh", "bc_device.cuh", "bc_launch.h"],
+    "query_kernel": ["bc_query.cu", "bc_phases.cuh", "bc_device.cuh", "bc_launch.h"],
 }
+KERNEL_LAUNCH_FIELDS = {
+    "persistent_insert_kernel": ["lanes_choose", "ctas_per_sm", "keys_per_cta", "persistent", "set_mode"],
+    "query_kernel": ["lanes_query", "query_early", "ctas_per_sm"],
+}
+
+
+def launch_config(tuning, kernel):
+    return {k: int(getattr(tuning, k)) for k in KERNEL_LAUNCH_FIELDS[kernel]}
 
 
 def sources_sha256(names):
@@ -172,9 +180,10 @@ def sources_sha256(names):
     return h.hexdigest()
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, tuning):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
-    None if the kernel's sources changed since it was taken."""
+    None if the kernel's sources or its launch configuration (`tuning`'s
+    fields that choose the instance and grid) differ from the capture's."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -183,6 +192,8 @@ def ncu_traffic(kernel):
     if kernel not in d or kernel not in KERNEL_SOURCES:
         return None
     if d[kernel].get("sources_sha256") != sources_sha256(KERNEL_SOURCES[kernel]):
+        return None
+    if d[kernel].get("launch") != launch_config(tuning, kernel):
         return None
     return d[kernel]["dram_bytes_per_launch"]
 
@@ -920,7 +931,7 @@ def main():
     dominant = "query_kernel" if qry_ms >= ins_ms else "persistent_insert_kernel"
     dom_ms = qry_ms if dominant == "query_kernel" else ins_ms
     dom_gbs = q_gbs if dominant == "query_kernel" else i_gbs
-    traffic = ncu_traffic(dominant)
+    traffic = ncu_traffic(dominant, f.tuning())
     ceil_filter = gather_ceiling(bc, torch, CONFIG["nblocks"])
     ceil_hbm = gather_ceiling(bc, torch, 1 << 26)
     out = {
