@@ -152,7 +152,9 @@ int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  * caller keeps both buffers alive and unchanged until `stream` completes;
  * the bitmap is complete when it does. The staging (two slots of up to 2^22
  * keys, or of one batch if B is larger) is owned by the filter and grows on
- * demand. Growing synchronises the device.
+ * demand. Growing synchronises the device. Host-buffer calls on one filter
+ * share that staging: issue them from one host thread at a time (any
+ * streams may be used; the staging events order the slots between them).
  * Errors: EINVAL (NULL filter, NULL buffers with n > 0), ENOMEM, ECUDA.
  */
 int blowchoc_insert_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, void *stream);
