@@ -61,8 +61,9 @@ __global__ void __launch_bounds__(kThreads) set_kernel(DevFilter f, const uint64
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t base = warp * G; base < n; base += nwarps * G) {
         const uint64_t i = base + g;
+        // the key is loaded beside the choice, not after it
         const uint32_t s = i < n ? (uint32_t)sel[i] : kSkip;
-        const uint64_t x = s != kSkip ? load_key(keys + i) : 0ull;
+        const uint64_t x = i < n ? load_key(keys + i) : 0ull;
         uint64_t m[W];
         key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
         if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
         for (uint32_t base = warp * G; base < cnt; base += nwarps * G) {
             const uint32_t i = base + g;
             const uint32_t s = i < cnt ? (uint32_t)sel[i] : kSkip;
-            const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
+            const uint64_t x = i < cnt ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
             key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
             if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
@@ -226,12 +227,17 @@ __global__ void __launch_bounds__(kThreads, persistent_min_ctas<LANES>()) persis
         }
         target += gridDim.x;
         if (!grid_barrier(bar, target, err)) return;
-        for (uint64_t base = warp * G; base < cnt; base += nwarps * G) {
+        // the choice (written by other CTAs in this launch: read through L2)
+        // and the key are loaded one step ahead
+        uint32_t swn = warp * G + g < cnt ? (uint32_t)__ldcg(sel16 + warp * G + g) : kSkip;
+        uint64_t xs = warp * G + g < cnt ? load_key(keys + s0 + warp * G + g) : 0ull;
+        for (uint64_t base = warp * G; base < cnt; base += stride) {
             const uint64_t i = base + g;
-            // written by other CTAs in this launch: read through L2
-            const uint32_t sw = i < cnt ? (uint32_t)__ldcg(sel16 + i) : kSkip;
+            const uint32_t sw = swn;
+            const uint64_t x = xs;
+            swn = i + stride < cnt ? (uint32_t)__ldcg(sel16 + i + stride) : kSkip;
+            xs = i + stride < cnt ? load_key(keys + s0 + i + stride) : 0ull;
             const uint32_t s = sw & 0xFFu;
-            const uint64_t x = s != kSkip ? load_key(keys + s0 + i) : 0ull;
             uint64_t m[W];
             key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
             if (s != kSkip) set_words<LANES>(f, block_addr(f, block_mult(f, s), x), q, m, sw >> 8);
@@ -300,8 +306,8 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
         // count keys per range
         for (uint64_t i = tid; i < cnt_b; i += nthreads) {
             const uint32_t s = __ldcg(sel + i);
-            if (s == kSkip) continue;
             const uint64_t x = load_key(bk + i);
+            if (s == kSkip) continue;
             atomicAdd(cnt + (uint32_t)(block_addr(f, block_mult(f, s), x) / kRangeBlocks), 1u);
         }
         target += gridDim.x;
@@ -336,8 +342,8 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
         // scatter key indices into their ranges
         for (uint64_t i = tid; i < cnt_b; i += nthreads) {
             const uint32_t s = __ldcg(sel + i);
-            if (s == kSkip) continue;
             const uint64_t x = load_key(bk + i);
+            if (s == kSkip) continue;
             const uint32_t r = (uint32_t)(block_addr(f, block_mult(f, s), x) / kRangeBlocks);
             perm[__ldcg(off + r) + atomicAdd(cur + r, 1u)] = (uint32_t)i;
         }

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
                         }
                     } else {
                         const uint32_t s = base + g < cnt ? (uint32_t)__ldcg(it->sel + (i - bstart)) : kSkip;
-                        const uint64_t x = s != kSkip ? load_key(it->keys + i) : 0ull;
+                        const uint64_t x = base + g < cnt ? load_key(it->keys + i) : 0ull;
                         uint64_t m[W];
                         key_mask_shared<LANES>(s_amul[wib], f.k, x, q, region, m, f.bitsel);
                         if (s != kSkip) set_one<LANES>(f, block_addr(f, block_mult(f, s), x), q, m);
