@@ -484,7 +484,7 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *   lanes_choose, lanes_set, lanes_query: lanes of a warp that share one key
  *       (1, 2, 4 or 8); each lane owns 8/lanes words of every 512-bit block.
  *       Defaults follow the filter's size against the device's L2:
- *       lanes_choose 1 up to L2/4, 2 up to 2 x L2, 4 beyond; lanes_query 1
+ *       lanes_choose 4 up to L2/2, 2 up to 2 x L2, 4 beyond; lanes_query 1
  *       up to L2, 2 beyond.
  *   query_early: 1 = load candidate i+1 only if the key was not found in
  *       candidates 1..i (fewer block reads for members); 0 = load all first;
@@ -500,7 +500,10 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       run in one CTA with CTA barriers, B = 1 in one warp.
  *   keys_per_cta: grid of the persistent insert, as keys of one batch per
  *       CTA (grid = ceil(min(B, n) / keys_per_cta), at most ctas_per_sm CTAs
- *       per SM): fewer CTAs make the barriers of small batches cheaper.
+ *       per SM, at most what is co-resident). The default, 64, spreads a
+ *       batch of up to about 40,000 keys over one CTA per 64 keys and gives
+ *       larger batches the whole co-resident grid; larger values trade
+ *       parallelism for fewer CTAs at each grid barrier.
  *   set_mode: how the persistent insert ORs a batch in: 0 = 64-bit atomic OR
  *       of each key's words at L2; 1 = sort by block: bucket the batch's keys
  *       by ranges of 256 blocks, stage each touched range in shared memory,

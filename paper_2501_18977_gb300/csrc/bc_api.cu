@@ -194,14 +194,15 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
         delete f;
         return cuda_fail(e, "no usable CUDA device");
     }
-    // measured defaults (one GB300, one process): inserts decide fastest with
-    // one lane per key while the filter is well inside L2 (2 MiB: 0.33 ms
-    // against 0.38 with two), with two lanes near the L2 size (128 MiB:
-    // 4.44 ms against 5.10 with one) and four beyond (512 MiB: 17.0 ms against
-    // 18.7 with two); queries with one lane while the filter fits in L2 and
-    // two beyond
+    // measured defaults (one GB300, one process, persistent insert over a
+    // full grid): inserts decide fastest with four lanes per key up to half
+    // the L2 size (4 MiB, B = 4096: 3.6 ms against 5.0 with one lane; 64 MiB,
+    // B = 2^18: 3.27 ms against 3.74 with two), with two lanes near the L2
+    // size (128 MiB: 7.41 ms against 7.63 with four) and four beyond
+    // (512 MiB: 39.3 ms against 46.4 with two); queries with one lane while
+    // the filter fits in L2 and two beyond
     const uint64_t bytes = params->nblocks * 64ull;
-    f->lanes_choose = bytes <= (uint64_t)l2 / 4 ? 1 : bytes <= 2ull * (uint64_t)l2 ? 2 : 4;
+    f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4 : bytes <= 2ull * (uint64_t)l2 ? 2 : 4;
     f->lanes_query = bytes <= (uint64_t)l2 ? 1 : 2;
     bc::DevFilter &d = f->dev;
     std::memset(&d, 0, sizeof d);
