@@ -700,9 +700,10 @@ def run_reference(args):
 def run_cluster(args):
     """Cluster-resident against global-memory insertion on serving-sized
     filters (k = 14, c = 2, cost^MIX sigma = 50, B = 2^floor(log2(M/2)),
-    ~10^6 uniform keys each): per shape the insert time with cluster_max = 0
-    and with the defaults, and the CTAs per cluster the defaults take.
-    Results are checked equal."""
+    ~10^6 uniform keys each): per shape the insert time of the global-memory
+    kernels (cluster_max = 0) and of the cluster-resident kernel (persistent
+    insert off, so that every shape qualifies), the CTAs per cluster, and the
+    path the defaults take. Results are checked equal."""
     import torch
     import paper_2501_18977_gb300 as bc
     shapes = [(2075, 1024, 939473), (5808, 2048, 950901), (9022, 4096, 978426), (6250, 2048, 200000)]
@@ -713,8 +714,11 @@ def run_cluster(args):
         f = bc.Filter(M, 14, 2, bc.COST_MIX, 50.0, hash_seed=3, batch=B, stream=s)
         row = {"M": M, "B": B, "n": n, "batches": (n + B - 1) // B}
         words = {}
-        for name, cmax in (("global", 0), ("cluster", 16)):
-            f.set_tuning(cluster_max=cmax)
+        # the cluster arm turns the persistent insert off so that batches
+        # above 2048 keys run cluster-resident too (by default they take the
+        # persistent insert, which is faster there)
+        for name, cmax, pers in (("global", 0, 1), ("cluster", 16, 0)):
+            f.set_tuning(cluster_max=cmax, persistent=pers)
             times = []
             for rep in range(args.warmup + args.steps):
                 a = torch.cuda.Event(enable_timing=True)
@@ -730,8 +734,9 @@ def run_cluster(args):
             words[name] = f.words_host()
             row[name + "_ms"] = round(ms, 4)
             row[name + "_us_per_batch"] = round(ms * 1e3 / row["batches"], 2)
-        f.set_tuning(cluster_max=16)
         row["ctas_per_cluster"] = f.cluster_ctas(n)
+        f.set_tuning(cluster_max=16, persistent=1)
+        row["default_path"] = "cluster" if f.cluster_ctas(n) else "global"
         row["identical"] = bool(np.array_equal(words["global"], words["cluster"]))
         f.close()
         rows.append(row)

@@ -248,9 +248,16 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
 namespace {
 
 // Shape of the cluster-resident insert for n keys, S = 0 if not taken.
+// The cluster-resident insert replaces the global-memory kernels where those
+// run a batch in one CTA (B <= 2048) or in two launches (persistent off).
+// Against the persistent insert over the whole grid it lost from B = 4096
+// on (one GB300, ~10^6 keys, 8,192 to 45,000 blocks: 1.72 ms against 1.41
+// at B = 4096, 1.45 against 0.74 at B = 8192), and won 1.6 to 5 times at
+// B = 512 to 2048.
 bc::ClusterShape cluster_plan(const blowchoc_filter *f, uint64_t n) {
     const uint64_t B = f->p.batch;
     if (f->cluster_max == 0 || B < 2 || n == 0 || (n + B - 1) / B < bc::kClusterMinRounds) return bc::ClusterShape();
+    if (f->persistent && B > bc::kSingleCtaBatch) return bc::ClusterShape();
     return bc::cluster_shape((int)f->p.choices, f->lanes_cluster, f->dev.M, f->dev.k, std::min(B, n),
                              f->cluster_max, (uint64_t)f->cluster_keys);
 }

@@ -251,6 +251,13 @@ __device__ __forceinline__ uint64_t load_key(const uint64_t *p) {
     return __ldcs(reinterpret_cast<const unsigned long long *>(p));
 }
 
+// 64-bit OR at L2 as a reduction that returns nothing: the set phases never
+// read the old value. Through atomicOr, ncu counted these as returning
+// atomics (no reductions) and the DNA insert took 4.33 ms against 3.74.
+__device__ __forceinline__ void red_or(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Sum of v over the LANES lanes of this lane's group (butterfly).
 template <int LANES>
 __device__ __forceinline__ uint32_t group_sum(uint32_t v) {

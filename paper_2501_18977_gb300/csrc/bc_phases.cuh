@@ -121,7 +121,7 @@ __device__ __forceinline__ void set_words(const DevFilter &f, uint64_t b, int q,
         reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + (uint64_t)q * W);
 #pragma unroll
     for (int j = 0; j < W; ++j)
-        if ((words >> (q * W + j)) & 1u) atomicOr(dst + j, (unsigned long long)m[j]);
+        if ((words >> (q * W + j)) & 1u) red_or(dst + j, (unsigned long long)m[j]);
 }
 
 // OR of the key's bits into block b: lane q of the group owns W words.
@@ -133,7 +133,7 @@ __device__ __forceinline__ void set_one(const DevFilter &f, uint64_t b, int q,
         reinterpret_cast<unsigned long long *>(f.words + b * kBlockWords + (uint64_t)q * W);
 #pragma unroll
     for (int j = 0; j < W; ++j)
-        if (m[j]) atomicOr(dst + j, (unsigned long long)m[j]);
+        if (m[j]) red_or(dst + j, (unsigned long long)m[j]);
 }
 
 // Sums two per-thread counters over the CTA and adds them to counters[0..1].

@@ -45,7 +45,9 @@ def test_cluster_insert_matches_oracle(M, k, c, kind, par, B, n, bitsel, cmax, l
     queries = np.concatenate([keys[: n // 2], workloads.uniform_keys(M * 3 + k + 1, n // 2)])
     f = bc.Filter(M, k, c, kind, par, hash_seed=M + 5, batch=B, bitsel=bitsel)
     try:
-        f.set_tuning(cluster_max=cmax, lanes_cluster=lanes)
+        # batches above 2048 keys run cluster-resident only with the
+        # persistent insert off
+        f.set_tuning(cluster_max=cmax, lanes_cluster=lanes, persistent=0 if B > 2048 else 1)
         S = f.cluster_ctas(n)
         if S == 0 and M > 20000:
             pytest.skip("the device co-schedules no cluster large enough")
@@ -89,7 +91,7 @@ def test_cluster_insert_continues_a_filter():
 
 def test_cluster_shape_limits():
     """Filters beyond the cluster's shared memory are not planned; the plan
-    follows cluster_max."""
+    follows cluster_max and the batch size."""
     import paper_2501_18977_gb300 as bc
     big = bc.Filter(1 << 20, 14, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=1024)
     small = bc.Filter(1000, 14, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=512)
@@ -106,6 +108,13 @@ def test_cluster_shape_limits():
         wide.set_tuning(cluster_max=1, lanes_cluster=8)
         assert wide.cluster_ctas(1 << 20) == 0           # eight passes per batch: grid-wide kernels
         wide.close()
+        # batches above 2048 keys take the persistent insert over the whole
+        # grid unless it is off
+        mid = bc.Filter(9022, 14, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=4096)
+        assert mid.cluster_ctas(1 << 20) == 0
+        mid.set_tuning(persistent=0)
+        assert mid.cluster_ctas(1 << 20) >= 1
+        mid.close()
     finally:
         big.close()
         small.close()
