@@ -173,14 +173,20 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
 // grid meets at a barrier, which gives exactly the batch rule above.
 
 // Registers per thread: one lane per key keeps three whole candidate blocks
-// in registers (128, two CTAs per SM); wider groups are held to 64 so that
-// four CTAs fit per SM, which measured 13% faster on an L2-sized filter than
-// letting them take 95 registers.
+// in registers (128; two 256-thread CTAs per SM). Wider groups are held to 64
+// registers so that 32 warps fit per SM, which measured 13% faster on an
+// L2-sized filter than letting them take 95 registers. They run as two
+// 512-thread CTAs per SM: against four of 256 threads, half as many CTAs
+// meet at each grid barrier, and the DNA insert measured 1-3% faster and a
+// 2 MiB filter's 8% (1024-thread CTAs: 4% faster with four lanes, 3% slower
+// with two).
 template <int LANES>
-constexpr int persistent_min_ctas() { return LANES == 1 ? 2 : 4; }
+constexpr int persistent_threads() { return LANES == 1 ? 256 : 512; }
+template <int LANES>
+constexpr int persistent_min_ctas() { return LANES == 1 ? 2 : 1024 / persistent_threads<LANES>(); }
 
 template <int C, int LANES>
-__global__ void __launch_bounds__(kThreads, persistent_min_ctas<LANES>()) persistent_insert_kernel(
+__global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ctas<LANES>()) persistent_insert_kernel(
     DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
     const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters,
     unsigned int *bar) {
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, persistent_min_ctas<LANES>()) persis
     constexpr int W = kBlockWords / LANES;
     extern __shared__ uint16_t s_rank[];
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(persistent_threads<LANES>() / 32) * G * region_u32<LANES>()];
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
@@ -635,7 +641,7 @@ cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_
     cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES>, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES>, kThreads, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES>, persistent_threads<LANES>(), sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int want = L.grid > 0 ? L.grid : 1;
@@ -645,7 +651,7 @@ cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_
     void *args[] = {(void *)&f, (void *)&keys, (void *)&n, (void *)&B, (void *)&rank,
                     (void *)&sel, (void *)&counters, (void *)&bar};
     return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES>, dim3(grid),
-                                       dim3(kThreads), args, sm, L.stream);
+                                       dim3(persistent_threads<LANES>()), args, sm, L.stream);
 }
 
 template <int C>
