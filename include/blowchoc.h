@@ -500,8 +500,8 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       run in one CTA with CTA barriers, B = 1 in one warp.
  *   keys_per_cta: grid of the persistent insert, as keys of one batch per
  *       CTA (grid = ceil(min(B, n) / keys_per_cta), at most ctas_per_sm CTAs
- *       per SM, at most what is co-resident). The default, 64, spreads a
- *       batch of up to about 20,000 keys over one CTA per 64 keys and gives
+ *       per SM, at most what is co-resident). The default, 128, spreads a
+ *       batch of up to about 39,000 keys over one CTA per 128 keys and gives
  *       larger batches the whole co-resident grid (two 512-thread CTAs per
  *       SM with 2 to 8 lanes per key, two of 256 threads with one); larger
  *       values trade parallelism for fewer CTAs at each grid barrier.

@@ -195,12 +195,12 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
         return cuda_fail(e, "no usable CUDA device");
     }
     // measured defaults (one GB300, one process, persistent insert over a
-    // full grid): inserts decide fastest with four lanes per key up to half
-    // the L2 size (4 MiB, B = 4096: 3.6 ms against 5.0 with one lane; 64 MiB,
-    // B = 2^18: 3.27 ms against 3.74 with two), with two lanes near the L2
-    // size (128 MiB: 7.41 ms against 7.63 with four) and four beyond
-    // (512 MiB: 39.3 ms against 46.4 with two); queries with one lane while
-    // the filter fits in L2 and two beyond
+    // full grid, B = 2^20, 12 bits per key): inserts decide fastest with four
+    // lanes per key up to half the L2 size (2 MiB: 0.112 ms against 0.134
+    // with one lane; 64 MiB, three choices: 3.07 ms against 3.20 with two),
+    // with two lanes near the L2 size (128 MiB: 6.36 ms against 6.50 with
+    // four) and four beyond (512 MiB: 38.9 ms against 48.6 with two); queries
+    // with one lane while the filter fits in L2 and two beyond
     const uint64_t bytes = params->nblocks * 64ull;
     f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4 : bytes <= 2ull * (uint64_t)l2 ? 2 : 4;
     f->lanes_query = bytes <= (uint64_t)l2 ? 1 : 2;

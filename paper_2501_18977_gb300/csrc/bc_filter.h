@@ -22,7 +22,7 @@ struct blowchoc_filter {
     int query_early = 1;
     int ctas_per_sm = 8;
     int persistent = 1;            // insert: one cooperative launch for all batches
-    int keys_per_cta = 64;         // persistent insert grid: keys of a batch per CTA
+    int keys_per_cta = 128;        // persistent insert grid: keys of a batch per CTA
     int set_mode = 0;              // 0: atomic OR at L2; 1: sort by block range
     uint32_t *d_sorted = nullptr;  // sort-by-block scratch (3 R + 1 + batch u32)
     uint64_t sorted_cap = 0;
