@@ -506,10 +506,10 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       SM with 2 to 8 lanes per key, two of 256 threads with one); larger
  *       values trade parallelism for fewer CTAs at each grid barrier.
  *   set_mode: how the persistent insert ORs a batch in: 0 = 64-bit atomic OR
- *       of each key's words at L2; 1 = sort by block: bucket the batch's keys
- *       by ranges of 256 blocks, stage each touched range in shared memory,
- *       OR there, write the range back (offered while ceil(M / 256) <= 65536;
- *       larger filters use 0).
+ *       reductions (no value returned) of each key's words at L2; 1 = sort by
+ *       block: bucket the batch's keys by ranges of 256 blocks, stage each
+ *       touched range in shared memory, OR there, write the range back
+ *       (offered while ceil(M / 256) <= 65536; larger filters use 0).
  *   seq_window: B = 1 (one key at a time) runs in parallel while staying
  *       exactly sequential: windows of seq_window keys (32..8192) go through
  *       rounds in which every pending key reserves its candidate blocks (the
