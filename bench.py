@@ -31,7 +31,9 @@ compares its greedy filter with cost^EXP and cost^MIX on held-out keys;
 `fig4`, `fig8` and `fig10` run the paper's FPR-against-size, load-histogram
 and cost-parameter sweeps at 2*10^9 keys per point (`--keys` scales them),
 with keys generated on the device; `cluster` compares cluster-resident with
-global-memory inserts on serving-sized filters.
+global-memory inserts on serving-sized filters; `lanes` times the persistent
+insert with 1, 2, 4 and 8 lanes per key for filters of 2 MiB to 512 MiB (the
+measurements behind the default lanes per filter size).
 """
 import argparse
 import json
@@ -66,7 +68,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
-                                           "learn", "fig4", "fig8", "fig10", "cluster"], default="dna")
+                                           "learn", "fig4", "fig8", "fig10", "cluster", "lanes"], default="dna")
     ap.add_argument("--keys", type=float, default=2e9, help="fig4/fig8/fig10: keys inserted and negatives")
     ap.add_argument("--ks", type=str, default="4,7,10,14,17,20", help="fig4/fig10: k values")
     ap.add_argument("--runs", type=int, default=1, help="fig10: repetitions with other seeds")
@@ -744,6 +746,52 @@ def run_cluster(args):
                       "timing": "CUDA events, median of --steps after --warmup"}))
 
 
+def run_lanes(args):
+    """Persistent insert time per lanes_choose across filter sizes: uniform
+    device-generated keys at 12 bits per key, B = 2^20, cluster path off, two
+    shapes (three choices, k = 16, cost^LA; two choices, k = 12, cost^EXP).
+    Per row the median of --steps timed inserts after one warm-up, the
+    fastest lane width and the default; the words must not depend on it."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    s = torch.cuda.current_stream()
+    phi = (1 + 5 ** 0.5) / 2
+    rows = []
+    for mib in (2, 8, 32, 64, 96, 128, 192, 256, 512):
+        M = mib * (1 << 20) // 64
+        n = M * 512 // 12
+        keys = bc.generate_keys(n, 7)
+        for c, k, cost, par, cname in ((3, 16, bc.COST_LA, 3.5, "LA"), (2, 12, bc.COST_EXP, phi, "EXP")):
+            f = bc.Filter(M, k, c, cost, par, hash_seed=5, batch=1 << 20, stream=s)
+            default = f.tuning().lanes_choose
+            f.set_tuning(cluster_max=0)
+            row = {"filter_mib": mib, "M": M, "n": n, "c": c, "k": k, "cost": cname, "default": default}
+            digests = set()
+            for lanes in (1, 2, 4, 8):
+                f.set_tuning(lanes_choose=lanes)
+                times = []
+                for rep in range(1 + max(1, args.steps)):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    f.clear(s)
+                    a.record(s)
+                    f.insert(keys, s)
+                    b.record(s)
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(a.elapsed_time(b))
+                row["lanes%d_ms" % lanes] = round(statistics.median(times), 4)
+                digests.add(int(f.words_view().sum().item()))
+            row["best"] = min((1, 2, 4, 8), key=lambda ln: row["lanes%d_ms" % ln])
+            row["identical"] = len(digests) == 1
+            f.close()
+            rows.append(row)
+        del keys
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "insert_lanes_by_filter_size", "B": 1 << 20, "bits_per_key": 12,
+                      "rows": rows, "timing": "CUDA events, median of --steps after one warm-up"}))
+
+
 def run_figures(args):
     """Paper-scale FPR and load sweeps on the device (keys generated there):
     fig4 = log2 FPR vs relative size for c = 1, 2, 3 and random/distinct bits
@@ -801,6 +849,9 @@ def main():
         return
     if args.workload == "cluster":
         run_cluster(args)
+        return
+    if args.workload == "lanes":
+        run_lanes(args)
         return
     if args.impl == "reference":
         run_reference(args)

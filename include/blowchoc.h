@@ -484,8 +484,8 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *   lanes_choose, lanes_set, lanes_query: lanes of a warp that share one key
  *       (1, 2, 4 or 8); each lane owns 8/lanes words of every 512-bit block.
  *       Defaults follow the filter's size against the device's L2:
- *       lanes_choose 4 up to L2/2, 2 up to 2 x L2, 4 beyond; lanes_query 1
- *       up to L2, 2 beyond.
+ *       lanes_choose 4 up to L2/2, 2 up to 1.5 x L2, 4 beyond; lanes_query
+ *       1 up to L2, 2 beyond.
  *   query_early: 1 = load candidate i+1 only if the key was not found in
  *       candidates 1..i (fewer block reads for members); 0 = load all first;
  *       2 = load the first two up front, later ones only while not found

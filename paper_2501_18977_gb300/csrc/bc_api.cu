@@ -194,15 +194,16 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
         delete f;
         return cuda_fail(e, "no usable CUDA device");
     }
-    // measured defaults (one GB300, one process, persistent insert over a
-    // full grid, B = 2^20, 12 bits per key): inserts decide fastest with four
-    // lanes per key up to half the L2 size (2 MiB: 0.112 ms against 0.134
-    // with one lane; 64 MiB, three choices: 3.07 ms against 3.20 with two),
-    // with two lanes near the L2 size (128 MiB: 6.36 ms against 6.50 with
-    // four) and four beyond (512 MiB: 38.9 ms against 48.6 with two); queries
-    // with one lane while the filter fits in L2 and two beyond
+    // measured defaults (one GB300 with 129 MiB of L2, one process, persistent
+    // insert over a full grid, B = 2^20, 12 bits per key): inserts decide
+    // fastest with four lanes per key up to half the L2 size (2 MiB: 0.112 ms
+    // against 0.131 with one lane; 64 MiB, three choices: 3.07 ms against 3.21
+    // with two), with two lanes up to 1.5 times the L2 size (128 MiB: 6.36 ms
+    // against 6.50 with four; 192 MiB: 11.46 against 11.75) and four beyond
+    // (256 MiB: 15.85 ms against 17.71 with two; 512 MiB: 38.9 against 48.5);
+    // queries with one lane while the filter fits in L2 and two beyond
     const uint64_t bytes = params->nblocks * 64ull;
-    f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4 : bytes <= 2ull * (uint64_t)l2 ? 2 : 4;
+    f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4 : bytes <= 3ull * (uint64_t)l2 / 2 ? 2 : 4;
     f->lanes_query = bytes <= (uint64_t)l2 ? 1 : 2;
     bc::DevFilter &d = f->dev;
     std::memset(&d, 0, sizeof d);
