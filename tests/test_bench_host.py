@@ -1,0 +1,77 @@
+"""Host-side checks of the benchmark's measurement bookkeeping.
+
+The roofline's DRAM traffic comes from a committed ncu capture and may only be
+reported while the kernel that was captured is the kernel that runs: the same
+sources and the same launch configuration. These tests pin that guard on a
+scratch copy of the bookkeeping, and that the committed record names the
+sources and launch fields the benchmark checks.
+"""
+import json
+import os
+
+import pytest
+
+import bench
+from paper_2501_18977_gb300.binding import blowchoc_tuning
+
+
+def _scratch_root(tmp_path, text="kernel v1"):
+    csrc = tmp_path / "paper_2501_18977_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text(text)
+    (tmp_path / "profiles").mkdir()
+    return csrc
+
+
+def _tuning(**kw):
+    t = blowchoc_tuning()
+    for k, v in dict(lanes_choose=2, ctas_per_sm=8, keys_per_cta=128, persistent=1, set_mode=0,
+                     lanes_query=1, query_early=1).items():
+        setattr(t, k, kw.get(k, v))
+    return t
+
+
+@pytest.fixture
+def scratch(tmp_path, monkeypatch):
+    csrc = _scratch_root(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.KERNEL_SOURCES, "persistent_insert_kernel", ["k.cu"])
+    record = {"kernels": {"persistent_insert_kernel": {
+        "dram_bytes_per_launch": 123456789,
+        "launch": bench.launch_config(_tuning(), "persistent_insert_kernel"),
+        "sources": ["k.cu"],
+        "sources_sha256": bench.sources_sha256(["k.cu"]),
+    }}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(record))
+    return csrc
+
+
+def test_traffic_reported_for_the_captured_kernel(scratch):
+    assert bench.ncu_traffic("persistent_insert_kernel", _tuning()) == 123456789
+
+
+def test_traffic_dropped_when_a_source_changes(scratch):
+    (scratch / "k.cu").write_text("kernel v2")
+    assert bench.ncu_traffic("persistent_insert_kernel", _tuning()) is None
+
+
+@pytest.mark.parametrize("field,value", [("lanes_choose", 4), ("keys_per_cta", 64), ("set_mode", 1),
+                                         ("persistent", 0), ("ctas_per_sm", 4)])
+def test_traffic_dropped_when_the_launch_differs(scratch, field, value):
+    assert bench.ncu_traffic("persistent_insert_kernel", _tuning(**{field: value})) is None
+
+
+def test_traffic_absent_for_an_uncaptured_kernel(scratch):
+    assert bench.ncu_traffic("query_kernel", _tuning()) is None
+
+
+def test_committed_record_matches_the_guard():
+    path = os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")
+    with open(path) as fh:
+        kernels = json.load(fh)["kernels"]
+    for name, entry in kernels.items():
+        assert entry["sources"] == bench.KERNEL_SOURCES[name]
+        assert sorted(entry["launch"]) == sorted(bench.KERNEL_LAUNCH_FIELDS[name])
+        assert entry["dram_bytes_per_launch"] > 0
+        for field in entry["launch"]:
+            assert hasattr(blowchoc_tuning(), field)
