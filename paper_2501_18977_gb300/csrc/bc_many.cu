@@ -22,7 +22,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint64_t kTile = 512;  // keys per insert tile
+// Keys per insert tile: one tile per warp at the grid's 1024 keys of a round
+// per CTA. Tiles of 512 keys left three warps in four idle and measured
+// 13.8 ms for the 256-filter workload against 11.7 with 128 (64: 11.8).
+constexpr uint64_t kTile = 128;
 
 // Index of the tile's item: the last f with prefix[f] <= t (prefix has
 // nitems + 1 ascending entries, prefix[0] = 0).
