@@ -217,6 +217,20 @@ int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit)
 int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs);
 
 /*
+ * blowchoc_cost_ranks -- the integer ranks the choose kernels compare in
+ * place of the costs of Eq. 4-6 (Section 3.2, Appendix A): for block load
+ * L = 0..512 and new bits a = 0..k with L + a <= 512, ranks[L * (k + 1) + a]
+ * is the position of cost(j = L + a, a) among the distinct values of all
+ * reachable costs, evaluated in IEEE double (equal costs share a rank), so
+ * that comparing ranks is comparing the doubles. Unreachable entries
+ * (L + a > 512) hold 0xFFFF. Host-only: needs no device. `ranks` is a host
+ * array of `capacity` >= 513 (k + 1) entries owned by the caller.
+ * Errors: EINVAL (NULL, k outside 1..32, unknown cost kind, a parameter that
+ * is not finite, negative, or zero for cost^EXP, capacity too small).
+ */
+int blowchoc_cost_ranks(int cost, double cost_param, uint32_t k, uint16_t *ranks, uint64_t capacity);
+
+/*
  * blowchoc_l2_residency -- keep part of the filter's words resident in L2
  * for the kernels later queued on `stream` (a created stream, not NULL):
  * sets aside fraction x the device's maximum persisting L2 for this process

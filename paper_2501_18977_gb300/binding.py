@@ -88,6 +88,7 @@ _SIGS = {
     "blowchoc_write_words": ([_VP, _U64, _U64, _VP], _I),
     "blowchoc_clear": ([_VP, _VP], _I),
     "blowchoc_set_cost_table": ([_VP, _VP], _I),
+    "blowchoc_cost_ranks": ([ctypes.c_int, ctypes.c_double, ctypes.c_uint32, _VP, ctypes.c_uint64], _I),
     "blowchoc_l2_residency": ([_VP, ctypes.c_double, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
@@ -245,6 +246,15 @@ def blowchoc_set_cost_table(f, costs):
     import numpy as np
     c = np.ascontiguousarray(costs, dtype=np.float64)
     _check(load_library().blowchoc_set_cost_table(f, c.ctypes.data))
+
+
+def blowchoc_cost_ranks(cost: int, cost_param: float, k: int):
+    """The host-side rank table of the costs (numpy uint16, 513 * (k + 1)
+    entries, index L * (k + 1) + a; 0xFFFF where L + a > 512)."""
+    import numpy as np
+    out = np.empty(513 * (int(k) + 1), dtype=np.uint16)
+    _check(load_library().blowchoc_cost_ranks(int(cost), float(cost_param), int(k), out.ctypes.data, out.size))
+    return out
 
 
 def blowchoc_l2_residency(f, fraction, stream):

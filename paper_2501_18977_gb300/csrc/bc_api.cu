@@ -500,6 +500,19 @@ int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs) {
     return BLOWCHOC_OK;
 }
 
+int blowchoc_cost_ranks(int cost, double cost_param, uint32_t k, uint16_t *ranks, uint64_t capacity) {
+    if (!ranks) return fail(BLOWCHOC_EINVAL, "ranks is NULL");
+    if (k < 1 || k > BLOWCHOC_MAX_K) return fail(BLOWCHOC_EINVAL, "k must be in 1..32 (got %u)", k);
+    if (cost < BLOWCHOC_COST_MIX || cost > BLOWCHOC_COST_EXP) return fail(BLOWCHOC_EINVAL, "unknown cost kind %d", cost);
+    if (!std::isfinite(cost_param) || cost_param < 0.0 || (cost == BLOWCHOC_COST_EXP && cost_param <= 0.0))
+        return fail(BLOWCHOC_EINVAL, "bad cost parameter %g", cost_param);
+    const uint64_t need = 513ull * (k + 1);
+    if (capacity < need) return fail(BLOWCHOC_EINVAL, "ranks needs 513 (k + 1) = %llu entries", (unsigned long long)need);
+    const std::vector<uint16_t> rank = rank_table(cost, cost_param, k);
+    std::memcpy(ranks, rank.data(), rank.size() * sizeof(uint16_t));
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_l2_residency(blowchoc_filter *f, double fraction, void *stream) {
     if (!f || !(fraction >= 0.0) || fraction > 1.0) return fail(BLOWCHOC_EINVAL, "fraction must be in [0, 1]");
     cudaStream_t s = (cudaStream_t)stream;
