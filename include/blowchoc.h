@@ -231,6 +231,20 @@ int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs);
 int blowchoc_cost_ranks(int cost, double cost_param, uint32_t k, uint16_t *ranks, uint64_t capacity);
 
 /*
+ * blowchoc_fpr_estimate -- the estimate blowchoc_stats reports, from a load
+ * histogram: hist[L] blocks of load L (513 host entries, caller-owned).
+ * A negative finds its bits in a block of load L with probability
+ * p_L = (L / 512)^k for independent bit addresses (Section 2.1 per block) or
+ * C(L, k) / C(512, k) for k distinct ones (Appendix B); q = the mean of p_L
+ * over the blocks, and the estimate is 1 - (1 - q)^c, treating the c
+ * candidate blocks as independent (exact in expectation for c = 1).
+ * Host-only: needs no device.
+ * Errors: EINVAL (NULL, k outside 1..32, c outside 1..3, bitsel > 1, a
+ * histogram that counts no block).
+ */
+int blowchoc_fpr_estimate(const uint64_t *hist, uint32_t k, uint32_t choices, uint32_t bitsel, double *out);
+
+/*
  * blowchoc_l2_residency -- keep part of the filter's words resident in L2
  * for the kernels later queued on `stream` (a created stream, not NULL):
  * sets aside fraction x the device's maximum persisting L2 for this process

@@ -89,6 +89,7 @@ _SIGS = {
     "blowchoc_clear": ([_VP, _VP], _I),
     "blowchoc_set_cost_table": ([_VP, _VP], _I),
     "blowchoc_cost_ranks": ([ctypes.c_int, ctypes.c_double, ctypes.c_uint32, _VP, ctypes.c_uint64], _I),
+    "blowchoc_fpr_estimate": ([_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _VP], _I),
     "blowchoc_l2_residency": ([_VP, ctypes.c_double, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
@@ -255,6 +256,18 @@ def blowchoc_cost_ranks(cost: int, cost_param: float, k: int):
     out = np.empty(513 * (int(k) + 1), dtype=np.uint16)
     _check(load_library().blowchoc_cost_ranks(int(cost), float(cost_param), int(k), out.ctypes.data, out.size))
     return out
+
+
+def blowchoc_fpr_estimate(hist, k: int, choices: int, bitsel: int = 0) -> float:
+    """The histogram FPR estimate of blowchoc_stats for a host histogram of
+    513 block counts (index = load)."""
+    import numpy as np
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    assert h.shape == (513,)
+    out = ctypes.c_double()
+    _check(load_library().blowchoc_fpr_estimate(h.ctypes.data, int(k), int(choices), int(bitsel),
+                                                 ctypes.byref(out)))
+    return float(out.value)
 
 
 def blowchoc_l2_residency(f, fraction, stream):

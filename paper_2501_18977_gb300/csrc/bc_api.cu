@@ -98,6 +98,27 @@ double cost_value(int kind, double par, uint32_t k, uint32_t j, uint32_t a) {
     return std::pow(par, (double)j / 128.0) + (double)a / dk;
 }
 
+// FPR estimate from the load histogram: a negative finds all its bits set in
+// a block of load L with probability (L / 512)^k for independent bit
+// addresses, C(L, k) / C(512, k) for k distinct ones (Appendix B); q is the
+// mean over blocks, and c candidates are treated as independent.
+double fpr_from_hist(const uint64_t *hist, uint32_t k, uint32_t choices, uint32_t bitsel) {
+    double q = 0.0, blocks = 0.0;
+    for (int L = 0; L <= 512; ++L) {
+        double pL = 1.0;
+        if (bitsel) {
+            for (uint32_t i = 0; i < k; ++i) pL *= (double)((int)L - (int)i) / (double)(512 - i);
+            if (pL < 0.0) pL = 0.0;
+        } else {
+            pL = std::pow((double)L / 512.0, (double)k);
+        }
+        q += (double)hist[L] * pL;
+        blocks += (double)hist[L];
+    }
+    q /= blocks;
+    return 1.0 - std::pow(1.0 - q, (double)choices);
+}
+
 // Integer rank of every reachable (L, a) cost: equal doubles share a rank,
 // so comparing ranks on the device is comparing the doubles exactly. With
 // `given` the costs come from a table instead of Eq. 4-6.
@@ -412,24 +433,11 @@ int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
     std::memset(out, 0, sizeof *out);
     out->inserted = h[0];
     out->skipped = h[1];
-    // probability that a negative finds all its bits set in a block of load
-    // L: (L / 512)^k for independent bit addresses, C(L, k) / C(512, k) for
-    // k distinct ones (Appendix B)
-    double q = 0.0;
     for (int L = 0; L <= 512; ++L) {
         out->hist[L] = h[3 + L];
         out->set_bits += (uint64_t)L * h[3 + L];
-        double pL = 1.0;
-        if (f->p.bitsel) {
-            for (uint32_t i = 0; i < f->p.k; ++i) pL *= (double)((int)L - (int)i) / (double)(512 - i);
-            if (pL < 0.0) pL = 0.0;
-        } else {
-            pL = std::pow((double)L / 512.0, (double)f->p.k);
-        }
-        q += (double)h[3 + L] * pL;
     }
-    q /= (double)f->dev.M;
-    out->fpr_est = 1.0 - std::pow(1.0 - q, (double)f->p.choices);
+    out->fpr_est = fpr_from_hist(out->hist, f->p.k, f->p.choices, f->p.bitsel);
     if (h[2]) return fail(BLOWCHOC_ETIMEOUT, "a bounded device wait of this filter gave up");
     return BLOWCHOC_OK;
 }
@@ -497,6 +505,18 @@ int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs) {
     BC_CUDA(cudaMemcpyAsync(f->d_rank, rank.data(), rank.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
                             f->home), "cost table upload");
     BC_CUDA(cudaStreamSynchronize(f->home), "cost table upload");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_fpr_estimate(const uint64_t *hist, uint32_t k, uint32_t choices, uint32_t bitsel, double *out) {
+    if (!hist || !out) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    if (k < 1 || k > BLOWCHOC_MAX_K) return fail(BLOWCHOC_EINVAL, "k must be in 1..32 (got %u)", k);
+    if (choices < 1 || choices > BLOWCHOC_MAX_CHOICES) return fail(BLOWCHOC_EINVAL, "choices must be in 1..3");
+    if (bitsel > 1) return fail(BLOWCHOC_EINVAL, "bitsel must be 0 (random) or 1 (distinct)");
+    uint64_t blocks = 0;
+    for (int L = 0; L <= 512; ++L) blocks += hist[L];
+    if (blocks == 0) return fail(BLOWCHOC_EINVAL, "the histogram counts no block");
+    *out = fpr_from_hist(hist, k, choices, bitsel);
     return BLOWCHOC_OK;
 }
 
