@@ -206,6 +206,18 @@ int blowchoc_words(blowchoc_filter *f, uint64_t **d_words, uint64_t *nwords);
 int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit);
 
 /*
+ * blowchoc_derive_multipliers -- the multipliers a filter created with
+ * `params` will use, without creating it: successive splitmix64 outputs of
+ * params->hash_seed, forced odd and redrawn until coprime to the hash's range
+ * (Section 3.4); first a_block[0..c) for the range M, then a_bit[0..k) for
+ * the range 512 (random bits) or 512 - i for the (i+1)-th (distinct bits,
+ * Appendix B). a_block and a_bit are host arrays of at least 3 and 32
+ * entries. Host-only: needs no device.
+ * Errors: EINVAL (NULL, the parameters blowchoc_create rejects).
+ */
+int blowchoc_derive_multipliers(const blowchoc_params *params, uint64_t *a_block, uint64_t *a_bit);
+
+/*
  * blowchoc_set_cost_table -- replace the filter's cost by a table (a learned
  * cost, or any cost outside Eq. 4-6): costs[L * (k + 1) + a] for block load
  * L = 0..512 and new bits a = 0..k; entries with L + a > 512 are never used.

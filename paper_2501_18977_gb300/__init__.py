@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     blowchoc_insert_noalloc, blowchoc_query,
     blowchoc_stats, blowchoc_destroy, blowchoc_words, blowchoc_multipliers,
     blowchoc_read_words, blowchoc_write_words, blowchoc_clear, blowchoc_set_cost_table, blowchoc_cost_ranks,
-    blowchoc_fpr_estimate,
+    blowchoc_fpr_estimate, blowchoc_derive_multipliers,
     blowchoc_cluster_ctas,
     blowchoc_query_count, blowchoc_generate_keys, generate_keys, blowchoc_insert_host, blowchoc_query_host,
     blowchoc_l2_residency, blowchoc_last_error, blowchoc_launch_count,

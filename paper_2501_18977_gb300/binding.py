@@ -90,6 +90,7 @@ _SIGS = {
     "blowchoc_set_cost_table": ([_VP, _VP], _I),
     "blowchoc_cost_ranks": ([ctypes.c_int, ctypes.c_double, ctypes.c_uint32, _VP, ctypes.c_uint64], _I),
     "blowchoc_fpr_estimate": ([_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _VP], _I),
+    "blowchoc_derive_multipliers": ([_VP, _VP, _VP], _I),
     "blowchoc_l2_residency": ([_VP, ctypes.c_double, _VP], _I),
     "blowchoc_last_error": ([], ctypes.c_char_p),
     "blowchoc_launch_count": ([], ctypes.c_uint64),
@@ -231,6 +232,17 @@ def blowchoc_multipliers(f):
     a_bit = (ctypes.c_uint64 * 32)()
     _check(load_library().blowchoc_multipliers(f, a_block, a_bit))
     return list(a_block), list(a_bit)
+
+
+def blowchoc_derive_multipliers(nblocks: int, k: int, choices: int, hash_seed: int, bitsel: int = 0):
+    """The multipliers (a_block[:choices], a_bit[:k]) a filter with these
+    parameters will use; host-only."""
+    p = blowchoc_params(nblocks=int(nblocks), k=int(k), choices=int(choices), cost=COST_EXP, bitsel=int(bitsel),
+                        cost_param=(1 + 5 ** 0.5) / 2, hash_seed=int(hash_seed), batch=1)
+    a_block = (ctypes.c_uint64 * 3)()
+    a_bit = (ctypes.c_uint64 * 32)()
+    _check(load_library().blowchoc_derive_multipliers(ctypes.byref(p), a_block, a_bit))
+    return list(a_block)[:int(choices)], list(a_bit)[:int(k)]
 
 
 def blowchoc_read_words(f, first: int, count: int, h_dst):

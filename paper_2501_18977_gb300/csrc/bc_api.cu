@@ -508,6 +508,15 @@ int blowchoc_set_cost_table(blowchoc_filter *f, const double *costs) {
     return BLOWCHOC_OK;
 }
 
+int blowchoc_derive_multipliers(const blowchoc_params *params, uint64_t *a_block, uint64_t *a_bit) {
+    if (!a_block || !a_bit) return fail(BLOWCHOC_EINVAL, "NULL argument");
+    const int rc = check_params(params);
+    if (rc) return rc;
+    derive_multipliers(params->hash_seed, params->nblocks, params->k, params->choices, params->bitsel, a_block,
+                       a_bit);
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_fpr_estimate(const uint64_t *hist, uint32_t k, uint32_t choices, uint32_t bitsel, double *out) {
     if (!hist || !out) return fail(BLOWCHOC_EINVAL, "NULL argument");
     if (k < 1 || k > BLOWCHOC_MAX_K) return fail(BLOWCHOC_EINVAL, "k must be in 1..32 (got %u)", k);
