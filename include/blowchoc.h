@@ -18,7 +18,10 @@
  *    caller orders calls on different streams (events) if one must see the
  *    other's result.
  *  - There is no CPU fallback: without a usable CUDA device every call that
- *    needs one fails with BLOWCHOC_ECUDA.
+ *    needs one fails with BLOWCHOC_ECUDA. The host-only calls
+ *    (blowchoc_cost_ranks, blowchoc_fpr_estimate,
+ *    blowchoc_derive_multipliers) compute host-side preparation and
+ *    statistics only; no insert or query runs without a device.
  */
 #ifndef BLOWCHOC_H
 #define BLOWCHOC_H
