@@ -95,6 +95,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest `value` over the job's ranks (the slowest replica's step
+    time); `value` itself with one rank."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mkeys_per_s(keys_per_rank, world, ms_per_step):
+    """Whole-job throughput: every rank's keys over the slowest rank's step."""
+    return world * keys_per_rank / (ms_per_step / 1e3) / 1e6
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -937,12 +954,8 @@ def main():
     barrier()
     launches = bc.blowchoc_launch_count() - launches0
     clk = clocks.stop()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * (n_ins + n_q) / (ms / 1e3) / 1e6
+    ms = max_over_ranks(t_start.elapsed_time(t_end) / args.steps, world, "cuda")
+    value = job_mkeys_per_s(n_ins + n_q, world, ms)
 
     ins_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     qry_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
@@ -987,13 +1000,9 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = a.elapsed_time(b) / args.steps
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(a.elapsed_time(b) / args.steps, world, "cuda")
         hits = int(np.unpackbits(h_bm.numpy().view(np.uint8), bitorder="little")[:n_q].sum())
-        e2e = {"value": round(world * (n_ins + n_q) / (ems / 1e3) / 1e6, 3), "unit": "Mkeys/s",
+        e2e = {"value": round(job_mkeys_per_s(n_ins + n_q, world, ems), 3), "unit": "Mkeys/s",
                "h2d_bytes_per_step": int(8 * (n_ins + n_q)), "d2h_bytes_per_step": int(8 * nwords),
                "ms_per_step": round(ems, 3), "api": "blowchoc_insert_host + blowchoc_query_host (pinned)",
                "query_hits": hits}
