@@ -190,7 +190,9 @@ int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out);
 
 /*
  * blowchoc_destroy -- synchronise the home stream and free the filter's
- * device memory. NULL is accepted (no-op).
+ * device memory. NULL is accepted (no-op). The memory is freed even when the
+ * synchronisation reports an error. Errors: ECUDA (an earlier asynchronous
+ * failure surfaced by the synchronisation).
  */
 int blowchoc_destroy(blowchoc_filter *f);
 
@@ -198,6 +200,7 @@ int blowchoc_destroy(blowchoc_filter *f);
  * blowchoc_words -- the device address and length (8 M words) of the filter
  * words. The library keeps ownership; the pointer is valid until destroy.
  * Reading or writing it must be ordered with the filter's other work.
+ * Errors: EINVAL (NULL argument).
  */
 int blowchoc_words(blowchoc_filter *f, uint64_t **d_words, uint64_t *nwords);
 
@@ -465,7 +468,8 @@ int blowchoc_server_stats(blowchoc_server *s, blowchoc_server_summary *out);
  * Use only while no request of it is in flight. Errors: EINVAL. */
 int blowchoc_server_filter(blowchoc_server *s, uint32_t id, blowchoc_filter **f);
 
-/* Stop the thread, wait for the GPU, free everything. NULL is accepted. */
+/* Stop the thread, wait for the GPU, free everything. NULL is accepted.
+ * Always returns OK. */
 int blowchoc_server_destroy(blowchoc_server *s);
 
 /*
@@ -486,25 +490,33 @@ typedef struct blowchoc_mlp blowchoc_mlp;
 /* Network for filters with k bit hashes; weights uniform in +-1/sqrt(fan in)
  * from splitmix64(seed), biases 0. Errors: EINVAL, ENOMEM, ECUDA. */
 int blowchoc_mlp_create(uint32_t k, uint64_t seed, blowchoc_mlp **out);
+/* Wait for the device, then free the network (NULL is accepted). Always
+ * returns OK. */
 int blowchoc_mlp_destroy(blowchoc_mlp *m);
 uint32_t blowchoc_mlp_param_count(void);
 
 /* Host copies of the parameters (1185 floats) and of the accumulated
- * gradient (1185 doubles); either pointer may be NULL. Synchronous. */
+ * gradient (1185 doubles); either pointer may be NULL. Synchronous.
+ * set_params uploads 1185 floats. Errors: EINVAL (NULL network, NULL
+ * h_params for set_params), ECUDA. */
 int blowchoc_mlp_get_params(blowchoc_mlp *m, float *h_params, double *h_grad);
 int blowchoc_mlp_set_params(blowchoc_mlp *m, const float *h_params);
 
-/* d_table[L (k+1) + a] = g(((L + a) / 512, a / k)) for L = 0..512, a = 0..k. */
+/* d_table[L (k+1) + a] = g(((L + a) / 512, a / k)) for L = 0..512, a = 0..k
+ * (a device array of 513 (k + 1) floats, caller-owned; stream-ordered).
+ * Errors: EINVAL (NULL argument), ECUDA. */
 int blowchoc_mlp_forward(blowchoc_mlp *m, float *d_table, void *stream);
 
 /* gradient += sum_r d_scales[r] * sum_p d_w[r * P + p] * d g(x_p) / d params,
  * P = 513 (k + 1): `rows` rows of per-point weights (device), one device
- * scale per row (e.g. one training filter's advantage each). */
+ * scale per row (e.g. one training filter's advantage each). Stream-ordered.
+ * Errors: EINVAL (NULL argument, rows = 0), ECUDA. */
 int blowchoc_mlp_backward(blowchoc_mlp *m, const float *d_w, uint32_t rows, const double *d_scales,
                           void *stream);
 
 /* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) down the accumulated
- * gradient, which is then cleared. */
+ * gradient, which is then cleared. Stream-ordered.
+ * Errors: EINVAL (NULL network, lr not > 0, NaN included), ECUDA. */
 int blowchoc_mlp_adam_step(blowchoc_mlp *m, float lr, void *stream);
 
 /*
@@ -600,6 +612,8 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t);
  * lanes_cluster, cluster_keys as above; cluster_max > 0 gives each eligible
  * filter of a call a cluster of its own, default 0). */
 int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out);
+/* Errors (both): EINVAL (NULL argument, a field outside its range; nothing
+ * changes then). */
 int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t);
 
 /* Launch configuration of a server's filters (applied as each is admitted,
