@@ -33,7 +33,9 @@ and cost-parameter sweeps at 2*10^9 keys per point (`--keys` scales them),
 with keys generated on the device; `cluster` compares cluster-resident with
 global-memory inserts on serving-sized filters; `lanes` times the persistent
 insert with 1, 2, 4 and 8 lanes per key for filters of 2 MiB to 512 MiB (the
-measurements behind the default lanes per filter size).
+measurements behind the default lanes per filter size); `variants` times the
+sort-by-block set against the direct set, and distinct against random bit
+selection.
 """
 import argparse
 import json
@@ -68,7 +70,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
-                                           "learn", "fig4", "fig8", "fig10", "cluster", "lanes"], default="dna")
+                                           "learn", "fig4", "fig8", "fig10", "cluster", "lanes", "variants"],
+                    default="dna")
     ap.add_argument("--keys", type=float, default=2e9, help="fig4/fig8/fig10: keys inserted and negatives")
     ap.add_argument("--ks", type=str, default="4,7,10,14,17,20", help="fig4/fig10: k values")
     ap.add_argument("--runs", type=int, default=1, help="fig10: repetitions with other seeds")
@@ -809,6 +812,71 @@ def run_lanes(args):
                       "rows": rows, "timing": "CUDA events, median of --steps after one warm-up"}))
 
 
+def run_variants(args):
+    """The set-phase and bit-selection variants beside the defaults, per
+    shape (uniform device-generated keys, cluster path off): the persistent
+    insert with the direct set (64-bit OR reductions at L2, set_mode 0) and
+    with the sort-by-block set (set_mode 1), whose words must be identical;
+    then insert and query times with random (bitsel 0) and distinct
+    (bitsel 1, Appendix B) bit selection, which build different filters by
+    design. Medians of --steps timed calls after one warm-up."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    s = torch.cuda.current_stream()
+    phi = (1 + 5 ** 0.5) / 2
+    shapes = [("128 MiB, three choices", 1 << 21, 16, 3, bc.COST_LA, 3.5, 1 << 20, 1 << 25),
+              ("2 MiB, two choices", 32768, 14, 2, bc.COST_MIX, 50.0, 65536, 1 << 20),
+              ("256 KiB, 64 keys per block per batch", 4096, 12, 2, bc.COST_EXP, phi, 1 << 18, 1 << 21)]
+
+    def timed(fn):
+        times = []
+        for rep in range(1 + max(1, args.steps)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            torch.cuda.synchronize()
+            if rep:
+                times.append(a.elapsed_time(b))
+        return round(statistics.median(times), 4)
+
+    rows = []
+    for name, M, k, c, cost, par, B, n in shapes:
+        keys = bc.generate_keys(n, 31)
+        negatives = bc.generate_keys(n, 32)
+        bitmap = torch.empty((n + 63) // 64, dtype=torch.int64, device="cuda")
+        row = {"shape": name, "M": M, "k": k, "c": c, "B": B, "n": n}
+        f = bc.Filter(M, k, c, cost, par, hash_seed=9, batch=B, stream=s)
+        f.set_tuning(cluster_max=0)
+        words = {}
+        for mode in (0, 1):
+            f.set_tuning(set_mode=mode)
+
+            def ins():
+                f.clear(s)
+                f.insert(keys, s)
+            row["set_mode%d_insert_ms" % mode] = timed(ins)
+            words[mode] = f.words_host()
+        row["set_modes_identical"] = bool(np.array_equal(words[0], words[1]))
+        f.close()
+        for bitsel in (0, 1):
+            g = bc.Filter(M, k, c, cost, par, hash_seed=9, batch=B, stream=s, bitsel=bitsel)
+            g.set_tuning(cluster_max=0)
+
+            def ins_g():
+                g.clear(s)
+                g.insert(keys, s)
+            row["bitsel%d_insert_ms" % bitsel] = timed(ins_g)
+            row["bitsel%d_query_ms" % bitsel] = timed(lambda: g.query(negatives, bitmap, s))
+            g.close()
+        rows.append(row)
+        del keys, negatives, bitmap
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "set_and_bit_selection_variants", "rows": rows,
+                      "timing": "CUDA events, median of --steps after one warm-up"}))
+
+
 def run_figures(args):
     """Paper-scale FPR and load sweeps on the device (keys generated there):
     fig4 = log2 FPR vs relative size for c = 1, 2, 3 and random/distinct bits
@@ -869,6 +937,9 @@ def main():
         return
     if args.workload == "lanes":
         run_lanes(args)
+        return
+    if args.workload == "variants":
+        run_variants(args)
         return
     if args.impl == "reference":
         run_reference(args)
