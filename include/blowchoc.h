@@ -107,7 +107,8 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
  * depends only on (params, key sequence), never on launch configuration.
  *   d_keys  device, n uint64 keys (any values; u = 64-bit keys).
  *   n       may be 0 (no-op).
- * May grow an internal device scratch buffer (min(B, n) bytes) on first use.
+ * May grow an internal device scratch buffer (up to 2 min(B, n) bytes: a
+ * choice byte per key, and a byte of word flags in the persistent insert).
  * Errors: EINVAL (NULL filter, NULL keys with n > 0), ENOMEM, ECUDA.
  */
 int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void *stream);
