@@ -6,8 +6,11 @@ insertion, and a, the newly set bits) as x = (j / 512, a / k) and outputs a
 cost g(x). Everything here is plain numpy in float64, written from the
 definitions: a two-hidden-layer tanh network, its exact gradient, the softmax
 policy over a key's candidates and the score-function weight
-d log pi(chosen) / d g. Pinned in tests/test_oracle_pins.py by a hand-derived
-value, finite differences and invariants.
+d log pi(chosen) / d g. Pinned in tests/test_oracle_pins.py: the forward pass
+by a hand-derived value, the gradient by finite differences, the score weight
+by a finite difference of log pi(s) (scipy's log_softmax) and the sampler by
+draw frequencies against softmax(-g / tau), Adam by hand-computed first and
+second steps, and the uniforms by the generator's check vector.
 """
 import numpy as np
 

@@ -451,6 +451,120 @@ def test_learned_sampling_limits_and_invariants():
     assert (ch2 != np.where(choices == 255, 255, choices)).any()
 
 
+def test_learned_adam_hand_steps():
+    """Adam (Kingma and Ba, 2015) with zero moments: the bias corrections make
+    m_hat = g and v_hat = g^2 on the first step, so the update is
+    -lr g / (|g| + eps), i.e. -lr sign(g) away from g = 0, and a constant
+    gradient keeps that size on every later step. A gradient +1 then -1 gives,
+    on step 2, m = 0.9 (0.1) - 0.1 = -0.01, so m_hat = -0.01 / (1 - 0.81) = -1/19,
+    and v = 0.999 (0.001) + 0.001 = 0.001999 = 1 - 0.999^2, so v_hat = 1: the
+    second update is +lr/19. Swapping beta1 and beta2, dropping a bias
+    correction or the square root changes one of these values."""
+    from oracle import learned as lr
+    z = np.zeros(4)
+    p0 = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.5, -2.0, 0.0, 1e-3])
+    p1, m1, m2 = lr.adam(p0, g, z.copy(), z.copy(), 1, 0.01)
+    want1 = np.array([1.0 - 0.01 * 0.5 / (0.5 + 1e-8), -2.0 + 0.01 * 2.0 / (2.0 + 1e-8), 0.5,
+                      3.0 - 0.01 * 1e-3 / (1e-3 + 1e-8)])
+    assert np.allclose(p1, want1, rtol=0, atol=1e-13)
+    assert np.allclose(m1, 0.1 * g, rtol=0, atol=1e-15) and np.allclose(m2, 1e-3 * g * g, rtol=0, atol=1e-15)
+    # constant gradient: -lr sign(g) every step
+    p, a, b = p0.copy(), z.copy(), z.copy()
+    for t in range(1, 8):
+        p, a, b = lr.adam(p, g, a, b, t, 0.01)
+    assert np.allclose(p[:2], [1.0 - 0.07, -2.0 + 0.07], rtol=0, atol=1e-8)
+    assert p[2] == 0.5
+    # +1 then -1: the second step moves by +lr/19
+    q1, a, b = lr.adam(np.zeros(1), np.ones(1), np.zeros(1), np.zeros(1), 1, 0.01)
+    assert np.allclose(q1, [-0.01], rtol=0, atol=1e-10)
+    q2, _, _ = lr.adam(q1, -np.ones(1), a, b, 2, 0.01)
+    assert np.allclose(q2 - q1, [0.01 / 19.0], rtol=0, atol=1e-10)
+
+
+def _distinct_point_key(f, table_len, want_c, seed=77):
+    """A key whose candidates are all partly empty (a > 0) at distinct (L, a)
+    grid points of the filter `f` as it stands."""
+    k1 = f.k + 1
+    for x in workloads.uniform_keys(seed, 5000):
+        terms = [f.block_terms(b, int(x)) for b in f.candidates(int(x))]
+        pts = [L * k1 + a for L, a in terms]
+        if len(set(pts)) == want_c and min(a for _, a in terms) > 0:
+            assert max(pts) < table_len
+            return int(x), pts
+    raise AssertionError("no key with distinct candidate points")
+
+
+@pytest.mark.parametrize("c", [2, 3])
+def test_learned_score_weight_is_gradient_of_log_policy(c):
+    """The score weight of a decision is d log pi(s) / d g at each candidate's
+    grid point, where pi = softmax(-g / tau) over the key's candidates and s
+    is the drawn choice. Checked by a central finite difference of
+    log pi(s), computed by scipy's log_softmax, in each candidate's table
+    value, for every possible draw s; a flipped sign or a missing 1/tau fails."""
+    from scipy.special import log_softmax
+    from oracle import learned as lr
+    k, M, tau, h = 6, 16, 0.7, 1e-6
+    f = _filter(M, k, c, COST_EXP, GOLDEN_RATIO, seed=4, B=1)
+    f.insert(workloads.uniform_keys(201, 300))
+    rng = np.random.default_rng(11)
+    table = rng.normal(0, 1, 513 * (k + 1))
+    x, pts = _distinct_point_key(f, len(table), c)
+    seen = set()
+    for seed in range(200):
+        ch, w, _ = lr.sampled_batch(f, np.array([x], dtype=np.uint64), table, tau, seed)
+        s = int(ch[0])
+        if s in seen:
+            continue
+        seen.add(s)
+        for i, p in enumerate(pts):
+            tp, tm = table.copy(), table.copy()
+            tp[p] += h
+            tm[p] -= h
+            lp = log_softmax(-np.array([tp[q] for q in pts]) / tau)[s]
+            lm = log_softmax(-np.array([tm[q] for q in pts]) / tau)[s]
+            fd = (lp - lm) / (2 * h)
+            assert abs(w[p] - fd) < 1e-6, (c, s, i, w[p], fd)
+        nz = np.flatnonzero(w)
+        assert set(nz.tolist()) <= set(pts)
+    assert seen == set(range(c))
+
+
+def test_learned_sampler_draws_from_softmax_of_minus_cost():
+    """4,000 draws for one key (u from consecutive stream positions): the
+    frequency of each candidate equals softmax(-g / tau) within 4.5 binomial
+    sigma. Drawing from softmax(+g / tau), or inverting the cumulative search,
+    fails."""
+    from scipy.special import softmax
+    from oracle import learned as lr
+    k, M, tau, n = 6, 16, 0.8, 4000
+    f = _filter(M, k, 3, COST_EXP, GOLDEN_RATIO, seed=4, B=1)
+    f.insert(workloads.uniform_keys(201, 300))
+    table = np.random.default_rng(12).normal(0, 1, 513 * (k + 1))
+    x, pts = _distinct_point_key(f, len(table), 3, seed=78)
+    ch, _, _ = lr.sampled_batch(f, np.full(n, x, dtype=np.uint64), table, tau, seed=9)
+    pi = softmax(-np.array([table[p] for p in pts]) / tau)
+    assert pi.max() - pi.min() > 0.15
+    for i in range(3):
+        got = float((ch == i).sum())
+        sd = math.sqrt(n * pi[i] * (1 - pi[i]))
+        assert abs(got - n * pi[i]) < 4.5 * sd, (i, got, n * pi[i])
+
+
+def test_learned_uniforms_are_the_generator_stream():
+    """splitmix_uniform(seed, i) is the top 53 bits of output i of the
+    published generator: equal to workloads.splitmix64 and to the check
+    vector of seed 1234567."""
+    from oracle import learned as lr
+    want = [int(r[0]) for r in _rows("splitmix64_seed1234567.txt")]
+    for i, v in enumerate(want):
+        assert lr.splitmix_uniform(1234567, i) == (v >> 11) / float(1 << 53)
+    for seed in (0, 5, 0xDEADBEEF12345678):
+        outs = workloads.splitmix64(seed, 300)
+        for i in (0, 1, 17, 299):
+            assert lr.splitmix_uniform(seed, i) == (int(outs[i]) >> 11) / float(1 << 53)
+
+
 # ---------------------------------------------------------------- distinct bit selection (Appendix B)
 
 def test_distinct_shift_rule_printed_example():
