@@ -70,13 +70,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
-                                           "learn", "fig4", "fig8", "fig10", "cluster", "lanes", "variants"],
+                                           "learn", "fig4", "fig8", "fig10", "cluster", "lanes", "variants",
+                                           "hbm"],
                     default="dna")
     ap.add_argument("--keys", type=float, default=2e9, help="fig4/fig8/fig10: keys inserted and negatives")
     ap.add_argument("--ks", type=str, default="4,7,10,14,17,20", help="fig4/fig10: k values")
     ap.add_argument("--runs", type=int, default=1, help="fig10: repetitions with other seeds")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--reps", type=int, default=3, help="hbm: timed passes after one untimed pass")
+    ap.add_argument("--no-extra-records", action="store_true",
+                    help="leave the gather ceilings and the hbm_resident record out of the DNA line")
     return ap.parse_args()
 
 
@@ -220,28 +224,37 @@ def ncu_traffic(kernel, tuning):
     return d[kernel]["dram_bytes_per_launch"]
 
 
-def gather_ceiling(bc, torch, nblocks, words=None, nreads=50_000_000, lanes=2, cps=16):
+def gather_ceiling(bc, torch, nblocks, words=None, nreads=50_000_000, grid=None):
     """Random whole-block read rate (GB/s of 64-byte blocks) over `nblocks`
-    blocks, best of 3, with the library's gather probe."""
+    blocks with the library's gather probe: the best over lanes per block,
+    CTAs per SM and independent loads in flight per lane group (each the best
+    of 3 timed runs after one untimed). Returns (GB/s, (lanes, ctas/SM, in flight))."""
     own = words is None
     if own:
         words = torch.ones(nblocks * 8, dtype=torch.int64, device="cuda")
     sink = torch.empty(4096 * 16, dtype=torch.int64, device="cuda")
     s = torch.cuda.current_stream()
-    best = None
-    for r in range(4):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        bc.blowchoc_gather_probe(words, nblocks, nreads, r, lanes, cps, sink, s)
-        b.record(s)
-        torch.cuda.synchronize()
-        if r:
-            t = a.elapsed_time(b)
-            best = t if best is None else min(best, t)
+    if grid is None:
+        grid = [(lanes, cps, inf) for lanes in (1, 2, 4) for cps in (4, 8, 16) for inf in (1, 2, 4, 8)]
+    best = (0.0, None)
+    for lanes, cps, inf in grid:
+        t_best = None
+        for r in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            bc.blowchoc_gather_probe(words, nblocks, nreads, r, lanes, cps, sink, s, inflight=inf)
+            b.record(s)
+            torch.cuda.synchronize()
+            if r:
+                t = a.elapsed_time(b)
+                t_best = t if t_best is None else min(t_best, t)
+        g = nreads * 64 / (t_best / 1e3) / 1e9
+        if g > best[0]:
+            best = (g, (lanes, cps, inf))
     if own:
         del words
-    return nreads * 64 / (best / 1e3) / 1e9
+    return best
 
 
 def run_gather(args):
@@ -250,14 +263,9 @@ def run_gather(args):
     out = []
     for mib in [2, 64, 128, 512, 4096]:
         nb = mib * (1 << 20) // 64
-        best = (0.0, None)
-        for lanes in (1, 2, 4, 8):
-            for cps in (4, 8, 16):
-                g = gather_ceiling(bc, torch, nb, nreads=100_000_000, lanes=lanes, cps=cps)
-                if g > best[0]:
-                    best = (g, (lanes, cps))
-        out.append({"footprint_mib": mib, "gbs": round(best[0], 1), "lanes": best[1][0],
-                    "ctas_per_sm": best[1][1]})
+        g, (lanes, cps, inf) = gather_ceiling(bc, torch, nb, nreads=100_000_000)
+        out.append({"footprint_mib": mib, "gbs": round(g, 1), "lanes": lanes, "ctas_per_sm": cps,
+                    "inflight": inf})
     print(json.dumps({"workload": "gather_ceiling", "unit": "GB/s of whole 64-byte blocks",
                       "reads": 100_000_000, "results": out}))
 
@@ -283,8 +291,9 @@ def run_many(args):
     s = torch.cuda.current_stream()
     ins = [(f, d, d.numel(), None) for f, d in zip(filters, dks)]
     qry = [(f, d, d.numel(), b) for f, d, b in zip(filters, dqs, bms)]
+    default_batch = bc.Batch()          # the fixed default configuration
     batch = bc.Batch()
-    best = batch.autotune(ins, qry)
+    best = batch.autotune(ins, qry)     # batch tuning, then per (size class, k, c)
 
     def clear_all():
         for f in filters:
@@ -300,6 +309,10 @@ def run_many(args):
         batch.insert_many(ins, s)
         batch.query_many(qry, s)
 
+    def batched_default():
+        default_batch.insert_many(ins, s)
+        default_batch.query_many(qry, s)
+
     batch.record(ins, qry)
 
     def graph():
@@ -310,7 +323,7 @@ def run_many(args):
             clear_all()
             fn()
         torch.cuda.synchronize()
-        total = 0.0
+        out = []
         for _ in range(reps):
             clear_all()
             a = torch.cuda.Event(enable_timing=True)
@@ -319,22 +332,34 @@ def run_many(args):
             fn()
             b.record(s)
             torch.cuda.synchronize()
-            total += a.elapsed_time(b)
-        return total / reps
+            out.append(a.elapsed_time(b))
+        return out
 
+    reps = max(5, args.steps)
+    forms = (("plain", plain), ("batched_default", batched_default), ("batched", batched), ("graph", graph))
     results, digests = {}, {}
-    for name, fn in (("plain", plain), ("batched", batched), ("graph", graph)):
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, fn in forms:
         launches0 = bc.blowchoc_launch_count()
-        ms = timed(fn, args.steps)
-        launches = (bc.blowchoc_launch_count() - launches0) // (args.steps + 2)
+        times = timed(fn, reps)
+        launches = (bc.blowchoc_launch_count() - launches0) // (reps + 2)
         words = [f.words_host() for f in filters]
         bits = [b.cpu().numpy().copy() for b in bms]
         digests[name] = (words, bits)
-        results[name] = {"ms": round(ms, 4), "mkeys_s": round((n_ins + n_q) / (ms / 1e3) / 1e6, 2),
-                         "launches": int(launches)}
+        ms = statistics.median(times)
+        results[name] = {"ms": round(ms, 4), "ms_min": round(min(times), 4), "ms_max": round(max(times), 4),
+                         "mkeys_s": round((n_ins + n_q) / (ms / 1e3) / 1e6, 2), "launches": int(launches)}
+    clk = clocks.stop()
     same = all(all(np.array_equal(a, b) for a, b in zip(digests[n][0], digests["plain"][0])) and
                all(np.array_equal(a, b) for a, b in zip(digests[n][1], digests["plain"][1]))
-               for n in ("batched", "graph"))
+               for n, _ in forms[1:])
+    classes = {}
+    for key in sorted({(batch.size_class(it["M"]), 11, 2) for it in cfg}):
+        t, is_set = batch.class_tuning(*key)
+        members = [it for it in cfg if batch.size_class(it["M"]) == key[0]]
+        classes[["cache", "l2", "spill", "hbm"][key[0]]] = dict(
+            t, tuned=bool(is_set), filters=len(members), keys=int(sum(it["n"] for it in members)))
     st = [f.stats() for f in filters]
     out = {"workload": "many_filters_256", "metric": "insert+query throughput, 256 filters",
            "unit": "Mkeys/s", "n_insert": n_ins, "n_query": n_q,
@@ -342,11 +367,15 @@ def run_many(args):
            "results": results,
            "batched_vs_plain": round(results["plain"]["ms"] / results["batched"]["ms"], 3),
            "graph_vs_plain": round(results["plain"]["ms"] / results["graph"]["ms"], 3),
+           "tuned_vs_default": round(results["batched_default"]["ms"] / results["batched"]["ms"], 3),
            "identical_words_and_bitmaps": bool(same),
            "inserted": int(sum(x.inserted for x in st)), "skipped": int(sum(x.skipped for x in st)),
            "autotuned": {"lanes_choose": best.lanes_choose, "lanes_query": best.lanes_query,
-                         "query_early": best.query_early, "ctas_per_sm": best.ctas_per_sm},
-           "steps": args.steps, "timing": "CUDA events per repetition, filters cleared before each"}
+                         "query_early": best.query_early, "ctas_per_sm": best.ctas_per_sm,
+                         "classes": classes},
+           "repeats": reps, "clocks": clk,
+           "timing": "CUDA events per repetition (median, min, max), filters cleared before each"}
+    default_batch.close()
     batch.close()
     for f in filters:
         f.close()
@@ -644,6 +673,116 @@ def golden_pbar():
     return 1.0, "lower bound 1.0 (oracle count not stored)"
 
 
+# The overload sweep's 12 bits/key point (Sec. 4.1), the HBM-resident
+# filter of the benchmark: M = 2^23 blocks (512 MiB, four times L2), k = 12,
+# B = 2^20, hash seed 3001; keys: the splitmix64 stream of seed 3001 grown
+# through 20, 18, 16, 14 and 12 bits per key in one insert call per point;
+# 10^8 negatives from seed 3002.
+HBM_POINT = dict(nblocks=1 << 23, k=12, batch=1 << 20, hash_seed=3001, neg_seed=3002,
+                 n_neg=100_000_000, bits=[20, 18, 16, 14, 12])
+HBM_SETTINGS = [(2, "EXP"), (3, "LA")]
+
+
+def sweep_golden_row(c, cost, bits):
+    """The oracle's stored row of the overload sweep at `bits` per key."""
+    path = os.path.join(ROOT, "tests", "golden", "overload_sweep_c%d_%s.txt" % (c, cost))
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or "|" not in line:
+                continue
+            f = [x.strip() for x in line.split("|")]
+            if int(f[0]) == bits:
+                return dict(n=int(f[1]), inserted=int(f[2]), skipped=int(f[3]), set_bits=int(f[4]),
+                            fp=int(f[5]), words=f[6], bitmap=f[7])
+    return None
+
+
+def hbm_resident(bc, torch, peak, local, reps=3):
+    """Insert and negative-query throughput of the 512 MiB filter at 12 bits
+    per key, for c = 2 cost^EXP and c = 3 cost^LA: insert time is the five
+    insert calls that grow the cleared filter to 357,913,941 keys, query time
+    one query of 10^8 negatives; best of `reps` after one untimed pass, with
+    clocks sampled. The final words and negative bitmap are compared with the
+    oracle's stored digests."""
+    import hashlib
+    P = HBM_POINT
+    stream = torch.cuda.current_stream()
+    nmax = (1 << 32) // P["bits"][-1]
+    keys = bc.generate_keys(nmax, P["hash_seed"], stream=stream)
+    neg = bc.generate_keys(P["n_neg"], P["neg_seed"], stream=stream)
+    bm = torch.empty((P["n_neg"] + 63) // 64, dtype=torch.int64, device="cuda")
+    ceil, ceil_cfg = gather_ceiling(bc, torch, P["nblocks"])
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    kinds = {"MIX": (bc.COST_MIX, 50.0), "LA": (bc.COST_LA, 3.5), "EXP": (bc.COST_EXP, phi)}
+    out = {"workload": "overload sweep point, 12 bits/key", "nblocks": P["nblocks"],
+           "filter_mib": P["nblocks"] * 64 >> 20, "k": P["k"], "batch": P["batch"],
+           "n_insert": nmax, "n_query": P["n_neg"],
+           "gather_ceiling_gbs": round(ceil, 1),
+           "gather_ceiling_config": {"lanes": ceil_cfg[0], "ctas_per_sm": ceil_cfg[1],
+                                     "inflight": ceil_cfg[2]},
+           "peak_gbs": peak, "settings": []}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for c, cost in HBM_SETTINGS:
+        kind, par = kinds[cost]
+        f = bc.Filter(P["nblocks"], P["k"], c, kind, par, hash_seed=P["hash_seed"], batch=P["batch"],
+                      stream=stream)
+        ins_ms, q_ms = [], []
+        for r in range(reps + 1):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            f.clear(stream)
+            e[0].record(stream)
+            n_prev = 0
+            for b in P["bits"]:
+                n = (1 << 32) // b
+                f.insert(keys[n_prev:n], stream)
+                n_prev = n
+            e[1].record(stream)
+            f.query(neg, bm, stream)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            if r or reps == 0:
+                ins_ms.append(e[0].elapsed_time(e[1]))
+                q_ms.append(e[1].elapsed_time(e[2]))
+        st = f.stats()
+        h = bm.cpu().numpy().view(np.uint64)
+        fp = int(np.unpackbits(h.view(np.uint8), bitorder="little")[:P["n_neg"]].sum())
+        words_sha = hashlib.sha256(f.words_host().astype("<u8").tobytes()).hexdigest()
+        bm_sha = hashlib.sha256(h.astype("<u8").tobytes()).hexdigest()
+        f.close()
+        g = sweep_golden_row(c, cost, P["bits"][-1])
+        if g is None:
+            parity = "oracle digest not stored"
+        else:
+            same = (g["n"] == nmax and g["inserted"] == st.inserted and g["skipped"] == st.skipped
+                    and g["set_bits"] == st.set_bits and g["fp"] == fp and g["words"] == words_sha
+                    and g["bitmap"] == bm_sha)
+            parity = "equal to the oracle's stored digests" if same else "DIFFERS from the oracle's stored digests"
+        skip = st.skipped / max(1, st.inserted + st.skipped)
+        ib = nmax * (8 + 64 * c + 64 * (1 - skip))
+        qb = P["n_neg"] * (8 + 64 * c + 1 / 8)
+        it, qt = min(ins_ms), min(q_ms)
+        igbs, qgbs = ib / (it / 1e3) / 1e9, qb / (qt / 1e3) / 1e9
+        out["settings"].append({
+            "choices": c, "cost": cost, "insert_ms": round(it, 3), "query_ms": round(qt, 3),
+            "insert_mkeys_s": round(nmax / (it / 1e3) / 1e6, 1),
+            "query_mkeys_s": round(P["n_neg"] / (qt / 1e3) / 1e6, 1),
+            "insert_gbs": round(igbs, 1), "query_gbs": round(qgbs, 1),
+            "insert_frac_of_peak": round(igbs / peak, 4), "query_frac_of_peak": round(qgbs / peak, 4),
+            "insert_frac_of_gather_ceiling": round(igbs / ceil, 4),
+            "query_frac_of_gather_ceiling": round(qgbs / ceil, 4),
+            "insert_bytes_per_key": round(8 + 64 * c + 64 * (1 - skip), 3),
+            "query_bytes_per_key": round(8 + 64 * c + 1 / 8, 3),
+            "inserted": st.inserted, "skipped": st.skipped, "false_positives": fp,
+            "fpr": fp / P["n_neg"], "parity": parity})
+    out["clocks"] = clocks.stop()
+    del keys, neg, bm
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_model():
     try:
         with open("/proc/cpuinfo") as fh:
@@ -824,9 +963,18 @@ def run_variants(args):
     import paper_2501_18977_gb300 as bc
     s = torch.cuda.current_stream()
     phi = (1 + 5 ** 0.5) / 2
-    shapes = [("128 MiB, three choices", 1 << 21, 16, 3, bc.COST_LA, 3.5, 1 << 20, 1 << 25),
-              ("2 MiB, two choices", 32768, 14, 2, bc.COST_MIX, 50.0, 65536, 1 << 20),
-              ("256 KiB, 64 keys per block per batch", 4096, 12, 2, bc.COST_EXP, phi, 1 << 18, 1 << 21)]
+    # filters of 2^12 .. 2^23 blocks at 16 bits per key (n = 32 M keys), with
+    # batches of M / 16, M / 2, 4 M and 32 M keys (1/16 .. 32 keys per block
+    # and batch; B >= n is one batch), c = 2 cost^EXP; plus the DNA shape
+    shapes = [("DNA shape, 128 MiB, three choices", 1 << 21, 16, 3, bc.COST_LA, 3.5, 1 << 20, 1 << 25)]
+    for lg in (12, 15, 18, 21, 23):
+        M = 1 << lg
+        for bm in (1 / 16, 1 / 2, 4, 32):
+            B = max(1, int(M * bm))
+            if B <= 2048:
+                continue  # batches of one CTA: the set mode does not apply
+            shapes.append(("%d MiB, B/M = %g" % (max(1, M * 64 >> 20), bm), M, 12, 2, bc.COST_EXP, phi, B,
+                           32 * M))
 
     def timed(fn):
         times = []
@@ -850,7 +998,7 @@ def run_variants(args):
         f = bc.Filter(M, k, c, cost, par, hash_seed=9, batch=B, stream=s)
         f.set_tuning(cluster_max=0)
         words = {}
-        for mode in (0, 1):
+        for mode in (0, 1, 2):
             f.set_tuning(set_mode=mode)
 
             def ins():
@@ -858,8 +1006,14 @@ def run_variants(args):
                 f.insert(keys, s)
             row["set_mode%d_insert_ms" % mode] = timed(ins)
             words[mode] = f.words_host()
-        row["set_modes_identical"] = bool(np.array_equal(words[0], words[1]))
+        row["set_modes_identical"] = bool(np.array_equal(words[0], words[1]) and np.array_equal(words[0], words[2]))
+        row["fastest_set_mode"] = min((0, 1, 2), key=lambda m: row["set_mode%d_insert_ms" % m])
         f.close()
+        if not (name == shapes[0][0] or B == M // 2):  # bit selection: the DNA shape and B = M / 2
+            rows.append(row)
+            del keys, negatives, bitmap
+            torch.cuda.empty_cache()
+            continue
         for bitsel in (0, 1):
             g = bc.Filter(M, k, c, cost, par, hash_seed=9, batch=B, stream=s, bitsel=bitsel)
             g.set_tuning(cluster_max=0)
@@ -946,6 +1100,12 @@ def main():
         return
     if args.workload == "gather":
         run_gather(args)
+        return
+    if args.workload == "hbm":
+        import torch
+        import paper_2501_18977_gb300 as bc
+        peak, _ = peaks()
+        print(json.dumps(hbm_resident(bc, torch, peak, 0, reps=args.reps)))
         return
     if args.workload == "many":
         run_many(args)
@@ -1092,8 +1252,12 @@ def main():
     dom_ms = qry_ms if dominant == "query_kernel" else ins_ms
     dom_gbs = q_gbs if dominant == "query_kernel" else i_gbs
     traffic = ncu_traffic(dominant, f.tuning())
-    ceil_filter = gather_ceiling(bc, torch, CONFIG["nblocks"])
-    ceil_hbm = gather_ceiling(bc, torch, 1 << 26)
+    if args.no_extra_records:
+        ceil_filter, ceil_filter_cfg, ceil_hbm, hbm = float("nan"), (None, None, None), float("nan"), None
+    else:
+        ceil_filter, ceil_filter_cfg = gather_ceiling(bc, torch, CONFIG["nblocks"])
+        ceil_hbm, _ = gather_ceiling(bc, torch, 1 << 26)
+        hbm = hbm_resident(bc, torch, peak, local)
     out = {
         "metric": "insert+query throughput (DNA 31-mers, c=3, k=16, cost^LA)",
         "value": round(value, 3), "unit": "Mkeys/s", "n_gpus": world, "steps": args.steps,
@@ -1111,10 +1275,21 @@ def main():
                      "traffic_unit": "GB per launch (ncu dram read+write)",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)",
                      "launch_ms": round(dom_ms, 4), "pbar": pbar, "pbar_source": pbar_src,
+                     "residency": ("L2-assisted: the 128 MiB filter is about L2's size, so part of "
+                                   "its block reads hit L2; see hbm_resident for a filter four "
+                                   "times L2"),
+                     "frac_of_gather_ceiling": round(dom_gbs / ceil_filter, 4),
                      "gather_ceiling_gbs": {"filter_footprint_128MiB": round(ceil_filter, 1),
+                                            "filter_footprint_config": {
+                                                "lanes": ceil_filter_cfg[0],
+                                                "ctas_per_sm": ceil_filter_cfg[1],
+                                                "inflight": ceil_filter_cfg[2]},
                                             "hbm_4GiB": round(ceil_hbm, 1)}},
+        "hbm_resident": hbm,
         "roofline_other": {"insert_gbs": round(i_gbs, 1), "insert_frac": round(i_gbs / peak, 4),
-                           "query_gbs": round(q_gbs, 1), "query_frac": round(q_gbs / peak, 4)},
+                           "query_gbs": round(q_gbs, 1), "query_frac": round(q_gbs / peak, 4),
+                           "insert_frac_of_gather_ceiling": round(i_gbs / ceil_filter, 4),
+                           "query_frac_of_gather_ceiling": round(q_gbs / ceil_filter, 4)},
         "skip_rate": round(skip_rate, 6), "inserted": st.inserted, "skipped": st.skipped,
         "query_hits": hits, "fpr_est": st.fpr_est,
         "gpu_launches": int(launches),

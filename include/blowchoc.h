@@ -20,7 +20,8 @@
  *  - There is no CPU fallback: without a usable CUDA device every call that
  *    needs one fails with BLOWCHOC_ECUDA. The host-only calls
  *    (blowchoc_cost_ranks, blowchoc_fpr_estimate,
- *    blowchoc_derive_multipliers) compute host-side preparation and
+ *    blowchoc_derive_multipliers, blowchoc_shard_layout,
+ *    blowchoc_shard_partition_scratch) compute host-side preparation and
  *    statistics only; no insert or query runs without a device.
  */
 #ifndef BLOWCHOC_H
@@ -121,16 +122,25 @@ int blowchoc_insert(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n, void
  * latency-critical loops (a request-serving loop, host code between CUDA
  * graph replays) where an allocation may synchronise the device.
  * Same arguments, semantics and results as blowchoc_insert (bit-identical
- * filter words and counters). Batches of more than 16384 keys keep their
- * per-key choices in one fixed array inside the library's device image
- * (4 MiB, held by every GPU that loads the library until the process exits)
- * instead of a buffer the filter allocates; smaller batches and B = 1 need no
- * scratch at all.
- *  - Limit: min(B, n) <= 4,194,304 keys when B > 16384; larger batches are
- *    rejected with EINVAL and a message naming the limit.
+ * filter words and counters). Batches that run over the whole grid (more
+ * than 2048 keys with the persistent insert on, the default; more than 16384
+ * with it off) keep their per-key choices in one fixed array inside the
+ * library's device image (4 MiB, held by every GPU that loads the library
+ * until the process exits) instead of a buffer the filter allocates, and run
+ * as a choose/set launch pair per batch rather than one persistent launch,
+ * so they are somewhat slower than blowchoc_insert; smaller batches and
+ * B = 1 need no scratch at all.
+ *  - Limit: min(B, n) <= 4,194,304 keys for batches on the fixed array;
+ *    larger batches are rejected with EINVAL and a message naming the limit.
+ *  - B = 1 runs the one-warp sequential kernel and 2 <= B <= 16 the one-CTA
+ *    batch loop: the tuning's seq_window is not used, because the exact
+ *    reservation kernels need a reservation buffer (one word per block) that
+ *    would have to be allocated. Results are the same.
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture. Call with the filter's device current.
+ *    before any stream capture. Call with the filter's device current. The
+ *    address is kept for the life of the process: after a device reset
+ *    (cudaDeviceReset) it is stale, and this call must not be used again.
  *  - Calls no cudaMalloc, cudaFree or allocating library routine.
  *  - All calls on a device share the one array: two of these calls whose
  *    work overlaps on the GPU (different streams, no ordering between them)
@@ -223,6 +233,64 @@ int blowchoc_multipliers(blowchoc_filter *f, uint64_t *a_block, uint64_t *a_bit)
  * Errors: EINVAL (NULL, the parameters blowchoc_create rejects).
  */
 int blowchoc_derive_multipliers(const blowchoc_params *params, uint64_t *a_block, uint64_t *a_bit);
+
+/*
+ * ---- Sub-arrays (Section 3.4, parallelization) ----------------------------
+ * A filter of M blocks can be split into T sub-arrays of ceil(M / T) blocks
+ * each, one writer per sub-array (one GPU per sub-array, or all of them on
+ * one GPU): an additional linear hash h_0 : U -> [T] with multiplier a_0
+ * (same range rules as the block hashes) routes a key to its sub-array, and
+ * the block hashes h_1..h_c address [ceil(M / T)] inside it. A sub-array is
+ * an ordinary filter (blowchoc_create) of ceil(M / T) blocks whose hash seed
+ * is the generator state after a_0 was drawn; each inserts the keys routed
+ * to it in their order, in its own batches of B. T = 1 is the unsplit filter.
+ */
+
+/* blowchoc_shard_layout -- host-only: a_0 (the first odd splitmix64 output
+ * of hash_seed coprime to T; 0 for T = 1), the sub-array size ceil(nblocks /
+ * T) and the hash seed of the sub-arrays (the generator state after a_0; the
+ * seed itself for T = 1). Errors: EINVAL (NULL, nblocks = 0, T outside
+ * 1..1024). */
+int blowchoc_shard_layout(uint64_t nblocks, uint32_t T, uint64_t hash_seed, uint64_t *a0, uint64_t *sub_nblocks,
+                          uint64_t *sub_seed);
+
+/* blowchoc_shard_partition_scratch -- *words = uint64 words of scratch that
+ * blowchoc_shard_partition needs for n keys and T sub-arrays. Host-only.
+ * Errors: EINVAL (NULL, T outside 1..1024). */
+int blowchoc_shard_partition_scratch(uint64_t n, uint32_t T, uint64_t *words);
+
+/*
+ * blowchoc_shard_partition -- stable partition of d_keys[0..n) by sub-array
+ * h_0(x) (Section 3.4: the main thread that distributes keys to the
+ * sub-arrays' writers).
+ *   d_out_keys   device, out, n uint64: the keys of sub-array 0, then of
+ *                sub-array 1, ..., each in input order.
+ *   d_out_index  device, out, n uint64: input index of each output key.
+ *   d_offsets    device, out, T + 1 uint64: sub-array t's keys are output
+ *                positions d_offsets[t] .. d_offsets[t + 1] - 1; d_offsets[T] = n.
+ *   d_scratch    device, scratch_words uint64 (blowchoc_shard_partition_scratch),
+ *                owned by the caller, overwritten.
+ * Stream-ordered, asynchronous; three kernels. Errors: EINVAL (NULL buffers
+ * with n > 0, T outside 1..1024, even a0 with T > 1, scratch too small), ECUDA.
+ */
+int blowchoc_shard_partition(const uint64_t *d_keys, uint64_t n, uint32_t T, uint64_t a0, uint64_t *d_out_keys,
+                             uint64_t *d_out_index, uint64_t *d_offsets, uint64_t *d_scratch, uint64_t scratch_words,
+                             void *stream);
+
+/*
+ * blowchoc_shard_unpermute -- the query bitmap in input order from the
+ * sub-arrays' answers in partition order.
+ *   d_seg_bits  device, in: per sub-array t, an LSB-first bitmap of its
+ *               d_offsets[t + 1] - d_offsets[t] keys (as blowchoc_query writes
+ *               it), segments of ceil(count / 64) words in order of t.
+ *   d_offsets, d_index  device, in: from blowchoc_shard_partition.
+ *   d_bitmap    device, out, ceil(n / 64) words: bit d_index[j] set iff the
+ *               j-th partitioned key was reported present; other bits 0.
+ * Stream-ordered. Errors: EINVAL (NULL buffers with n > 0, T outside
+ * 1..1024), ECUDA.
+ */
+int blowchoc_shard_unpermute(const uint64_t *d_seg_bits, const uint64_t *d_offsets, const uint64_t *d_index,
+                             uint64_t n, uint32_t T, uint64_t *d_bitmap, void *stream);
 
 /*
  * blowchoc_set_cost_table -- replace the filter's cost by a table (a learned
@@ -565,7 +633,10 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       reductions (no value returned) of each key's words at L2; 1 = sort by
  *       block: bucket the batch's keys by ranges of 256 blocks, stage each
  *       touched range in shared memory, OR there, write the range back
- *       (offered while ceil(M / 256) <= 65536; larger filters use 0).
+ *       (offered while ceil(M / 256) <= 65536; larger filters use 0); 2 =
+ *       bulk: stage each key's 64-byte mask in shared memory and OR it into
+ *       its block with one asynchronous bulk reduction of the copy engine.
+ *       Default 2 for filters larger than 1.5 times the L2 size, else 0.
  *   seq_window: B = 1 (one key at a time) runs in parallel while staying
  *       exactly sequential: windows of seq_window keys (32..8192) go through
  *       rounds in which every pending key reserves its candidate blocks (the
@@ -627,11 +698,67 @@ int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t);
 int blowchoc_server_set_tuning(blowchoc_server *s, const blowchoc_tuning *t);
 
 /*
+ * ---- Per-size-class launch configuration of a batch object ----------------
+ * A many-filter call treats each filter according to its size class, from
+ * its bytes (64 M) against the device's L2 size:
+ *   BLOWCHOC_CLASS_CACHE  64 M <= L2 / 16  (a few of them fit L2 at once)
+ *   BLOWCHOC_CLASS_L2     64 M <= L2 / 2
+ *   BLOWCHOC_CLASS_SPILL  64 M <= 2 L2     (partly L2-resident)
+ *   BLOWCHOC_CLASS_HBM    larger           (HBM-resident)
+ * and keeps one configuration per (class, k, c): the class tuning below. A
+ * filter whose (class, k, c) has none uses the batch object's tuning (route
+ * 0, its lanes, 128 keys per tile). Results never depend on the choice.
+ */
+enum {
+    BLOWCHOC_CLASS_CACHE = 0,
+    BLOWCHOC_CLASS_L2 = 1,
+    BLOWCHOC_CLASS_SPILL = 2,
+    BLOWCHOC_CLASS_HBM = 3,
+    BLOWCHOC_NUM_CLASSES = 4
+};
+enum {
+    BLOWCHOC_ROUTE_WORKLIST = 0,  /* inserted over the many-filter work list */
+    BLOWCHOC_ROUTE_DIRECT = 1,    /* blowchoc_insert with the direct (atomic OR) set */
+    BLOWCHOC_ROUTE_SORTED = 2     /* blowchoc_insert with the sort-by-block set */
+};
+typedef struct {
+    uint32_t route;         /* BLOWCHOC_ROUTE_*: how the class's inserts run */
+    uint32_t lanes_choose;  /* work-list insert: lanes per key, 1, 2, 4 or 8 */
+    uint32_t tile;          /* work-list insert: keys per tile, 32 .. 1024, a power of two */
+    uint32_t lanes_query;   /* work-list query: lanes per key, 1, 2, 4 or 8 */
+    uint32_t query_early;   /* work-list query: 1 = stop at the first candidate holding the key */
+} blowchoc_class_tuning;
+
+/* Size class (BLOWCHOC_CLASS_*) of a filter of `nblocks` blocks on the batch
+ * object's device. Errors: EINVAL (NULL). */
+int blowchoc_batch_size_class(blowchoc_batch *b, uint64_t nblocks, uint32_t *cls);
+
+/* The configuration of (cls, k, c): *is_set = 1 if one was set or tuned,
+ * else 0 and *out holds the defaults that apply. Errors: EINVAL. */
+int blowchoc_batch_get_class_tuning(blowchoc_batch *b, uint32_t cls, uint32_t k, uint32_t c,
+                                    blowchoc_class_tuning *out, uint32_t *is_set);
+
+/* Set the configuration of (cls, k, c); every field is checked and nothing
+ * changes on error. A recorded graph keeps the configuration it was recorded
+ * with. Errors: EINVAL. */
+int blowchoc_batch_set_class_tuning(blowchoc_batch *b, uint32_t cls, uint32_t k, uint32_t c,
+                                    const blowchoc_class_tuning *t);
+
+/* Forget every class configuration. Errors: EINVAL (NULL). */
+int blowchoc_batch_clear_class_tuning(blowchoc_batch *b);
+
+/*
  * blowchoc_batch_autotune -- time insert_many + query_many of `ins` / `qry`
  * on scratch copies of the filters (same parameters, empty; the callers'
- * filters are not touched) for a set of launch configurations, keep the
- * fastest on the batch object and return it in *best (may be NULL). Results
- * never depend on the choice. Synchronises `stream`. Errors: EINVAL, ENOMEM,
+ * filters are not touched). First the batch object's tuning: lanes per key
+ * for insert and query and CTAs per SM over the whole call. Then, for every
+ * (size class, k, c) present, one dimension at a time on that class's
+ * filters alone: lanes per key and keys per tile of the work-list insert,
+ * the route (work list, direct or sort-by-block single-filter insert), and
+ * lanes per key and early exit of the query. The fastest of each is kept on
+ * the batch object (class tunings cached per (class, k, c) for later calls)
+ * and the batch tuning is returned in *best (may be NULL). Results never
+ * depend on the choices. Synchronises `stream`. Errors: EINVAL, ENOMEM,
  * ECUDA.
  */
 int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_t n_ins,
@@ -642,12 +769,15 @@ int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_
  * blowchoc_gather_probe -- measurement aid, not part of the filter: reads
  * nreads pseudo-random whole 64-byte blocks of d_words[0 .. 8 nblocks) (the
  * access pattern of insert and query) with `lanes` lanes per block (1, 2, 4
- * or 8) on SMs x ctas_per_sm CTAs, and writes one folded word per warp to
- * d_sink (at least SMs x ctas_per_sm x 8 words). Timed by the caller, it
- * gives the random-sector ceiling of the device. Errors: EINVAL, ECUDA.
+ * or 8) on SMs x ctas_per_sm CTAs, each lane group keeping `inflight` (1, 2,
+ * 4 or 8) independent block loads in flight before folding them, and writes
+ * one folded word per warp to d_sink (at least SMs x ctas_per_sm x 8 words).
+ * Timed by the caller, it gives the random-sector ceiling of the device.
+ * Errors: EINVAL, ECUDA.
  */
 int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, uint64_t nreads, uint64_t seed,
-                          uint32_t lanes, uint32_t ctas_per_sm, uint64_t *d_sink, void *stream);
+                          uint32_t lanes, uint32_t ctas_per_sm, uint32_t inflight, uint64_t *d_sink,
+                          void *stream);
 
 /*
  * blowchoc_barrier_selftest -- diagnostic of the bounded device waits, not

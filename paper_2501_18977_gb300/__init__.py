@@ -19,6 +19,10 @@ from .binding import (  # noqa: F401
     blowchoc_work, Batch, blowchoc_batch_create, blowchoc_batch_destroy, blowchoc_insert_many,
     blowchoc_query_many, blowchoc_batch_record, blowchoc_batch_replay, blowchoc_batch_get_tuning,
     blowchoc_batch_set_tuning, blowchoc_batch_autotune, Server, blowchoc_server_config,
+    blowchoc_class_tuning, blowchoc_batch_size_class, blowchoc_batch_get_class_tuning,
+    blowchoc_batch_set_class_tuning, blowchoc_batch_clear_class_tuning, CLASS_CACHE, CLASS_L2, CLASS_SPILL,
+    CLASS_HBM, ROUTE_WORKLIST, ROUTE_DIRECT, ROUTE_SORTED, blowchoc_shard_layout,
+    blowchoc_shard_partition_scratch, blowchoc_shard_partition, blowchoc_shard_unpermute,
     blowchoc_server_summary, REQ_INSERT, REQ_QUERY, Mlp, blowchoc_insert_sampled,
     blowchoc_barrier_selftest,
     load_library, exported_symbols, LIB_PATH)

@@ -51,6 +51,11 @@ class blowchoc_tuning(ctypes.Structure):
                 ("lanes_cluster", ctypes.c_uint32), ("cluster_keys", ctypes.c_uint32)]
 
 
+class blowchoc_class_tuning(ctypes.Structure):
+    _fields_ = [("route", ctypes.c_uint32), ("lanes_choose", ctypes.c_uint32), ("tile", ctypes.c_uint32),
+                ("lanes_query", ctypes.c_uint32), ("query_early", ctypes.c_uint32)]
+
+
 class blowchoc_work(ctypes.Structure):
     _fields_ = [("filter", ctypes.c_void_p), ("d_keys", ctypes.c_void_p),
                 ("n", ctypes.c_uint64), ("d_bitmap", ctypes.c_void_p)]
@@ -111,6 +116,17 @@ _SIGS = {
     "blowchoc_batch_autotune": ([_VP, ctypes.POINTER(blowchoc_work), ctypes.c_uint32,
                                  ctypes.POINTER(blowchoc_work), ctypes.c_uint32, _VP,
                                  ctypes.POINTER(blowchoc_tuning)], _I),
+    "blowchoc_shard_layout": ([_U64, ctypes.c_uint32, _U64, ctypes.POINTER(_U64), ctypes.POINTER(_U64),
+                               ctypes.POINTER(_U64)], _I),
+    "blowchoc_shard_partition_scratch": ([_U64, ctypes.c_uint32, ctypes.POINTER(_U64)], _I),
+    "blowchoc_shard_partition": ([_VP, _U64, ctypes.c_uint32, _U64, _VP, _VP, _VP, _VP, _U64, _VP], _I),
+    "blowchoc_shard_unpermute": ([_VP, _VP, _VP, _U64, ctypes.c_uint32, _VP, _VP], _I),
+    "blowchoc_batch_size_class": ([_VP, _U64, ctypes.POINTER(ctypes.c_uint32)], _I),
+    "blowchoc_batch_get_class_tuning": ([_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.POINTER(blowchoc_class_tuning), ctypes.POINTER(ctypes.c_uint32)], _I),
+    "blowchoc_batch_set_class_tuning": ([_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.POINTER(blowchoc_class_tuning)], _I),
+    "blowchoc_batch_clear_class_tuning": ([_VP], _I),
     "blowchoc_server_create": ([ctypes.POINTER(blowchoc_server_config), ctypes.POINTER(_VP)], _I),
     "blowchoc_server_add_filter": ([_VP, ctypes.POINTER(blowchoc_params), ctypes.POINTER(ctypes.c_uint32)], _I),
     "blowchoc_server_remove_filter": ([_VP, ctypes.c_uint32], _I),
@@ -134,7 +150,8 @@ _SIGS = {
     "blowchoc_mlp_adam_step": ([_VP, ctypes.c_float, _VP], _I),
     "blowchoc_insert_sampled": ([_VP, _VP, _U64, _VP, ctypes.c_float, _U64, _VP, _VP, _VP], _I),
     "blowchoc_barrier_selftest": ([ctypes.c_uint32, ctypes.c_double, _VP], _I),
-    "blowchoc_gather_probe": ([_VP, _U64, _U64, _U64, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP], _I),
+    "blowchoc_gather_probe": ([_VP, _U64, _U64, _U64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                               _VP, _VP], _I),
     "blowchoc_get_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
     "blowchoc_set_tuning": ([_VP, ctypes.POINTER(blowchoc_tuning)], _I),
 }
@@ -346,9 +363,9 @@ def blowchoc_set_tuning(f, t: blowchoc_tuning):
 
 
 def blowchoc_gather_probe(d_words, nblocks: int, nreads: int, seed: int, lanes: int,
-                          ctas_per_sm: int, d_sink, stream=None):
+                          ctas_per_sm: int, d_sink, stream=None, inflight: int = 1):
     _check(load_library().blowchoc_gather_probe(_dev_ptr(d_words), int(nblocks), int(nreads),
-                                                int(seed), int(lanes), int(ctas_per_sm),
+                                                int(seed), int(lanes), int(ctas_per_sm), int(inflight),
                                                 _dev_ptr(d_sink), _stream(stream)))
 
 
@@ -413,6 +430,60 @@ def blowchoc_batch_autotune(b, ins, qry, stream=None) -> blowchoc_tuning:
     return out
 
 
+def blowchoc_shard_layout(nblocks: int, T: int, hash_seed: int):
+    """(a_0, blocks per sub-array, hash seed of the sub-arrays) of a filter of
+    nblocks blocks split into T sub-arrays (host-only)."""
+    a0, ms, seed = _U64(), _U64(), _U64()
+    _check(load_library().blowchoc_shard_layout(int(nblocks), int(T), int(hash_seed) & 0xFFFFFFFFFFFFFFFF,
+                                                ctypes.byref(a0), ctypes.byref(ms), ctypes.byref(seed)))
+    return a0.value, ms.value, seed.value
+
+
+def blowchoc_shard_partition_scratch(n: int, T: int) -> int:
+    out = _U64()
+    _check(load_library().blowchoc_shard_partition_scratch(int(n), int(T), ctypes.byref(out)))
+    return out.value
+
+
+def blowchoc_shard_partition(d_keys, n: int, T: int, a0: int, d_out_keys, d_out_index, d_offsets, d_scratch,
+                             scratch_words: int, stream=None):
+    _check(load_library().blowchoc_shard_partition(_dev_ptr(d_keys), int(n), int(T), int(a0), _dev_ptr(d_out_keys),
+                                                   _dev_ptr(d_out_index), _dev_ptr(d_offsets), _dev_ptr(d_scratch),
+                                                   int(scratch_words), _stream(stream)))
+
+
+def blowchoc_shard_unpermute(d_seg_bits, d_offsets, d_index, n: int, T: int, d_bitmap, stream=None):
+    _check(load_library().blowchoc_shard_unpermute(_dev_ptr(d_seg_bits), _dev_ptr(d_offsets), _dev_ptr(d_index),
+                                                   int(n), int(T), _dev_ptr(d_bitmap), _stream(stream)))
+
+
+CLASS_CACHE, CLASS_L2, CLASS_SPILL, CLASS_HBM = 0, 1, 2, 3
+ROUTE_WORKLIST, ROUTE_DIRECT, ROUTE_SORTED = 0, 1, 2
+
+
+def blowchoc_batch_size_class(b, nblocks: int) -> int:
+    out = ctypes.c_uint32()
+    _check(load_library().blowchoc_batch_size_class(b, int(nblocks), ctypes.byref(out)))
+    return out.value
+
+
+def blowchoc_batch_get_class_tuning(b, cls: int, k: int, c: int):
+    """(blowchoc_class_tuning, is_set) of (size class, k, c)."""
+    out = blowchoc_class_tuning()
+    is_set = ctypes.c_uint32()
+    _check(load_library().blowchoc_batch_get_class_tuning(b, int(cls), int(k), int(c), ctypes.byref(out),
+                                                          ctypes.byref(is_set)))
+    return out, bool(is_set.value)
+
+
+def blowchoc_batch_set_class_tuning(b, cls: int, k: int, c: int, t: blowchoc_class_tuning):
+    _check(load_library().blowchoc_batch_set_class_tuning(b, int(cls), int(k), int(c), ctypes.byref(t)))
+
+
+def blowchoc_batch_clear_class_tuning(b):
+    _check(load_library().blowchoc_batch_clear_class_tuning(b))
+
+
 class Batch:
     """Owning handle of a many-filter batch object."""
 
@@ -453,6 +524,23 @@ class Batch:
 
     def autotune(self, ins, qry, stream=None):
         return blowchoc_batch_autotune(self.handle, ins, qry, stream)
+
+    def size_class(self, nblocks):
+        return blowchoc_batch_size_class(self.handle, nblocks)
+
+    def class_tuning(self, cls, k, c):
+        """(fields as a dict, is_set) of (size class, k, c)."""
+        t, is_set = blowchoc_batch_get_class_tuning(self.handle, cls, k, c)
+        return {name: int(getattr(t, name)) for name, _ in t._fields_}, is_set
+
+    def set_class_tuning(self, cls, k, c, **kw):
+        t, _ = blowchoc_batch_get_class_tuning(self.handle, cls, k, c)
+        for name, v in kw.items():
+            setattr(t, name, int(v))
+        blowchoc_batch_set_class_tuning(self.handle, cls, k, c, t)
+
+    def clear_class_tuning(self):
+        blowchoc_batch_clear_class_tuning(self.handle)
 
 
 class Server:

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
     constexpr int W = kBlockWords / LANES;    // words per lane
     constexpr int TC = kClThreads / LANES;    // groups per CTA
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kClThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kClThreads / 32) * mask_u32_per_warp<LANES>()];
     // dynamic: the slice's words | two key buffers of kpc keys (one batch's
     // keys of this CTA, the next batch's arriving) | rank table | kpc choices
     extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
     cluster_sync();  // every slice loaded before any CTA reads another's
 
     const int lane = threadIdx.x & 31, q = lane % LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + lane / LANES) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
     const uint32_t gl = threadIdx.x / LANES;  // group within the CTA
     const int lead = lane & ~(LANES - 1);     // the group's first lane
     static_assert(LANES >= C, "a group locates its candidates one per lane");

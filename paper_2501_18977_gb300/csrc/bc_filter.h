@@ -43,5 +43,9 @@ void bc_note_launch();
 // Records msg as the calling thread's last error (blowchoc_last_error); returns code.
 int bc_set_error(int code, const char *msg);
 
+// Allocates the device scratch that blowchoc_insert of n keys into f would
+// allocate on first use, without launching (for graph capture).
+extern "C" int bc_reserve_insert_scratch(blowchoc_filter *f, uint64_t n);
+
 // Checks the fields of a filter launch configuration; EINVAL with a message.
 extern "C" int bc_check_tuning(const blowchoc_tuning *t);

@@ -22,12 +22,12 @@ __global__ void __launch_bounds__(kThreads) choose_kernel(DevFilter f, const uin
     constexpr int W = kBlockWords / LANES;
     extern __shared__ uint16_t s_rank[];
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * mask_u32_per_warp<LANES>()];
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t ins = 0, skp = 0;
@@ -52,11 +52,11 @@ __global__ void __launch_bounds__(kThreads) set_kernel(DevFilter f, const uint64
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * mask_u32_per_warp<LANES>()];
     stage_bit_mults(f, s_amul);
     __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t base = warp * G; base < n; base += nwarps * G) {
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(32) sequential_kernel(DevFilter f, const uint6
 constexpr int kSmallThreads = 1024;
 
 template <int LANES>
-constexpr size_t small_mask_bytes() { return (kSmallThreads / 32) * (32 / LANES) * region_u32<LANES>() * 4; }
+constexpr size_t small_mask_bytes() { return (kSmallThreads / 32) * mask_u32_per_warp<LANES>() * 4; }
 
 template <int C, int LANES>
 __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f, const uint64_t *__restrict__ keys,
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint32_t ins = 0, skp = 0;
     for (uint64_t s0 = 0; s0 < n; s0 += B) {
@@ -185,21 +185,43 @@ constexpr int persistent_threads() { return LANES == 1 ? 256 : 512; }
 template <int LANES>
 constexpr int persistent_min_ctas() { return LANES == 1 ? 2 : 1024 / persistent_threads<LANES>(); }
 
-template <int C, int LANES>
+// Bulk set (set_mode 2): the set phase stages each key's mask in a 64-byte
+// slot and ORs it into the chosen block with one bulk reduction (the copy
+// engine's cp.reduce.async.bulk) instead of a 64-bit red per word. A lane
+// group cycles through kBulkRing slots, so a slot is rewritten only after
+// the reduction issued kBulkRing keys earlier has read it. Measured on one
+// GB300 against the red path: 512 MiB filter (c = 2, four lanes) 29.5 against
+// 30.6 ms; the 128 MiB DNA filter 4.24 against 3.77 ms and a 2 MiB filter
+// 0.174 against 0.164 ms, so it is the default only beyond 1.5 times L2.
+constexpr int kBulkRing = 4;
+template <int LANES>
+constexpr size_t bulk_ring_bytes() {
+    return (size_t)(persistent_threads<LANES>() / LANES) * kBulkRing * 64;
+}
+// Offset of the slot ring in the dynamic shared memory, after the rank table.
+__host__ __device__ inline size_t bulk_ring_offset(int C, uint32_t k) {
+    return ((C > 1 ? 513u * (k + 1) * 2u : 0u) + 127u) & ~(size_t)127;
+}
+
+template <int C, int LANES, bool BULK>
 __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ctas<LANES>()) persistent_insert_kernel(
     DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
     const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters,
     unsigned int *bar) {
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
-    extern __shared__ uint16_t s_rank[];
+    extern __shared__ __align__(16) uint8_t s_dyn[];  // rank table | bulk slot ring (16-byte aligned slots)
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_dyn);
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(persistent_threads<LANES>() / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(persistent_threads<LANES>() / 32) * mask_u32_per_warp<LANES>()];
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
+    uint32_t *ring = reinterpret_cast<uint32_t *>(s_dyn + bulk_ring_offset(C, f.k)) +
+                     (size_t)(threadIdx.x / LANES) * (kBulkRing * 16);  // used with BULK only
+    uint32_t slot_i = 0;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     uint16_t *sel16 = reinterpret_cast<uint16_t *>(sel);  // choice | words with new bits << 8
@@ -222,7 +244,7 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
             // measured faster for them (the flags cost registers)
             uint32_t words = 0xFFu;
             uint32_t s;
-            if constexpr (LANES <= 2)
+            if constexpr (LANES <= 2 && !BULK)
                 s = choose_key_words<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m, words);
             else
                 s = choose_key<C, LANES, kLoadCG>(f, x, valid, q, rank, s_amul, region, m);
@@ -244,9 +266,35 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
             swn = i + stride < cnt ? (uint32_t)__ldcg(sel16 + i + stride) : kSkip;
             xs = i + stride < cnt ? load_key(keys + s0 + i + stride) : 0ull;
             const uint32_t s = sw & 0xFFu;
-            uint64_t m[W];
-            key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
-            if (s != kSkip) set_words<LANES>(f, block_addr(f, block_mult(f, s), x), q, m, sw >> 8);
+            if constexpr (BULK) {
+                // the group's next slot, free once the reduction that last
+                // read it has (the group's first lane issued and waits for those)
+                uint32_t *slot = ring + (slot_i % kBulkRing) * 16;
+                ++slot_i;
+                if (q == 0) bulk_wait_read<kBulkRing - 1>();
+                __syncwarp();
+                uint64_t *s64 = reinterpret_cast<uint64_t *>(slot);
+#pragma unroll
+                for (int j = 0; j < W; ++j) s64[q * W + j] = 0ull;
+                __syncwarp();
+                mask_into_slot<LANES>(s_amul, f.k, x, q, slot, f.bitsel);
+                fence_proxy_async_shared();
+                __syncwarp();
+                if (q == 0) {
+                    if (s != kSkip) bulk_or_block(f.words + block_addr(f, block_mult(f, s), x) * kBlockWords, slot);
+                    bulk_commit();
+                }
+            } else {
+                uint64_t m[W];
+                key_mask_shared<LANES>(s_amul, f.k, x, q, region, m, f.bitsel);
+                if (s != kSkip) set_words<LANES>(f, block_addr(f, block_mult(f, s), x), q, m, sw >> 8);
+            }
+        }
+        if constexpr (BULK) {
+            // every reduction of this batch has reached global memory before
+            // the barrier that lets the next batch choose
+            if (q == 0) bulk_wait_all();
+            fence_proxy_async_global();
         }
         if (s0 + B < n) {
             target += gridDim.x;
@@ -255,6 +303,10 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
     }
     flush_counts(ins, skp, counters);
 }
+
+#ifndef BC_SORTED_BULK
+#define BC_SORTED_BULK 0
+#endif
 
 // ---------------------------------------------------------------------------
 // Sort-by-block set variant. After the choose phase of a batch, the chosen
@@ -277,14 +329,23 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
     uint32_t *s_range32 = reinterpret_cast<uint32_t *>(s_dyn);
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_dyn + kRangeBlocks * 64);
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * mask_u32_per_warp<LANES>()];
     __shared__ uint32_t s_part[kThreads];
+#if BC_SORTED_BULK
+    __shared__ uint64_t s_mbar;
+    uint32_t phase = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar, 1);
+        fence_proxy_async_shared();
+    }
+    __syncthreads();
+#endif
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
     const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, wib);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -318,25 +379,33 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
         }
         target += gridDim.x;
         if (!grid_barrier(bar, target, err)) return;
-        // exclusive scan of the counts (one CTA), cursors to zero
+        // exclusive scan of the counts (one CTA: each thread sums a run of
+        // ranges, a shuffle scan over the threads' sums), cursors to zero
         if (blockIdx.x == 0) {
             const uint32_t per = (R + blockDim.x - 1) / blockDim.x;
             const uint32_t lo = threadIdx.x * per, hi = lo + per < R ? lo + per : R;
             uint32_t sum = 0;
             for (uint32_t r = lo; r < hi; ++r) sum += __ldcg(cnt + r);
-            s_part[threadIdx.x] = sum;
+            uint32_t v = sum;  // inclusive scan within the warp
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t u = __shfl_up_sync(kFull, v, d);
+                if (lane >= d) v += u;
+            }
+            if (lane == 31) s_part[wib] = v;
             __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t acc = 0;
-                for (int t = 0; t < (int)blockDim.x; ++t) {
-                    const uint32_t v = s_part[t];
-                    s_part[t] = acc;
-                    acc += v;
+            if (wib == 0) {
+                uint32_t t = lane < wpc ? s_part[lane] : 0u;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t u = __shfl_up_sync(kFull, t, d);
+                    if (lane >= d) t += u;
                 }
-                off[R] = acc;
+                if (lane < wpc) s_part[lane] = t;  // inclusive over warps
+                if (lane == wpc - 1) off[R] = t;
             }
             __syncthreads();
-            uint32_t acc = s_part[threadIdx.x];
+            uint32_t acc = v - sum + (wib ? s_part[wib - 1] : 0u);
             for (uint32_t r = lo; r < hi; ++r) {
                 off[r] = acc;
                 acc += __ldcg(cnt + r);
@@ -363,7 +432,23 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
             const uint64_t first = (uint64_t)r * kRangeBlocks;
             const uint64_t nb = f.M - first < kRangeBlocks ? f.M - first : kRangeBlocks;
             const uint64_t *src = f.words + first * kBlockWords;
+#if BC_SORTED_BULK
+            // one bulk copy of the range (after the previous range's write-back
+            // has read the staging area), counted on the CTA's mbarrier
+            if (threadIdx.x == 0) {
+                bulk_wait_read<0>();
+                mbar_arrive_expect_tx(&s_mbar, (uint32_t)(nb * 64));
+                bulk_load(s_range, src, (uint32_t)(nb * 64), &s_mbar);
+            }
+            if (!mbar_wait(&s_mbar, phase, kBarrierCycles)) {
+                atomicExch(err, 1ull);
+                mbar_wait(&s_mbar, phase, kBarrierCycles);  // the copy in flight, bounded again
+                return;
+            }
+            phase ^= 1u;
+#else
             for (uint32_t w = threadIdx.x; w < nb * kBlockWords; w += blockDim.x) s_range[w] = __ldcg(src + w);
+#endif
             __syncthreads();
             for (uint32_t base = c0 + wib * G; base < c1; base += wpc * G) {
                 const uint32_t idx = base + g;
@@ -385,9 +470,22 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
             }
             __syncthreads();
             uint64_t *dst = f.words + first * kBlockWords;
+#if BC_SORTED_BULK
+            fence_proxy_async_shared();  // every thread's ORs, visible to the bulk copy
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bulk_store(dst, s_range, (uint32_t)(nb * 64));
+                bulk_commit();
+            }
+#else
             for (uint32_t w = threadIdx.x; w < nb * kBlockWords; w += blockDim.x) dst[w] = s_range[w];
             __syncthreads();
+#endif
         }
+#if BC_SORTED_BULK
+        if (threadIdx.x == 0) bulk_wait_all();  // the batch's ranges are written
+        fence_proxy_async_global();
+#endif
         if (s0 + B < n) {
             target += gridDim.x;
             if (!grid_barrier(bar, target, err)) return;
@@ -419,14 +517,14 @@ __global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
     uint8_t *s_state = s_dyn + (size_t)window * 8;                           // 1 = pending
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_state + ((window + 15) & ~15u));
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * mask_u32_per_warp<LANES>()];
     __shared__ int s_left;
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
     const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, wib);
     uint32_t ins = 0, skp = 0;
     uint64_t round = 0;
     for (uint64_t s0 = 0; s0 < n; s0 += window) {
@@ -501,14 +599,14 @@ __global__ void __launch_bounds__(kSeqThreads) exact_batched_kernel(
     uint8_t *s_ok = s_sel + wpad;                            // per batch: every key holds its reservations
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_ok + wpad);
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * mask_u32_per_warp<LANES>()];
     __shared__ int s_left;
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
     const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, wib);
     uint32_t ins = 0, skp = 0;
     uint64_t round = 0;
     for (uint64_t s0 = 0; s0 < n; s0 += window) {
@@ -633,15 +731,15 @@ cudaError_t small_dispatch(const Launch &L, const DevFilter &f, const uint64_t *
     }
 }
 
-template <int C, int LANES>
+template <int C, int LANES, bool BULK>
 cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                               uint64_t B, const uint16_t *rank, uint8_t *sel,
                               unsigned long long *counters, unsigned int *bar, int sms) {
-    const size_t sm = rank_bytes(C, f.k);
-    cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES>, sm);
+    const size_t sm = BULK ? bulk_ring_offset(C, f.k) + bulk_ring_bytes<LANES>() : rank_bytes(C, f.k);
+    cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES, BULK>, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES>, persistent_threads<LANES>(), sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES, BULK>, persistent_threads<LANES>(), sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int want = L.grid > 0 ? L.grid : 1;
@@ -650,19 +748,19 @@ cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&f, (void *)&keys, (void *)&n, (void *)&B, (void *)&rank,
                     (void *)&sel, (void *)&counters, (void *)&bar};
-    return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES>, dim3(grid),
+    return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES, BULK>, dim3(grid),
                                        dim3(persistent_threads<LANES>()), args, sm, L.stream);
 }
 
-template <int C>
+template <int C, bool BULK>
 cudaError_t persistent_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                                 uint64_t B, const uint16_t *rank, uint8_t *sel,
                                 unsigned long long *counters, unsigned int *bar, int sms) {
     switch (L.lanes) {
-        case 1: return persistent_launch<C, 1>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 2: return persistent_launch<C, 2>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 4: return persistent_launch<C, 4>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 8: return persistent_launch<C, 8>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 1: return persistent_launch<C, 1, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 2: return persistent_launch<C, 2, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 4: return persistent_launch<C, 4, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 8: return persistent_launch<C, 8, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -771,11 +869,14 @@ cudaError_t launch_sorted_insert(int C, const Launch &L, const DevFilter &f, con
 
 cudaError_t launch_persistent_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                                      uint64_t n, uint64_t B, const uint16_t *rank, uint8_t *sel,
-                                     unsigned long long *counters, unsigned int *bar, int sms) {
+                                     unsigned long long *counters, unsigned int *bar, int sms, bool bulk) {
     switch (C) {
-        case 1: return persistent_dispatch<1>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 2: return persistent_dispatch<2>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 3: return persistent_dispatch<3>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 1: return bulk ? persistent_dispatch<1, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
+                            : persistent_dispatch<1, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 2: return bulk ? persistent_dispatch<2, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
+                            : persistent_dispatch<2, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 3: return bulk ? persistent_dispatch<3, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
+                            : persistent_dispatch<3, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -32,10 +32,12 @@ cudaError_t launch_set(const Launch &L, const DevFilter &f, const uint64_t *keys
 // All batches of one insert in a single cooperative launch (grid barriers
 // between phases; every CTA co-resident). L.grid is the wanted grid, capped
 // at what fits on `sms` SMs. sel holds min(B, n) choices; bar is a zeroed
-// arrival counter; a barrier wait that times out sets counters[2].
+// arrival counter; a barrier wait that times out sets counters[2]. With
+// `bulk` the set phase ORs each key's 64-byte mask in with one bulk
+// reduction (set_mode 2) instead of a 64-bit red per word.
 cudaError_t launch_persistent_insert(int C, const Launch &L, const DevFilter &f, const uint64_t *keys,
                                      uint64_t n, uint64_t B, const uint16_t *rank, uint8_t *sel,
-                                     unsigned long long *counters, unsigned int *bar, int sms);
+                                     unsigned long long *counters, unsigned int *bar, int sms, bool bulk);
 
 // Sort-by-block variant of the persistent insert: blocks per range, and the
 // number of ranges up to which it is offered.
@@ -95,8 +97,8 @@ struct ManyItem {
 // rounds of a work list, and one query launch over its bitmap words.
 uint64_t many_tile();
 cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
-                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
-                               unsigned long long *err, int sms);
+                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, uint32_t tile,
+                               unsigned int *bar, unsigned long long *err, int sms);
 cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
                               uint32_t nitems, const uint32_t *prefix);
 

@@ -147,13 +147,13 @@ __global__ void __launch_bounds__(256) sampled_choose_kernel(bc::DevFilter f, co
     constexpr int W = bc::kBlockWords / LANES;
     extern __shared__ float s_w[];  // 513 (k+1) per-point weights of this CTA
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[8 * G * bc::region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[8 * bc::mask_u32_per_warp<LANES>()];
     const uint32_t k1 = f.k + 1, npts = 513u * k1;
     for (uint32_t t = threadIdx.x; t < npts; t += blockDim.x) s_w[t] = 0.0f;
     bc::stage_bit_mults(f, s_amul);
     __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * bc::region_u32<LANES>();
+    uint32_t *region = bc::warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t ins = 0, skp = 0;

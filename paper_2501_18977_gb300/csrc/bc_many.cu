@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "bc_filter.h"
@@ -22,9 +24,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-// Keys per insert tile: one tile per warp at the grid's 1024 keys of a round
-// per CTA. Tiles of 512 keys left three warps in four idle and measured
-// 13.8 ms for the 256-filter workload against 11.7 with 128 (64: 11.8).
+// Default keys per insert tile (a class tuning may choose another): one tile
+// per warp at the grid's 1024 keys of a round per CTA. Tiles of 512 keys left
+// three warps in four idle and measured 13.8 ms for the 256-filter workload
+// against 11.7 with 128 (64: 11.8).
 constexpr uint64_t kTile = 128;
 
 // Index of the tile's item: the last f with prefix[f] <= t (prefix has
@@ -60,15 +63,15 @@ __device__ __forceinline__ void load_item(const ManyItem *it, DevFilter &f, uint
 template <int C, int LANES>
 __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *__restrict__ items, uint32_t nitems,
                                                                const uint32_t *__restrict__ prefix,
-                                                               uint32_t nrounds, unsigned int *bar,
-                                                               unsigned long long *err) {
+                                                               uint32_t nrounds, uint32_t tile,
+                                                               unsigned int *bar, unsigned long long *err) {
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
     __shared__ uint64_t s_amul[kWarps][32];
-    __shared__ __align__(16) uint32_t s_mask[kWarps * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[kWarps * mask_u32_per_warp<LANES>()];
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
     const int wib = threadIdx.x >> 5;
-    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, wib);
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     unsigned int target = 0;
@@ -84,8 +87,8 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
                 const uint64_t B = it->B, n = it->n;
                 const uint64_t bstart = (uint64_t)r * B;
                 const uint64_t bend = bstart + B < n ? bstart + B : n;
-                const uint64_t start = bstart + (uint64_t)(t - __ldg(pre + fi)) * kTile;
-                const uint64_t cnt = bend - start < kTile ? bend - start : kTile;
+                const uint64_t start = bstart + (uint64_t)(t - __ldg(pre + fi)) * tile;
+                const uint64_t cnt = bend - start < tile ? bend - start : (uint64_t)tile;
                 uint32_t ins = 0, skp = 0;
                 for (uint64_t base = 0; base < cnt; base += G) {
                     const uint64_t i = start + base + g;  // key index within the filter
@@ -130,10 +133,10 @@ __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__
                                                               const uint32_t *__restrict__ prefix) {
     constexpr int G = 32 / LANES;
     __shared__ uint64_t s_amul[kWarps][32];
-    __shared__ __align__(16) uint32_t s_mask[kWarps * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[kWarps * mask_u32_per_warp<LANES>()];
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
     const int wib = threadIdx.x >> 5;
-    uint32_t *region = s_mask + (wib * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, wib);
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t ntiles = __ldg(prefix + nitems);
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__
 
 template <int C, int LANES>
 cudaError_t insert_many_launch(int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
-                               const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
+                               const uint32_t *prefix, uint32_t nrounds, uint32_t tile, unsigned int *bar,
                                unsigned long long *err, int sms) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_many_kernel<C, LANES>,
@@ -165,21 +168,21 @@ cudaError_t insert_many_launch(int grid, cudaStream_t s, const ManyItem *items, 
     const int g = std::min(std::max(grid, 1), per_sm * sms);
     e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&items, (void *)&nitems, (void *)&prefix, (void *)&nrounds, (void *)&bar,
-                    (void *)&err};
+    void *args[] = {(void *)&items, (void *)&nitems, (void *)&prefix, (void *)&nrounds, (void *)&tile,
+                    (void *)&bar, (void *)&err};
     return cudaLaunchCooperativeKernel((const void *)insert_many_kernel<C, LANES>, dim3(g), dim3(kThreads),
                                        args, 0, s);
 }
 
 template <int C>
 cudaError_t insert_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
-                                 const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
+                                 const uint32_t *prefix, uint32_t nrounds, uint32_t tile, unsigned int *bar,
                                  unsigned long long *err, int sms) {
     switch (lanes) {
-        case 1: return insert_many_launch<C, 1>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
-        case 2: return insert_many_launch<C, 2>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
-        case 4: return insert_many_launch<C, 4>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
-        case 8: return insert_many_launch<C, 8>(grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 1: return insert_many_launch<C, 1>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 2: return insert_many_launch<C, 2>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 4: return insert_many_launch<C, 4>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 8: return insert_many_launch<C, 8>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -200,12 +203,12 @@ cudaError_t query_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyI
 }  // namespace
 
 cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
-                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, unsigned int *bar,
-                               unsigned long long *err, int sms) {
+                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, uint32_t tile,
+                               unsigned int *bar, unsigned long long *err, int sms) {
     switch (C) {
-        case 1: return insert_many_dispatch<1>(lanes, grid, s, items, nitems, prefix, nrounds, bar, err, sms);
-        case 2: return insert_many_dispatch<2>(lanes, grid, s, items, nitems, prefix, nrounds, bar, err, sms);
-        case 3: return insert_many_dispatch<3>(lanes, grid, s, items, nitems, prefix, nrounds, bar, err, sms);
+        case 1: return insert_many_dispatch<1>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 2: return insert_many_dispatch<2>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 3: return insert_many_dispatch<3>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -245,6 +248,9 @@ struct ManyPlan {
         size_t prefix0;           // offset in the prefix array
         uint32_t nrounds;         // insert only
         uint64_t keys;            // keys of the group's items
+        int lanes;                // lanes per key of the group's launch
+        uint32_t tile;            // insert: keys per tile
+        int early;                // query: stop at the first candidate holding the key
     };
     struct Slot {
         ManyItem *d_items = nullptr, *h_items = nullptr;
@@ -267,6 +273,7 @@ struct ManyPlan {
     };
     std::vector<ClusterGroup> cgroups;
     std::vector<blowchoc_work> side;  // items run by the single-filter kernels
+    std::vector<int> side_mode;       // per side item: -1 the filter's own tuning, else its set_mode
 };
 
 void free_plan(ManyPlan &p) {
@@ -295,6 +302,8 @@ struct blowchoc_batch {
     // filters spreads every round over all SMs, which measured faster than one
     // cluster per filter (256 lognormal filters: 18.3 ms against 20.8-33 ms)
     int cluster_max = 0, lanes_cluster = 8, cluster_keys = 128;
+    uint64_t l2_bytes = 0;  // the device's L2, for the size classes
+    std::map<uint64_t, blowchoc_class_tuning> ctune;  // per (size class, k, c)
 };
 
 namespace {
@@ -305,7 +314,36 @@ namespace {
 // through the single-filter kernels on the same stream instead, so that it
 // does not hold every other item of the launch behind its rounds.
 constexpr uint64_t kManyMinRounds = 64;
-constexpr uint64_t kManyKeysPerCta = 1024;
+constexpr uint64_t kManyWarpsPerCta = 8;  // the work-list kernels' 256-thread CTAs
+
+uint32_t size_class_of(const blowchoc_batch *b, uint64_t M) {
+    const uint64_t bytes = 64 * M;
+    const uint64_t l2 = b->l2_bytes ? b->l2_bytes : (126ull << 20);
+    if (bytes <= l2 / 16) return BLOWCHOC_CLASS_CACHE;
+    if (bytes <= l2 / 2) return BLOWCHOC_CLASS_L2;
+    if (bytes <= 2 * l2) return BLOWCHOC_CLASS_SPILL;
+    return BLOWCHOC_CLASS_HBM;
+}
+
+uint64_t class_key(uint32_t cls, uint32_t k, uint32_t c) {
+    return ((uint64_t)cls << 40) | ((uint64_t)k << 8) | (uint64_t)c;
+}
+
+blowchoc_class_tuning default_class(const blowchoc_batch *b) {
+    blowchoc_class_tuning t;
+    t.route = BLOWCHOC_ROUTE_WORKLIST;
+    t.lanes_choose = (uint32_t)b->lanes_choose;
+    t.tile = (uint32_t)bc::many_tile();
+    t.lanes_query = (uint32_t)b->lanes_query;
+    t.query_early = (uint32_t)b->query_early;
+    return t;
+}
+
+// The configuration a filter runs with in a many-filter call.
+blowchoc_class_tuning class_tuning(const blowchoc_batch *b, const blowchoc_filter *f) {
+    const auto it = b->ctune.find(class_key(size_class_of(b, f->dev.M), f->dev.k, f->p.choices));
+    return it == b->ctune.end() ? default_class(b) : it->second;
+}
 
 uint64_t rounds_of(const blowchoc_work &w) {
     const uint64_t B = w.filter->p.batch;
@@ -423,14 +461,14 @@ int prepare(const blowchoc_batch *b, ManyPlan &p, const blowchoc_work *items, ui
     p.groups.clear();
     p.cgroups.clear();
     p.side.clear();
+    p.side_mode.clear();
     std::vector<ManyItem> list;
     std::vector<uint32_t> prefix;
-    std::vector<size_t> sel_off;
-    size_t sel_total = 0;
     const uint64_t cap = query ? 0 : round_cap(items, count);
     for (int C = 1; C <= 3; ++C) {
-        ManyPlan::Group g{C, (uint32_t)list.size(), 0, prefix.size(), 0, 0};
-        std::vector<ManyItem> mine;
+        // work-list items by launch configuration: (lanes, tile) for inserts,
+        // (lanes, early exit) for queries, from each filter's class tuning
+        std::map<std::pair<int, uint32_t>, std::vector<ManyItem>> buckets;
         std::vector<std::pair<int, ManyItem>> clustered;  // (CTAs per cluster, item)
         for (uint32_t i = 0; i < count; ++i) {
             const blowchoc_work &w = items[i];
@@ -448,14 +486,18 @@ int prepare(const blowchoc_batch *b, ManyPlan &p, const blowchoc_work *items, ui
             }
             if (!query && side_path(w, cap)) {
                 p.side.push_back(w);
+                p.side_mode.push_back(-1);
                 continue;
             }
-            const ManyItem it = make_item(w);
-            if (!query) {
-                sel_off.push_back(sel_total);
-                sel_total += (std::min(it.B, it.n) + 15) & ~uint64_t(15);
+            const blowchoc_class_tuning ct = class_tuning(b, w.filter);
+            if (!query && ct.route != BLOWCHOC_ROUTE_WORKLIST) {
+                p.side.push_back(w);
+                p.side_mode.push_back(ct.route == BLOWCHOC_ROUTE_SORTED ? 1 : 0);
+                continue;
             }
-            mine.push_back(it);
+            const std::pair<int, uint32_t> key =
+                query ? std::make_pair((int)ct.lanes_query, ct.query_early) : std::make_pair((int)ct.lanes_choose, ct.tile);
+            buckets[key].push_back(make_item(w));
         }
         // clustered items: launches of equal cluster size, packed while one
         // shared-memory layout (largest slice, rank table, choice bytes) fits
@@ -484,44 +526,59 @@ int prepare(const blowchoc_batch *b, ManyPlan &p, const blowchoc_work *items, ui
             }
             p.cgroups.push_back(cg);
         }
-        g.item0 = (uint32_t)list.size();
-        if (mine.empty()) continue;
-        g.nitems = (uint32_t)mine.size();
-        for (const ManyItem &it : mine) g.keys += it.n;
-        if (query) {
-            prefix.push_back(0);
-            for (const ManyItem &it : mine) {
-                const uint64_t next = prefix.back() + (it.n + 63) / 64;
-                if (next > 0xFFFFFFFFull) return set_err(BLOWCHOC_EINVAL, "work list too large");
-                prefix.push_back((uint32_t)next);
-            }
-        } else {
-            uint64_t rounds = 0;
-            for (const ManyItem &it : mine) rounds = std::max<uint64_t>(rounds, (it.n + it.B - 1) / it.B);
-            if (rounds > (1u << 24)) return set_err(BLOWCHOC_EINVAL, "too many batches in one call");
-            g.nrounds = (uint32_t)rounds;
-            const uint64_t T = bc::many_tile();
-            for (uint64_t r = 0; r < rounds; ++r) {
+        for (auto &kv : buckets) {
+            std::vector<ManyItem> &mine = kv.second;
+            ManyPlan::Group g{C, (uint32_t)list.size(), (uint32_t)mine.size(), prefix.size(), 0, 0,
+                              kv.first.first, query ? 0u : kv.first.second, query ? (int)kv.first.second : 0};
+            for (const ManyItem &it : mine) g.keys += it.n;
+            if (query) {
                 prefix.push_back(0);
                 for (const ManyItem &it : mine) {
-                    const uint64_t s0 = r * it.B;
-                    const uint64_t cnt = s0 < it.n ? std::min(it.B, it.n - s0) : 0;
-                    const uint64_t next = prefix.back() + (cnt + T - 1) / T;
+                    const uint64_t next = prefix.back() + (it.n + 63) / 64;
                     if (next > 0xFFFFFFFFull) return set_err(BLOWCHOC_EINVAL, "work list too large");
                     prefix.push_back((uint32_t)next);
                 }
+            } else {
+                uint64_t rounds = 0;
+                for (const ManyItem &it : mine) rounds = std::max<uint64_t>(rounds, (it.n + it.B - 1) / it.B);
+                if (rounds > (1u << 24)) return set_err(BLOWCHOC_EINVAL, "too many batches in one call");
+                g.nrounds = (uint32_t)rounds;
+                const uint64_t T = g.tile;
+                for (uint64_t r = 0; r < rounds; ++r) {
+                    prefix.push_back(0);
+                    for (const ManyItem &it : mine) {
+                        const uint64_t s0 = r * it.B;
+                        const uint64_t cnt = s0 < it.n ? std::min(it.B, it.n - s0) : 0;
+                        const uint64_t next = prefix.back() + (cnt + T - 1) / T;
+                        if (next > 0xFFFFFFFFull) return set_err(BLOWCHOC_EINVAL, "work list too large");
+                        prefix.push_back((uint32_t)next);
+                    }
+                }
             }
+            list.insert(list.end(), mine.begin(), mine.end());
+            p.groups.push_back(g);
         }
-        list.insert(list.end(), mine.begin(), mine.end());
-        p.groups.push_back(g);
     }
     int rc = BLOWCHOC_OK;
-    if (!query && sel_total) {
-        rc = grow_device(p.d_sel, p.sel_cap, sel_total, s, p.sel_last, "batch choice scratch");
-        if (rc) return rc;
-        size_t j = 0;
+    if (!query) {
+        // choice bytes of one batch per work-list item, 16-byte aligned slices
+        size_t sel_total = 0;
         for (const ManyPlan::Group &g : p.groups)
-            for (uint32_t i = 0; i < g.nitems; ++i) list[g.item0 + i].sel = p.d_sel + sel_off[j++];
+            for (uint32_t i = 0; i < g.nitems; ++i) {
+                const ManyItem &it = list[g.item0 + i];
+                sel_total += (std::min(it.B, it.n) + 15) & ~uint64_t(15);
+            }
+        if (sel_total) {
+            rc = grow_device(p.d_sel, p.sel_cap, sel_total, s, p.sel_last, "batch choice scratch");
+            if (rc) return rc;
+            size_t off = 0;
+            for (const ManyPlan::Group &g : p.groups)
+                for (uint32_t i = 0; i < g.nitems; ++i) {
+                    ManyItem &it = list[g.item0 + i];
+                    it.sel = p.d_sel + off;
+                    off += (std::min(it.B, it.n) + 15) & ~uint64_t(15);
+                }
+        }
     }
     if (list.empty()) return BLOWCHOC_OK;
     cudaStream_t last_items = sl.last, last_prefix = sl.last;
@@ -567,25 +624,39 @@ int launch(blowchoc_batch *b, const ManyPlan &p, bool query, cudaStream_t s, boo
     for (const ManyPlan::Group &g : p.groups) {
         const ManyItem *items = sl.d_items + g.item0;
         const uint32_t *prefix = sl.d_prefix + g.prefix0;
-        // insert: about kManyKeysPerCta keys of a round per CTA, so that
-        // rounds with little work meet at cheap barriers
+        // insert: about one tile of a round per warp, so that rounds with
+        // little work meet at cheap barriers
         int grid = b->sms * b->ctas_per_sm;
         if (!query && g.nrounds) {
             const uint64_t per_round = (g.keys + g.nrounds - 1) / g.nrounds;
-            grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid,
-                                                                 (per_round + kManyKeysPerCta - 1) / kManyKeysPerCta));
+            const uint64_t per_cta = (uint64_t)g.tile * kManyWarpsPerCta;
+            grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, (per_round + per_cta - 1) / per_cta));
         }
         cudaError_t e;
         if (query)
-            e = bc::launch_query_many(g.C, b->lanes_query, b->query_early != 0, grid, s, items, g.nitems, prefix);
+            e = bc::launch_query_many(g.C, g.lanes, g.early != 0, grid, s, items, g.nitems, prefix);
         else
-            e = bc::launch_insert_many(g.C, b->lanes_choose, grid, s, items, g.nitems, prefix, g.nrounds, bar, err,
+            e = bc::launch_insert_many(g.C, g.lanes, grid, s, items, g.nitems, prefix, g.nrounds, g.tile, bar, err,
                                        b->sms);
         if (e != cudaSuccess) return cuda_err(e, query ? "query_many launch" : "insert_many launch");
         bc_note_launch();
     }
-    for (const blowchoc_work &w : p.side) {
-        const int rc = blowchoc_insert(w.filter, w.d_keys, w.n, s);
+    for (size_t i = 0; i < p.side.size(); ++i) {
+        const blowchoc_work &w = p.side[i];
+        blowchoc_filter *f = w.filter;
+        int rc;
+        if (p.side_mode[i] < 0) {
+            rc = blowchoc_insert(f, w.d_keys, w.n, s);
+        } else {
+            // a routed class: the single-filter insert with the class's set
+            // (host-side launch fields, restored once the launch is queued)
+            const int set_mode = f->set_mode, persistent = f->persistent;
+            f->set_mode = p.side_mode[i];
+            f->persistent = 1;
+            rc = blowchoc_insert(f, w.d_keys, w.n, s);
+            f->set_mode = set_mode;
+            f->persistent = persistent;
+        }
         if (rc) return rc;
     }
     if (mark) MANY_CUDA(cudaEventRecord(sl.done, s), "batch event");
@@ -604,6 +675,20 @@ int run_many(blowchoc_batch *b, ManyPlan &p, const blowchoc_work *items, uint32_
 
 bool lanes_ok(uint32_t l) { return l == 1 || l == 2 || l == 4 || l == 8; }
 
+int check_class_tuning(const blowchoc_class_tuning *t) {
+    if (t->route > BLOWCHOC_ROUTE_SORTED) return set_err(BLOWCHOC_EINVAL, "route must be 0, 1 or 2");
+    if (!lanes_ok(t->lanes_choose) || !lanes_ok(t->lanes_query))
+        return set_err(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
+    if (t->tile < 32 || t->tile > 1024 || (t->tile & (t->tile - 1)))
+        return set_err(BLOWCHOC_EINVAL, "tile must be a power of two in 32..1024");
+    if (t->query_early > 1) return set_err(BLOWCHOC_EINVAL, "query_early must be 0 or 1");
+    return BLOWCHOC_OK;
+}
+
+bool class_args_ok(uint32_t cls, uint32_t k, uint32_t c) {
+    return cls < BLOWCHOC_NUM_CLASSES && k >= 1 && k <= 32 && c >= 1 && c <= 3;
+}
+
 }  // namespace
 
 extern "C" {
@@ -614,6 +699,9 @@ int blowchoc_batch_create(blowchoc_batch **out) {
     blowchoc_batch *b = new blowchoc_batch();
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    int l2 = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
+    b->l2_bytes = (uint64_t)(l2 > 0 ? l2 : 0);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_state, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(b->d_state, 0, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
@@ -658,6 +746,21 @@ int blowchoc_batch_record(blowchoc_batch *b, const blowchoc_work *ins, uint32_t 
     if (rc) return rc;
     if (n_ins) rc = prepare(b, b->rec_ins, ins, n_ins, false, nullptr, true);
     if (!rc && n_qry) rc = prepare(b, b->rec_qry, qry, n_qry, true, nullptr, true);
+    // the single-filter inserts of side items allocate their scratch on first
+    // use, which a capture does not allow: allocate it now, with the launch
+    // fields each will run with
+    for (size_t i = 0; !rc && i < b->rec_ins.side.size(); ++i) {
+        const blowchoc_work &w = b->rec_ins.side[i];
+        blowchoc_filter *f = w.filter;
+        const int set_mode = f->set_mode, persistent = f->persistent;
+        if (b->rec_ins.side_mode[i] >= 0) {
+            f->set_mode = b->rec_ins.side_mode[i];
+            f->persistent = 1;
+        }
+        rc = bc_reserve_insert_scratch(f, w.n);
+        f->set_mode = set_mode;
+        f->persistent = persistent;
+    }
     if (rc) return rc;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -730,6 +833,38 @@ int blowchoc_batch_set_tuning(blowchoc_batch *b, const blowchoc_tuning *t) {
     return BLOWCHOC_OK;
 }
 
+int blowchoc_batch_size_class(blowchoc_batch *b, uint64_t nblocks, uint32_t *cls) {
+    if (!b || !cls) return set_err(BLOWCHOC_EINVAL, "NULL argument");
+    *cls = size_class_of(b, nblocks);
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_get_class_tuning(blowchoc_batch *b, uint32_t cls, uint32_t k, uint32_t c,
+                                    blowchoc_class_tuning *out, uint32_t *is_set) {
+    if (!b || !out) return set_err(BLOWCHOC_EINVAL, "NULL argument");
+    if (!class_args_ok(cls, k, c)) return set_err(BLOWCHOC_EINVAL, "class 0..3, k 1..32, c 1..3");
+    const auto it = b->ctune.find(class_key(cls, k, c));
+    *out = it == b->ctune.end() ? default_class(b) : it->second;
+    if (is_set) *is_set = it == b->ctune.end() ? 0u : 1u;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_set_class_tuning(blowchoc_batch *b, uint32_t cls, uint32_t k, uint32_t c,
+                                    const blowchoc_class_tuning *t) {
+    if (!b || !t) return set_err(BLOWCHOC_EINVAL, "NULL argument");
+    if (!class_args_ok(cls, k, c)) return set_err(BLOWCHOC_EINVAL, "class 0..3, k 1..32, c 1..3");
+    const int rc = check_class_tuning(t);
+    if (rc) return rc;
+    b->ctune[class_key(cls, k, c)] = *t;
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_batch_clear_class_tuning(blowchoc_batch *b) {
+    if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
+    b->ctune.clear();
+    return BLOWCHOC_OK;
+}
+
 int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_t n_ins,
                             const blowchoc_work *qry, uint32_t n_qry, void *stream, blowchoc_tuning *best) {
     if (!b) return set_err(BLOWCHOC_EINVAL, "batch is NULL");
@@ -767,6 +902,38 @@ int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = set_err(BLOWCHOC_ECUDA, "autotune events");
     const int saved[4] = {b->lanes_choose, b->lanes_query, b->query_early, b->ctas_per_sm};
+    const std::map<uint64_t, blowchoc_class_tuning> saved_classes = b->ctune;
+
+    // Time of `wi` inserted then `wq` queried on cleared scratch filters, summed
+    // over two repetitions after a warm-up; with query_only the inserts run
+    // untimed before the timed queries.
+    auto timed = [&](const std::vector<blowchoc_work> &wi, const std::vector<blowchoc_work> &wq,
+                     bool query_only, float *out_ms) -> int {
+        float total = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            for (size_t i = 0; i < scratch.size(); i += 2) {
+                const int r = blowchoc_clear(scratch[i], stream);
+                if (r) return r;
+            }
+            int r = BLOWCHOC_OK;
+            if (query_only && !wi.empty()) r = blowchoc_insert_many(b, wi.data(), (uint32_t)wi.size(), stream);
+            if (r) return r;
+            if (cudaEventRecord(e0, s) != cudaSuccess) return set_err(BLOWCHOC_ECUDA, "autotune event");
+            if (!query_only && !wi.empty()) r = blowchoc_insert_many(b, wi.data(), (uint32_t)wi.size(), stream);
+            if (!r && !wq.empty()) r = blowchoc_query_many(b, wq.data(), (uint32_t)wq.size(), stream);
+            if (r) return r;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return set_err(BLOWCHOC_ECUDA, "autotune sync");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) total += ms;
+        }
+        *out_ms = total;
+        return BLOWCHOC_OK;
+    };
+
+    // 1. the batch object's tuning over the whole call, class tunings aside
+    b->ctune.clear();
     float best_ms = -1.0f;
     int best_cfg[4] = {saved[0], saved[1], saved[2], saved[3]};
     const int lanes_c[] = {1, 2, 4}, lanes_q[] = {1, 2}, ctas[] = {4, 8};
@@ -778,34 +945,92 @@ int blowchoc_batch_autotune(blowchoc_batch *b, const blowchoc_work *ins, uint32_
                 b->lanes_query = lq;
                 b->query_early = 1;
                 b->ctas_per_sm = cp;
-                float total = 0.0f;
-                for (int rep = 0; rep < 2 && !rc; ++rep) {
-                    for (size_t i = 0; i < scratch.size() && !rc; i += 2) rc = blowchoc_clear(scratch[i], stream);
-                    if (rc) break;
-                    cudaEventRecord(e0, s);
-                    if (!sins.empty()) rc = blowchoc_insert_many(b, sins.data(), (uint32_t)sins.size(), stream);
-                    if (!rc && !sqry.empty()) rc = blowchoc_query_many(b, sqry.data(), (uint32_t)sqry.size(), stream);
-                    cudaEventRecord(e1, s);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_err(BLOWCHOC_ECUDA, "autotune sync");
-                    float ms = 0.0f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep) total += ms;  // first repetition warms up
-                }
-                if (!rc && (best_ms < 0.0f || total < best_ms)) {
-                    best_ms = total;
+                float ms = 0.0f;
+                rc = timed(sins, sqry, false, &ms);
+                if (!rc && (best_ms < 0.0f || ms < best_ms)) {
+                    best_ms = ms;
                     best_cfg[0] = lc; best_cfg[1] = lq; best_cfg[2] = 1; best_cfg[3] = cp;
                 }
             }
+    if (!rc) {
+        b->lanes_choose = best_cfg[0];
+        b->lanes_query = best_cfg[1];
+        b->query_early = best_cfg[2];
+        b->ctas_per_sm = best_cfg[3];
+    }
+
+    // 2. per (size class, k, c): one dimension at a time on that class's filters
+    std::map<uint64_t, std::pair<std::vector<blowchoc_work>, std::vector<blowchoc_work>>> by_class;
+    for (const auto &w : sins)
+        by_class[class_key(size_class_of(b, w.filter->dev.M), w.filter->dev.k, w.filter->p.choices)].first.push_back(w);
+    for (const auto &w : sqry)
+        by_class[class_key(size_class_of(b, w.filter->dev.M), w.filter->dev.k, w.filter->p.choices)].second.push_back(w);
+    const std::vector<blowchoc_work> none;
+    for (auto &kv : by_class) {
+        if (rc) break;
+        const uint64_t key = kv.first;
+        const std::vector<blowchoc_work> &wi = kv.second.first, &wq = kv.second.second;
+        blowchoc_class_tuning cur = default_class(b);
+        float cur_ms = -1.0f;
+        // keeps t (and its time) if it beats the best so far
+        auto consider = [&](const blowchoc_class_tuning &t, bool query_only) -> int {
+            b->ctune[key] = t;
+            float ms = 0.0f;
+            const int r = query_only ? timed(wi, wq, true, &ms) : timed(wi, none, false, &ms);
+            if (r) return r;
+            if (cur_ms < 0.0f || ms < cur_ms) {
+                cur_ms = ms;
+                cur = t;
+            }
+            return BLOWCHOC_OK;
+        };
+        if (!wi.empty()) {
+            for (uint32_t lanes : {1u, 2u, 4u, 8u}) {
+                blowchoc_class_tuning t = cur;
+                t.lanes_choose = lanes;
+                if (!rc) rc = consider(t, false);
+            }
+            const blowchoc_class_tuning base = cur;
+            for (uint32_t tile : {64u, 128u, 256u, 512u}) {
+                blowchoc_class_tuning t = base;
+                t.tile = tile;
+                if (!rc) rc = consider(t, false);
+            }
+            const blowchoc_class_tuning listed = cur;
+            for (uint32_t route : {(uint32_t)BLOWCHOC_ROUTE_DIRECT, (uint32_t)BLOWCHOC_ROUTE_SORTED}) {
+                blowchoc_class_tuning t = listed;
+                t.route = route;
+                if (!rc) rc = consider(t, false);
+            }
+        }
+        if (!wq.empty()) {
+            cur_ms = -1.0f;
+            const blowchoc_class_tuning base = cur;
+            for (uint32_t lanes : {1u, 2u, 4u, 8u})
+                for (uint32_t early : {0u, 1u}) {
+                    blowchoc_class_tuning t = base;
+                    t.lanes_query = lanes;
+                    t.query_early = early;
+                    if (!rc) rc = consider(t, true);
+                }
+        }
+        b->ctune[key] = cur;
+    }
+
     for (size_t i = 0; i < scratch.size(); i += 2) blowchoc_destroy(scratch[i]);
     cudaFree(d_bm);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    b->lanes_choose = rc ? saved[0] : best_cfg[0];
-    b->lanes_query = rc ? saved[1] : best_cfg[1];
-    b->query_early = rc ? saved[2] : best_cfg[2];
-    b->ctas_per_sm = rc ? saved[3] : best_cfg[3];
-    if (!rc && best) blowchoc_batch_get_tuning(b, best);
-    return rc;
+    if (rc) {
+        b->lanes_choose = saved[0];
+        b->lanes_query = saved[1];
+        b->query_early = saved[2];
+        b->ctas_per_sm = saved[3];
+        b->ctune = saved_classes;
+        return rc;
+    }
+    if (best) blowchoc_batch_get_tuning(b, best);
+    return BLOWCHOC_OK;
 }
 
 }  // extern "C"

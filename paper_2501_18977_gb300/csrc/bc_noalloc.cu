@@ -14,7 +14,7 @@
 #include "bc_launch.h"
 
 // Choice bytes of one batch: at most this many keys per batch on the path
-// that needs them (batches larger than the single-CTA kernel's limit).
+// that needs them (batches that run over the whole grid).
 static constexpr uint64_t kNoAllocMaxBatch = 1ull << 22;  // 4,194,304 keys, 4 MiB
 
 // Every device that loads the library holds its own copy until the process
@@ -29,7 +29,9 @@ std::mutex g_setup_mu;
 uint8_t *g_choices_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_choices on the current device `dev`, looked up
-// once per device (with that device current). Returns nullptr on failure.
+// once per device (with that device current) and kept for the life of the
+// process: a device reset, which unloads the module, leaves it stale, so the
+// library must not be used after one. Returns nullptr on failure.
 uint8_t *choices_on(int dev, cudaError_t *err) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     if (g_choices_addr[dev] == nullptr) {
@@ -65,7 +67,9 @@ extern "C" int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_key
         bc_note_launch();
         return BLOWCHOC_OK;
     }
-    if (B <= bc::kSmallBatchMax) {
+    // the single-CTA kernel takes the batches that blowchoc_insert also runs in
+    // one CTA; larger ones run over the whole grid (choose/set pairs below)
+    if (B <= bc::kSingleCtaBatch || (!f->persistent && B <= bc::kSmallBatchMax)) {
         bc::Launch L{1, f->lanes_choose, s};
         e = bc::launch_small_batch(C, L, f->dev, d_keys, n, B, f->d_rank, f->d_counters);
         if (e != cudaSuccess) return noalloc_cuda_error(e);

@@ -11,8 +11,11 @@ constexpr int kThreads = 256;
 
 // Each group of LANES lanes reads `per_group` pseudo-random whole blocks
 // (block index from a multiplicative hash of a counter, so addresses are
-// spread uniformly) and folds them into one word per warp.
-template <int LANES>
+// spread uniformly) and folds them into one word per warp. A trip issues U
+// independent block loads before folding any of them, so U loads per lane
+// group are in flight at once (memory-level parallelism beyond one load per
+// thread).
+template <int LANES, int U>
 __global__ void __launch_bounds__(kThreads) gather_probe_kernel(const uint64_t *__restrict__ words,
                                                                 uint64_t mask_or_m, int pow2,
                                                                 uint64_t nreads, uint64_t seed,
@@ -22,22 +25,43 @@ __global__ void __launch_bounds__(kThreads) gather_probe_kernel(const uint64_t *
     const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / LANES;
     const uint64_t ngroups = ((uint64_t)gridDim.x * blockDim.x) / LANES;
     uint64_t acc = 0;
-    const uint64_t trips = (nreads + ngroups - 1) / ngroups;
+    const uint64_t per_trip = ngroups * U;
+    const uint64_t trips = (nreads + per_trip - 1) / per_trip;
     for (uint64_t t = 0; t < trips; ++t) {
-        const uint64_t r = t * ngroups + gid;
-        const bool valid = r < nreads;
-        const uint64_t h = (r + seed) * 0x9E3779B97F4A7C15ull;
-        const uint64_t b = pow2 ? ((h >> 20) & mask_or_m) : ((h >> 20) % mask_or_m);
-        uint64_t v[W];
-        if (valid) {
-            bc::load_words<W, bc::kLoadNC>(words + b * bc::kBlockWords + (uint64_t)q * W, v);
+        uint64_t v[U][W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) acc ^= v[j];
+        for (int u = 0; u < U; ++u) {
+            const uint64_t r = t * per_trip + (uint64_t)u * ngroups + gid;
+            const uint64_t h = (r + seed) * 0x9E3779B97F4A7C15ull;
+            const uint64_t b = pow2 ? ((h >> 20) & mask_or_m) : ((h >> 20) % mask_or_m);
+            if (r < nreads) {
+                bc::load_words<W, bc::kLoadNC>(words + b * bc::kBlockWords + (uint64_t)q * W, v[u]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; ++j) v[u][j] = 0;
+            }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < W; ++j) acc ^= v[u][j];
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, s);
     if (lane == 0) sink[((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = acc;
+}
+
+template <int LANES>
+cudaError_t launch_probe(int grid, cudaStream_t s, uint32_t inflight, const uint64_t *w, uint64_t mm,
+                         int pow2, uint64_t nreads, uint64_t seed, uint64_t *sink) {
+    switch (inflight) {
+        case 1: gather_probe_kernel<LANES, 1><<<grid, kThreads, 0, s>>>(w, mm, pow2, nreads, seed, sink); break;
+        case 2: gather_probe_kernel<LANES, 2><<<grid, kThreads, 0, s>>>(w, mm, pow2, nreads, seed, sink); break;
+        case 4: gather_probe_kernel<LANES, 4><<<grid, kThreads, 0, s>>>(w, mm, pow2, nreads, seed, sink); break;
+        case 8: gather_probe_kernel<LANES, 8><<<grid, kThreads, 0, s>>>(w, mm, pow2, nreads, seed, sink); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // Barrier self-test: every CTA but the last arrives at one grid barrier; the
@@ -80,10 +104,12 @@ extern "C" int blowchoc_barrier_selftest(uint32_t ctas, double seconds, void *st
 }
 
 extern "C" int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, uint64_t nreads,
-                                     uint64_t seed, uint32_t lanes, uint32_t ctas_per_sm,
+                                     uint64_t seed, uint32_t lanes, uint32_t ctas_per_sm, uint32_t inflight,
                                      uint64_t *d_sink, void *stream) {
     if (!d_words || !d_sink || nblocks == 0) return bc_set_error(BLOWCHOC_EINVAL, "bad probe arguments");
     if (ctas_per_sm < 1 || ctas_per_sm > 16) return bc_set_error(BLOWCHOC_EINVAL, "ctas_per_sm must be in 1..16");
+    if (inflight != 1 && inflight != 2 && inflight != 4 && inflight != 8)
+        return bc_set_error(BLOWCHOC_EINVAL, "inflight must be 1, 2, 4 or 8");
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -92,14 +118,14 @@ extern "C" int blowchoc_gather_probe(const uint64_t *d_words, uint64_t nblocks, 
     const int pow2 = (nblocks & (nblocks - 1)) == 0;
     const uint64_t mm = pow2 ? nblocks - 1 : nblocks;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
     switch (lanes) {
-        case 1: gather_probe_kernel<1><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
-        case 2: gather_probe_kernel<2><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
-        case 4: gather_probe_kernel<4><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
-        case 8: gather_probe_kernel<8><<<grid, kThreads, 0, s>>>(d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 1: e = launch_probe<1>(grid, s, inflight, d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 2: e = launch_probe<2>(grid, s, inflight, d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 4: e = launch_probe<4>(grid, s, inflight, d_words, mm, pow2, nreads, seed, d_sink); break;
+        case 8: e = launch_probe<8>(grid, s, inflight, d_words, mm, pow2, nreads, seed, d_sink); break;
         default: return bc_set_error(BLOWCHOC_EINVAL, "lanes must be 1, 2, 4 or 8");
     }
-    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bc_set_error(BLOWCHOC_ECUDA, cudaGetErrorString(e));
     bc_note_launch();
     return BLOWCHOC_OK;

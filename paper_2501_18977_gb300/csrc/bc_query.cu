@@ -16,11 +16,11 @@ __global__ void __launch_bounds__(kThreads) query_kernel(DevFilter f, const uint
                                                          unsigned long long *__restrict__ count) {
     constexpr int G = 32 / LANES;
     __shared__ uint64_t s_amul[32];
-    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * G * region_u32<LANES>()];
+    __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * mask_u32_per_warp<LANES>()];
     stage_bit_mults(f, s_amul);
     __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
-    uint32_t *region = s_mask + ((threadIdx.x >> 5) * G + g) * region_u32<LANES>();
+    uint32_t *region = warp_mask_area<LANES>(s_mask, threadIdx.x >> 5);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nwords = (n + 63) / 64;

@@ -9,7 +9,7 @@ algorithmic bytes of member queries).
 
 Usage: python tests/golden/make_golden.py dna        (about 5 minutes on one core)
        python tests/golden/make_golden.py sweep I    (one filter setting I = 0..6 of the
-                                                      overload sweep, about 30 minutes)
+                                                      overload sweep, about 60 minutes)
        python tests/golden/make_golden.py many       (the 256-filter workload, about 6 minutes)
 """
 import hashlib
@@ -73,12 +73,12 @@ def dna():
 
 # Overload sweep: M = 2^23 blocks (512 MiB), k = 12, B = 2^20; keys are the
 # splitmix64 stream of seed 3001, grown through n = floor(2^32 / b) for
-# b = 20, 18, 16, 14, 12 bits per key, one insert call per step; 10^8 negatives
-# from seed 3002 queried at every point.
+# b = 20, 18, ..., 6 bits per key (Sec. 4.1: the FPR under overload), one insert
+# call per step; 10^8 negatives from seed 3002 queried at every point.
 SWEEP_SETTINGS = [(1, COST_EXP, GOLDEN_RATIO), (2, COST_MIX, 50.0), (2, COST_LA, 3.5),
                   (2, COST_EXP, GOLDEN_RATIO), (3, COST_MIX, 50.0), (3, COST_LA, 3.5),
                   (3, COST_EXP, GOLDEN_RATIO)]
-SWEEP_BITS = [20, 18, 16, 14, 12]
+SWEEP_BITS = [20, 18, 16, 14, 12, 10, 8, 6]
 SWEEP_M, SWEEP_K, SWEEP_B, SWEEP_NEG = 1 << 23, 12, 1 << 20, 100_000_000
 COST_NAMES = {COST_MIX: "MIX", COST_LA: "LA", COST_EXP: "EXP"}
 

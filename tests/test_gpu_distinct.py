@@ -29,6 +29,7 @@ def _oracle(M, k, c, kind, par, seed, B, keys, queries):
     (512, 16, 2, COST_MIX, 50.0, 1, 20000, {}),                           # exact sequential rounds
     (300, 20, 3, COST_EXP, PHI, 1, 5000, dict(seq_window=0)),              # one warp
     (4096, 12, 2, COST_MIX, 50.0, 65536, 200000, dict(set_mode=1)),        # sort by block
+    (4096, 12, 3, COST_LA, 3.5, 65536, 200000, dict(set_mode=2)),          # bulk set
     (2048, 32, 2, COST_EXP, PHI, 30000, 60000, dict(persistent=0, lanes_choose=8, lanes_set=2,
                                                     lanes_query=8, query_early=0)),
     (6150, 9, 1, COST_EXP, PHI, 20000, 60000, dict(lanes_query=4)),

@@ -155,6 +155,107 @@ def test_autotune_leaves_filters_untouched_and_results_unchanged():
             f.close()
 
 
+def _classes_present(bc, batch, cases):
+    return sorted({(batch.size_class(M), k, c) for (M, k, c, kind, par, B, n) in cases})
+
+
+# class tunings forced on every (size class, k, c) of the mix
+CLASS_CONFIGS = [
+    dict(route=0, lanes_choose=8, tile=32, lanes_query=4, query_early=0),
+    dict(route=0, lanes_choose=1, tile=1024, lanes_query=8, query_early=1),
+    dict(route=0, lanes_choose=2, tile=256, lanes_query=1, query_early=0),
+    dict(route=1, lanes_choose=4, tile=64, lanes_query=2, query_early=1),
+    dict(route=2, lanes_choose=4, tile=128, lanes_query=1, query_early=1),
+]
+
+
+@pytest.mark.parametrize("cfg", CLASS_CONFIGS, ids=["wl-l8-t32", "wl-l1-t1024", "wl-l2-t256", "direct", "sorted"])
+def test_class_tunings_keep_results(cfg):
+    """Whatever launch configuration a size class gets (work-list lanes and
+    tile, direct or sort-by-block single-filter route, query lanes and early
+    exit), every filter's words, bitmap and counters equal the oracle's."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    seed0 = 41
+    cases = [c for c in MIX if c[5] != 1]
+    filters, keys, queries = _setup(bc, cases, seed0)
+    dk = [to_dev(k) for k in keys]
+    dq = [to_dev(q) for q in queries]
+    bms = [torch.zeros(max(1, (len(q) + 63) // 64), dtype=torch.int64, device="cuda") for q in queries]
+    batch = bc.Batch()
+    try:
+        for cls, k, c in _classes_present(bc, batch, cases):
+            batch.set_class_tuning(cls, k, c, **cfg)
+            got, is_set = batch.class_tuning(cls, k, c)
+            assert is_set and got == cfg
+        batch.insert_many([(f, d, len(kk), None) for f, d, kk in zip(filters, dk, keys)])
+        batch.query_many([(f, d, len(q), b) for f, d, q, b in zip(filters, dq, queries, bms)])
+        torch.cuda.synchronize()
+        _check_against_oracle(cases, filters, keys, queries, bms, seed0)
+        # the filters' own launch fields are restored after a routed call
+        for f in filters:
+            t = f.tuning()
+            assert (t.set_mode, t.persistent) == (0, 1)
+    finally:
+        batch.close()
+        for f in filters:
+            f.close()
+
+
+def test_class_tuning_api_checks_and_classes():
+    import paper_2501_18977_gb300 as bc
+    batch = bc.Batch()
+    try:
+        # classes by filter bytes against L2: tiny, a quarter of L2, twice L2, 8 GiB
+        assert batch.size_class(64) == bc.CLASS_CACHE
+        assert batch.size_class(1 << 27 >> 6) in (bc.CLASS_L2, bc.CLASS_SPILL)
+        assert batch.size_class((1 << 33) >> 6) == bc.CLASS_HBM
+        t, is_set = batch.class_tuning(1, 11, 2)
+        assert not is_set and t["route"] == 0 and t["tile"] == 128
+        for bad in (dict(route=3), dict(lanes_choose=3), dict(tile=48), dict(tile=2048), dict(query_early=2)):
+            with pytest.raises(bc.BlowChocError) as ei:
+                batch.set_class_tuning(1, 11, 2, **bad)
+            assert ei.value.code == bc.BLOWCHOC_EINVAL
+        with pytest.raises(bc.BlowChocError):
+            batch.class_tuning(4, 11, 2)
+        batch.set_class_tuning(1, 11, 2, tile=512)
+        assert batch.class_tuning(1, 11, 2)[1]
+        batch.clear_class_tuning()
+        assert not batch.class_tuning(1, 11, 2)[1]
+    finally:
+        batch.close()
+
+
+def test_autotuned_classes_match_the_oracle():
+    """After the per-class autotune, every (size class, k, c) of the mix has
+    a cached tuning, and the tuned call is bit-exact against the oracle."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    seed0 = 51
+    cases = [c for c in MIX if c[5] != 1]
+    filters, keys, queries = _setup(bc, cases, seed0)
+    dk = [to_dev(k) for k in keys]
+    dq = [to_dev(q) for q in queries]
+    bms = [torch.zeros(max(1, (len(q) + 63) // 64), dtype=torch.int64, device="cuda") for q in queries]
+    batch = bc.Batch()
+    try:
+        ins = [(f, d, len(kk), None) for f, d, kk in zip(filters, dk, keys)]
+        qry = [(f, d, len(q), b) for f, d, q, b in zip(filters, dq, queries, bms)]
+        batch.autotune(ins, qry)
+        for cls, k, c in _classes_present(bc, batch, [cs for cs in cases if cs[6] > 0]):
+            assert batch.class_tuning(cls, k, c)[1], (cls, k, c)
+        for f in filters:
+            assert not f.words_host().any()
+        batch.insert_many(ins)
+        batch.query_many(qry)
+        torch.cuda.synchronize()
+        _check_against_oracle(cases, filters, keys, queries, bms, seed0)
+    finally:
+        batch.close()
+        for f in filters:
+            f.close()
+
+
 def test_many_rejects_a_repeated_filter():
     import paper_2501_18977_gb300 as bc
     f = bc.Filter(64, 8, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=2048)

@@ -154,6 +154,14 @@ def test_config_small_uniform_full():
          keys_per_cta=64, set_mode=1, cluster_max=0),
     dict(lanes_choose=8, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=16, persistent=1,
          set_mode=1, cluster_max=0),
+    dict(lanes_choose=1, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=8, persistent=1,
+         set_mode=2, cluster_max=0),
+    dict(lanes_choose=2, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=8, persistent=1,
+         set_mode=2, cluster_max=0),
+    dict(lanes_choose=4, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=3, persistent=1,
+         keys_per_cta=64, set_mode=2, cluster_max=0),
+    dict(lanes_choose=8, lanes_set=2, lanes_query=1, query_early=1, ctas_per_sm=16, persistent=1,
+         set_mode=2, cluster_max=0),
     dict(lanes_choose=2, lanes_set=4, lanes_query=1, query_early=2, ctas_per_sm=8, persistent=1, cluster_max=0),
     dict(lanes_choose=2, lanes_set=4, lanes_query=2, query_early=2, ctas_per_sm=8, persistent=1, cluster_max=0),
     dict(cluster_max=16, lanes_cluster=4),
@@ -191,7 +199,7 @@ def test_set_tuning_rejects_bad_values():
         before = (f.tuning().lanes_query, f.tuning().ctas_per_sm)
         for bad in [dict(lanes_query=3), dict(lanes_choose=16), dict(query_early=3),
                     dict(ctas_per_sm=0), dict(ctas_per_sm=17), dict(persistent=2),
-                    dict(keys_per_cta=8), dict(set_mode=2), dict(seq_window=16),
+                    dict(keys_per_cta=8), dict(set_mode=3), dict(seq_window=16),
                     dict(seq_window=9000), dict(cluster_max=17), dict(lanes_cluster=2),
                     dict(lanes_cluster=16), dict(cluster_keys=8), dict(cluster_keys=(1 << 20) + 1)]:
             with pytest.raises(bc.BlowChocError):

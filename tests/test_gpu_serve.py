@@ -1,11 +1,17 @@
 """The serving loop: every request's result equals the result of running the
 requests of its filter alone, one after another, in arrival order (tolerance
 0), while waves of requests of different filters share launches and overlap
-on several streams; filters beyond the HBM budget wait for admission."""
+on several streams; filters beyond the HBM budget wait for admission.
+
+Every served query bitmap and every filter's final words are also compared
+with the oracle replaying each filter's requests in arrival order (Sec. 3.1
+and 3.2: an insert request is its own sequence of B-key batches; a query sees
+exactly the inserts that arrived before it)."""
 import numpy as np
 import pytest
 
 import workloads
+from oracle import OracleFilter, COST_MIX
 from tests.gpu_helpers import to_dev
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +44,29 @@ def _alone(bc, filters, reqs, keys):
     for f in fs:
         f.close()
     return out, words
+
+
+def _oracle(filters, reqs, keys):
+    """Each filter's requests replayed by the oracle in arrival order."""
+    fs = [OracleFilter(f["M"], 14, 2, COST_MIX, 50.0, seed=f["key_seed"], batch=f["B"])
+          for f in filters]
+    out = {}
+    for r in sorted(reqs, key=lambda r: (r["arrival"], r["index"])):
+        f = fs[r["filter"]]
+        if r["kind"] == 0:
+            f.insert(keys[r["index"]])
+        else:
+            out[r["index"]] = np.asarray(f.query(keys[r["index"]]), dtype=np.uint64)
+    return out, [np.asarray(f.words, dtype=np.uint64) for f in fs]
+
+
+def _check_oracle(filters, reqs, keys, served, served_words):
+    want, want_words = _oracle(filters, reqs, keys)
+    assert set(want) == set(served)
+    for j, bm in want.items():
+        assert np.array_equal(served[j], bm), j
+    for f, a, b in zip(filters, want_words, served_words):
+        assert np.array_equal(a, b), f["index"]
 
 
 def _serve(bc, filters, reqs, keys, budget=1 << 30, streams=3, wave=8, time_scale=1e-4,
@@ -77,6 +106,7 @@ def test_served_results_equal_alone_results():
         assert np.array_equal(served[j], bm), j
     for a, b in zip(alone_words, served_words):
         assert np.array_equal(a, b)
+    _check_oracle(filters, reqs, keys, served, served_words)
 
 
 @pytest.mark.parametrize("tune", [dict(cluster_max=0, lanes_choose=4, lanes_query=1),
@@ -95,6 +125,7 @@ def test_server_launch_configuration_keeps_results(tune):
         assert np.array_equal(served[j], bm), j
     for a, b in zip(alone_words, served_words):
         assert np.array_equal(a, b)
+    _check_oracle(filters, reqs, keys, served, served_words)
     srv = bc.Server(1 << 24, staging_bytes=1 << 20, streams=1, max_wave_requests=1)
     try:
         with pytest.raises(bc.BlowChocError):
@@ -112,10 +143,11 @@ def test_concurrent_waves_share_launches():
     filters, reqs = _small_trace(n_filters=16, n_requests=200, seed=8)
     keys = {r["index"]: workloads.serving_keys(filters, r, seed=8) for r in reqs}
     alone, _ = _alone(bc, filters, reqs, keys)
-    served, _, st, _ = _serve(bc, filters, reqs, keys, time_scale=0.0, wave=16, streams=4)
+    served, served_words, st, _ = _serve(bc, filters, reqs, keys, time_scale=0.0, wave=16, streams=4)
     assert st.mean_wave_requests > 2.0
     for j, bm in alone.items():
         assert np.array_equal(served[j], bm), j
+    _check_oracle(filters, reqs, keys, served, served_words)
 
 
 def test_admission_waits_for_budget():
@@ -131,6 +163,9 @@ def test_admission_waits_for_budget():
     assert st.completed == len(reqs)
     assert st.max_filter_bytes_used <= int(2.5 * one)
     for j, bm in alone.items():
+        assert np.array_equal(served[j], bm), j
+    want, _ = _oracle(filters, reqs, keys)
+    for j, bm in want.items():
         assert np.array_equal(served[j], bm), j
 
 

@@ -2,7 +2,8 @@
 
 For every filter setting whose oracle results exist in tests/golden
 (written by make_golden.py sweep I), the GPU filter is grown through the same
-load points (one insert call per point) and its words, counters and false
+load points, 20 down to 6 bits per key (Sec. 4.1: the FPR under overload; one
+insert call per point) and its words, counters and false
 positives among 10^8 negatives must match the oracle's exactly.
 """
 import hashlib
@@ -36,7 +37,8 @@ def _rows(name):
 def sweep_inputs():
     import torch
     import workloads
-    nmax = (1 << 32) // 12
+    nmax = max([r["n"] for c, cost in SETTINGS
+                for r in (_rows("overload_sweep_c%d_%s.txt" % (c, cost)) or [])] + [1])
     keys = torch.empty(nmax, dtype=torch.int64, device="cuda")
     chunk = 1 << 25
     for s0 in range(0, nmax, chunk):

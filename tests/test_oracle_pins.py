@@ -630,3 +630,71 @@ def test_distinct_one_choice_fpr_given_state():
     g.insert(keys)
     W2 = int(bits_of_bitmap(g.query(neg), len(neg)).sum())
     assert W < W2
+
+
+# ---------------------------------------------------------------- sub-arrays (Section 3.4)
+
+def test_sharded_one_subarray_is_the_plain_filter():
+    from oracle.sharded import ShardedOracle
+    keys = workloads.uniform_keys(61, 20000)
+    for c, kind, par, B in [(2, COST_MIX, 50.0, 1), (3, COST_LA, 3.5, 512)]:
+        s = ShardedOracle(333, 1, 11, c, kind, par, seed=9, batch=B)
+        o = _filter(333, 11, c, kind, par, seed=9, B=B)
+        s.insert(keys)
+        o.insert(keys)
+        assert np.array_equal(s.words, o.words)
+        assert np.array_equal(s.query(keys[:777]), o.query(keys[:777]))
+
+
+@pytest.mark.parametrize("M,T", [(64, 4), (100, 3), (1000, 6), (7, 8)])
+def test_sharded_one_choice_is_a_textbook_blocked_bloom(M, T):
+    """c = 1 over T sub-arrays: key x sets bits H_512(a'_i, x) of block
+    h_0(x) * ceil(M/T) + H_{M/T}(a_1, x), written here with Python integers;
+    a_0 is the seed's first odd generator output coprime to T and a_1, a'_i
+    continue the stream (each odd and coprime to its range)."""
+    from oracle.sharded import ShardedOracle
+    k, seed = 5, 1234
+    Ms = -(-M // T)
+    outs = [int(v) | 1 for v in workloads.splitmix64(seed, 64)]
+    it = iter(outs)
+    a0 = next(a for a in it if math.gcd(a, T) == 1)
+    a1 = next(a for a in it if math.gcd(a, Ms) == 1)
+    abits = [next(it) for _ in range(k)]      # odd is coprime to 512
+    keys = workloads.uniform_keys(71, 3000)
+    want = [0] * (T * Ms)
+    for x in keys:
+        x = int(x)
+        blk = oracle.hash_lin(a0, x, T) * Ms + oracle.hash_lin(a1, x, Ms)
+        for a in abits:
+            want[blk] |= 1 << (((a * x) & ((1 << 64) - 1)) >> 55)
+    s = ShardedOracle(M, T, k, 1, COST_EXP, GOLDEN_RATIO, seed=seed, batch=64)
+    s.insert(keys)
+    w = s.words
+    got = [sum(int(w[8 * b + j]) << (64 * j) for j in range(8)) for b in range(T * Ms)]
+    assert got == want
+
+
+@pytest.mark.parametrize("T", [2, 3, 4, 6])
+def test_sharded_h0_is_uniform_and_leaves_other_subarrays_alone(T):
+    from oracle.sharded import ShardedOracle
+    s = ShardedOracle(120, T, 8, 2, COST_EXP, GOLDEN_RATIO, seed=5, batch=32)
+    keys = workloads.uniform_keys(81, 60000)
+    sh = s.shard_of(keys)
+    cnt = np.bincount(sh, minlength=T)
+    exp = len(keys) / T
+    chi2 = float(np.sum((cnt - exp) ** 2 / exp))
+    assert chi2 < (T - 1) + 6 * math.sqrt(2 * (T - 1)) + 1, (T, cnt)
+    s.insert(keys[sh == 0][:2000])
+    w = s.words.reshape(T, -1)
+    assert w[0].any() and not w[1:].any()
+
+
+@pytest.mark.parametrize("T,c,kind,par,B", [(2, 2, COST_MIX, 50.0, 1), (3, 3, COST_LA, 3.5, 97),
+                                            (5, 2, COST_EXP, GOLDEN_RATIO, 4096)])
+def test_sharded_no_false_negatives(T, c, kind, par, B):
+    from oracle.sharded import ShardedOracle
+    s = ShardedOracle(200, T, 9, c, kind, par, seed=3, batch=B)
+    keys = workloads.uniform_keys(91, 8000)
+    s.insert(keys)
+    assert bits_of_bitmap(s.query(keys), len(keys)).all()
+    assert s.inserted + s.skipped == len(keys)
