@@ -636,7 +636,8 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       (offered while ceil(M / 256) <= 65536; larger filters use 0); 2 =
  *       bulk: stage each key's 64-byte mask in shared memory and OR it into
  *       its block with one asynchronous bulk reduction of the copy engine.
- *       Default 2 for filters larger than 1.5 times the L2 size, else 0.
+ *       Default 2 for filters larger than the L2 size with c <= 2 and for
+ *       filters larger than 1.5 times the L2 size with c = 3, else 0.
  *   seq_window: B = 1 (one key at a time) runs in parallel while staying
  *       exactly sequential: windows of seq_window keys (32..8192) go through
  *       rounds in which every pending key reserves its candidate blocks (the

@@ -236,9 +236,12 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
     const uint64_t bytes = params->nblocks * 64ull;
     f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4 : bytes <= 3ull * (uint64_t)l2 / 2 ? 2 : 4;
     f->lanes_query = bytes <= (uint64_t)l2 ? 1 : 2;
-    // the bulk set paid only beyond the L2 size (512 MiB: 29.5 ms against
-    // 30.6 with 64-bit reds; 128 MiB: 4.24 against 3.77)
-    f->set_mode = bytes > 3ull * (uint64_t)l2 / 2 ? 2 : 0;
+    // the bulk set paid at the L2 size and beyond, except with three choices
+    // at about the L2 size (one GB300, c = 2, k = 12: 128 MiB 3.26 against
+    // 4.18 ms at 32 keys per block and batch, 3.91 against 4.23 at 1/2;
+    // 512 MiB 21.0-21.8 against 23.2-23.4; 16 MiB and below 3-18% slower;
+    // the 128 MiB DNA shape, c = 3, k = 16: 2.83 against 2.59)
+    f->set_mode = (bytes > (uint64_t)l2 && (params->choices <= 2 || bytes > 3ull * (uint64_t)l2 / 2)) ? 2 : 0;
     bc::DevFilter &d = f->dev;
     std::memset(&d, 0, sizeof d);
     d.M = params->nblocks;

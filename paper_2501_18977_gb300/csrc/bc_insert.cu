@@ -189,10 +189,9 @@ constexpr int persistent_min_ctas() { return LANES == 1 ? 2 : 1024 / persistent_
 // slot and ORs it into the chosen block with one bulk reduction (the copy
 // engine's cp.reduce.async.bulk) instead of a 64-bit red per word. A lane
 // group cycles through kBulkRing slots, so a slot is rewritten only after
-// the reduction issued kBulkRing keys earlier has read it. Measured on one
-// GB300 against the red path: 512 MiB filter (c = 2, four lanes) 29.5 against
-// 30.6 ms; the 128 MiB DNA filter 4.24 against 3.77 ms and a 2 MiB filter
-// 0.174 against 0.164 ms, so it is the default only beyond 1.5 times L2.
+// the reduction issued kBulkRing keys earlier has read it. It pays from about
+// the L2 size on (the default rule and its measurements are in
+// blowchoc_create); smaller filters keep the 64-bit reds.
 constexpr int kBulkRing = 4;
 template <int LANES>
 constexpr size_t bulk_ring_bytes() {
@@ -304,18 +303,17 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
     flush_counts(ins, skp, counters);
 }
 
-#ifndef BC_SORTED_BULK
-#define BC_SORTED_BULK 0
-#endif
-
 // ---------------------------------------------------------------------------
 // Sort-by-block set variant. After the choose phase of a batch, the chosen
 // blocks are bucketed by range of kRangeBlocks blocks (count, scan, scatter);
-// then each CTA takes whole ranges, stages the range's words in shared memory,
-// ORs the masks of the range's keys in with shared atomics and writes the
-// range back: no global atomics on the filter, one read and one write per
-// touched range. It pays when a batch hits blocks many times (small M or
-// large B).
+// then each CTA takes whole ranges, stages the range's words in shared memory
+// with one bulk copy (cp.async.bulk, completion counted on an mbarrier), ORs
+// the masks of the range's keys in with shared atomics and writes the range
+// back with one bulk copy: no global atomics on the filter, one read and one
+// write per touched range. Measured on one GB300 over filters of 1 to 512 MiB
+// and 1/16 to 32 keys per block and batch, it never beat the direct or bulk
+// set (1.4 to 10 times slower); the bulk copies made it up to 28% faster than
+// staging with plain loads and stores.
 
 template <int C, int LANES>
 __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
@@ -331,7 +329,6 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(kThreads / 32) * mask_u32_per_warp<LANES>()];
     __shared__ uint32_t s_part[kThreads];
-#if BC_SORTED_BULK
     __shared__ uint64_t s_mbar;
     uint32_t phase = 0;
     if (threadIdx.x == 0) {
@@ -339,7 +336,6 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
         fence_proxy_async_shared();
     }
     __syncthreads();
-#endif
     stage_bit_mults(f, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
@@ -432,7 +428,6 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
             const uint64_t first = (uint64_t)r * kRangeBlocks;
             const uint64_t nb = f.M - first < kRangeBlocks ? f.M - first : kRangeBlocks;
             const uint64_t *src = f.words + first * kBlockWords;
-#if BC_SORTED_BULK
             // one bulk copy of the range (after the previous range's write-back
             // has read the staging area), counted on the CTA's mbarrier
             if (threadIdx.x == 0) {
@@ -446,9 +441,6 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
                 return;
             }
             phase ^= 1u;
-#else
-            for (uint32_t w = threadIdx.x; w < nb * kBlockWords; w += blockDim.x) s_range[w] = __ldcg(src + w);
-#endif
             __syncthreads();
             for (uint32_t base = c0 + wib * G; base < c1; base += wpc * G) {
                 const uint32_t idx = base + g;
@@ -470,22 +462,15 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
             }
             __syncthreads();
             uint64_t *dst = f.words + first * kBlockWords;
-#if BC_SORTED_BULK
             fence_proxy_async_shared();  // every thread's ORs, visible to the bulk copy
             __syncthreads();
             if (threadIdx.x == 0) {
                 bulk_store(dst, s_range, (uint32_t)(nb * 64));
                 bulk_commit();
             }
-#else
-            for (uint32_t w = threadIdx.x; w < nb * kBlockWords; w += blockDim.x) dst[w] = s_range[w];
-            __syncthreads();
-#endif
         }
-#if BC_SORTED_BULK
         if (threadIdx.x == 0) bulk_wait_all();  // the batch's ranges are written
         fence_proxy_async_global();
-#endif
         if (s0 + B < n) {
             target += gridDim.x;
             if (!grid_barrier(bar, target, err)) return;
