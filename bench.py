@@ -125,10 +125,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    count = 0
+
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join("/tmp", "bc_clocks_%d_%d.csv" % (os.getpid(), index))
+        ClockSampler.count += 1  # unique file per sampler: several may run at once
+        self.path = os.path.join("/tmp", "bc_clocks_%d_%d_%d.csv" % (os.getpid(), index, ClockSampler.count))
 
     def start(self):
         try:
@@ -169,6 +172,21 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# Clock record of a --workload run: every JSON line a workload prints carries
+# the SM clocks and throttle reasons sampled since the previous line.
+_WORKLOAD_CLOCKS = None
+
+
+def emit(record):
+    """Print one workload JSON line with the clocks sampled since the last one."""
+    global _WORKLOAD_CLOCKS
+    if _WORKLOAD_CLOCKS is not None and "clocks" not in record:
+        record = dict(record, clocks=_WORKLOAD_CLOCKS.stop())
+        _WORKLOAD_CLOCKS = ClockSampler(_WORKLOAD_CLOCKS.index)
+        _WORKLOAD_CLOCKS.start()
+    print(json.dumps(record), flush=True)
 
 
 def peaks():
@@ -266,8 +284,8 @@ def run_gather(args):
         g, (lanes, cps, inf) = gather_ceiling(bc, torch, nb, nreads=100_000_000)
         out.append({"footprint_mib": mib, "gbs": round(g, 1), "lanes": lanes, "ctas_per_sm": cps,
                     "inflight": inf})
-    print(json.dumps({"workload": "gather_ceiling", "unit": "GB/s of whole 64-byte blocks",
-                      "reads": 100_000_000, "results": out}))
+    emit({"workload": "gather_ceiling", "unit": "GB/s of whole 64-byte blocks",
+                      "reads": 100_000_000, "results": out})
 
 
 def run_many(args):
@@ -379,7 +397,7 @@ def run_many(args):
     batch.close()
     for f in filters:
         f.close()
-    print(json.dumps(out))
+    emit(out)
 
 
 def run_serve(args):
@@ -420,33 +438,44 @@ def run_serve(args):
         span = st.last_done_s - st.first_arrival_s
         return bms, st, span, launches
 
-    # plain: one request at a time, in arrival order, one stream
-    fs = [bc.Filter(f["M"], 14, 2, bc.COST_MIX, 50.0, hash_seed=f["key_seed"], batch=f["B"])
-          for f in filters]
-    dev = torch.empty(max(sizes), dtype=torch.int64, device="cuda")
-    dbm = torch.empty((max(sizes) + 63) // 64, dtype=torch.int64, device="cuda")
-    plain_bms = {}
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in sorted(reqs, key=lambda r: (r["arrival"], r["index"])):
-        n = r["n"]
-        dev[:n].copy_(pinned[offs[r["index"]]:offs[r["index"] + 1]], non_blocking=True)
-        if r["kind"] == 0:
-            fs[r["filter"]].insert(dev[:n])
-        else:
-            fs[r["filter"]].query(dev[:n], dbm)
-            out = np.zeros((n + 63) // 64, dtype=np.uint64)
-            out[:] = dbm[: (n + 63) // 64].cpu().numpy().view(np.uint64)
-            plain_bms[r["index"]] = out
-    torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t0
-    for f in fs:
-        f.close()
+    reps = max(5, min(args.steps, 10))
 
-    closed_bms, closed_st, closed_span, _ = serve(0.0)
+    def plain():
+        # one request at a time, in arrival order, one stream
+        fs = [bc.Filter(f["M"], 14, 2, bc.COST_MIX, 50.0, hash_seed=f["key_seed"], batch=f["B"])
+              for f in filters]
+        dev = torch.empty(max(sizes), dtype=torch.int64, device="cuda")
+        dbm = torch.empty((max(sizes) + 63) // 64, dtype=torch.int64, device="cuda")
+        bms = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in sorted(reqs, key=lambda r: (r["arrival"], r["index"])):
+            n = r["n"]
+            dev[:n].copy_(pinned[offs[r["index"]]:offs[r["index"] + 1]], non_blocking=True)
+            if r["kind"] == 0:
+                fs[r["filter"]].insert(dev[:n])
+            else:
+                fs[r["filter"]].query(dev[:n], dbm)
+                out = np.zeros((n + 63) // 64, dtype=np.uint64)
+                out[:] = dbm[: (n + 63) // 64].cpu().numpy().view(np.uint64)
+                bms[r["index"]] = out
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        for f in fs:
+            f.close()
+        return bms, secs
+
+    plain_runs = [plain() for _ in range(reps)]
+    plain_bms = plain_runs[0][0]
+    plain_times = sorted(t for _, t in plain_runs)
+    plain_s = statistics.median(plain_times)
+    closed_runs = [serve(0.0) for _ in range(reps)]
+    closed_runs.sort(key=lambda r: r[2])
+    closed_bms, closed_st, closed_span, _ = closed_runs[len(closed_runs) // 2]
     capacity = total_keys / closed_span
     mean_req = total_keys / len(reqs)
-    same = all(np.array_equal(closed_bms[j], b) for j, b in plain_bms.items())
+    same = all(all(np.array_equal(run[0][j], b) for j, b in plain_bms.items())
+               for run in plain_runs[1:] + [(c[0], None) for c in closed_runs])
     loads = []
     for load in (0.5, 0.8, 0.95):
         rate = load * capacity / mean_req          # requests per second
@@ -460,8 +489,13 @@ def run_serve(args):
     out = {"workload": "serving_64_filters", "metric": "served keys/s with p50/p99 latency",
            "requests": len(reqs), "keys": total_keys,
            "filter_gb": round(sum(f["M"] for f in filters) * 64 / 1e9, 3),
+           "repeats": reps,
            "plain_per_request_mkeys_s": round(total_keys / plain_s / 1e6, 1),
+           "plain_per_request_mkeys_s_range": [round(total_keys / plain_times[-1] / 1e6, 1),
+                                               round(total_keys / plain_times[0] / 1e6, 1)],
            "served_capacity_mkeys_s": round(capacity / 1e6, 1),
+           "served_capacity_mkeys_s_range": [round(total_keys / closed_runs[-1][2] / 1e6, 1),
+                                             round(total_keys / closed_runs[0][2] / 1e6, 1)],
            "served_vs_plain": round(capacity / (total_keys / plain_s), 2),
            "closed_loop": {"p50_ms": round(closed_st.p50_latency_s * 1e3, 3),
                            "p99_ms": round(closed_st.p99_latency_s * 1e3, 3),
@@ -471,8 +505,9 @@ def run_serve(args):
                            "launch_host_s": round(closed_st.launch_host_s, 3),
                            "span_s": round(closed_span, 3)},
            "poisson": loads, "identical_to_plain_results": bool(same),
-           "timing": "host steady clock (server) and wall clock (plain); keys from pinned host memory"}
-    print(json.dumps(out))
+           "timing": "host steady clock (server) and wall clock (plain), medians of the repeats; "
+                     "keys from pinned host memory"}
+    emit(out)
 
 
 SWEEP_SETTINGS = [(1, "EXP", 0), (2, "MIX", 50.0), (2, "LA", 3.5), (2, "EXP", 0), (3, "MIX", 50.0),
@@ -503,32 +538,44 @@ def run_sweep(args):
     bm = torch.empty((neg.numel() + 63) // 64, dtype=torch.int64, device="cuda")
     s = torch.cuda.current_stream()
     rows = []
+    reps = max(5, min(args.steps, 10))
     for c, cname, par in SWEEP_SETTINGS:
         par = phi if cname == "EXP" else par
         f = bc.Filter(M, k, c, kinds[cname], par, hash_seed=3001, batch=B)
-        n_prev = 0
+        times = {b: ([], []) for b in SWEEP_BITS}
+        first = {}
+        for rep in range(reps):  # the filter regrown from empty each time; results are deterministic
+            f.clear(s)
+            n_prev = 0
+            for b in SWEEP_BITS:
+                n = (1 << 32) // b
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(s)
+                f.insert(keys[n_prev:n], s)
+                e[1].record(s)
+                f.query(neg, bm, s)
+                e[2].record(s)
+                torch.cuda.synchronize()
+                times[b][0].append(e[0].elapsed_time(e[1]))
+                times[b][1].append(e[1].elapsed_time(e[2]))
+                if rep == 0:
+                    st = f.stats()
+                    W = int(np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")[: neg.numel()].sum())
+                    first[b] = (n, n_prev, W, st)
+                n_prev = n
         for b in SWEEP_BITS:
-            n = (1 << 32) // b
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(s)
-            f.insert(keys[n_prev:n], s)
-            e[1].record(s)
-            f.query(neg, bm, s)
-            e[2].record(s)
-            torch.cuda.synchronize()
-            st = f.stats()
-            W = int(np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")[: neg.numel()].sum())
+            n, n_prev, W, st = first[b]
+            ti, tq = statistics.median(times[b][0]), statistics.median(times[b][1])
             rows.append({"c": c, "cost": cname, "bits_per_key": b, "n": n, "fpr": W / neg.numel(),
                          "false_positives": W, "fpr_est_hist": st.fpr_est,
                          "blocked_bloom_formula": sweeps.blocked_bloom_fpr(n, M, k),
                          "bloom_formula": sweeps.bloom_fpr(n, M * 512, k),
                          "inserted": st.inserted, "skipped": st.skipped, "set_bits": st.set_bits,
-                         "insert_mkeys_s": round((n - n_prev) / (e[0].elapsed_time(e[1]) / 1e3) / 1e6, 1),
-                         "query_mkeys_s": round(neg.numel() / (e[1].elapsed_time(e[2]) / 1e3) / 1e6, 1)})
-            n_prev = n
+                         "insert_mkeys_s": round((n - n_prev) / (ti / 1e3) / 1e6, 1),
+                         "query_mkeys_s": round(neg.numel() / (tq / 1e3) / 1e6, 1)})
         f.close()
-    print(json.dumps({"workload": "overload_sweep", "M": M, "k": k, "B": B, "negatives": neg.numel(),
-                      "rows": rows}))
+    emit({"workload": "overload_sweep", "M": M, "k": k, "B": B, "negatives": neg.numel(),
+          "repeats": reps, "timing": "CUDA events, median of the repeats", "rows": rows})
 
 
 def run_batching(args):
@@ -549,11 +596,16 @@ def run_batching(args):
         for B in (1, 16, 256, 4096, 1 << 14, 1 << 16, 1 << 18, 1 << 20):
             f = bc.Filter(M, k, c, bc.COST_EXP, phi, hash_seed=3001, batch=B)
             s = torch.cuda.current_stream()
-            a = torch.cuda.Event(enable_timing=True)
-            b2 = torch.cuda.Event(enable_timing=True)
-            a.record(s)
-            f.insert(keys, s)
-            b2.record(s)
+            ins_ms = []
+            for rep in range(max(5, min(args.steps, 10))):
+                f.clear(s)
+                a = torch.cuda.Event(enable_timing=True)
+                b2 = torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                f.insert(keys, s)
+                b2.record(s)
+                torch.cuda.synchronize()
+                ins_ms.append(a.elapsed_time(b2))
             f.query(neg, bm, s)
             torch.cuda.synchronize()
             st = f.stats()
@@ -564,10 +616,11 @@ def run_batching(args):
             sd = float(math.sqrt((h * (L - mean) ** 2).sum() / M))
             rows.append({"c": c, "B": B, "fpr": W / neg.numel(), "fpr_est_hist": st.fpr_est,
                          "mean_load": round(mean, 3), "sd_load": round(sd, 3),
-                         "insert_ms": round(a.elapsed_time(b2), 3)})
+                         "insert_ms": round(statistics.median(ins_ms), 3),
+                         "insert_ms_range": [round(min(ins_ms), 3), round(max(ins_ms), 3)]})
             f.close()
-    print(json.dumps({"workload": "batching_cost", "M": M, "k": k, "n": n, "cost": "EXP golden ratio",
-                      "rows": rows}))
+    emit({"workload": "batching_cost", "M": M, "k": k, "n": n, "cost": "EXP golden ratio",
+                      "rows": rows})
 
 
 def run_small(args):
@@ -585,9 +638,9 @@ def run_small(args):
     rows = []
     for B in (65536, 1):
         f = bc.Filter(32768, 14, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=B)
-        reps = max(1, args.steps) if B > 1 else 1
+        reps = max(5, args.steps) if B > 1 else 5
         ti, tq = [], []
-        for _ in range(reps + (1 if B > 1 else 0)):
+        for _ in range(reps + 1):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             f.clear(s)
             e[0].record(s)
@@ -598,8 +651,7 @@ def run_small(args):
             torch.cuda.synchronize()
             ti.append(e[0].elapsed_time(e[1]))
             tq.append(e[1].elapsed_time(e[2]))
-        if B > 1:
-            ti, tq = ti[1:], tq[1:]
+        ti, tq = ti[1:], tq[1:]  # after one warm-up
         h = bm.cpu().numpy().view(np.uint8)
         bits = np.unpackbits(h, bitorder="little")[: dq.numel()]
         st = f.stats()
@@ -611,8 +663,8 @@ def run_small(args):
                      "fpr": float(bits[1_000_000:].mean()), "fpr_est_hist": st.fpr_est,
                      "inserted": st.inserted, "skipped": st.skipped})
         f.close()
-    print(json.dumps({"workload": "small_uniform", "M": 32768, "k": 14, "c": 2, "cost": "MIX 50",
-                      "rows": rows}))
+    emit({"workload": "small_uniform", "M": 32768, "k": 14, "c": 2, "cost": "MIX 50",
+          "timing": "CUDA events, median of at least 5 repeats after one warm-up", "rows": rows})
 
 
 def run_learn(args):
@@ -653,12 +705,12 @@ def run_learn(args):
     learned = evaluate(bc.COST_EXP, phi, table)
     exp_cost = evaluate(bc.COST_EXP, phi)
     mix_cost = evaluate(bc.COST_MIX, 50.0)
-    print(json.dumps({"workload": "learned_cost", "M": M, "k": k, "c": c, "B": B, "n": n,
+    emit({"workload": "learned_cost", "M": M, "k": k, "c": c, "B": B, "n": n,
                       "train_steps": args.train_steps, "train_seconds": round(train_s, 2),
                       "reward_first10": float(np.mean(rewards[:10])), "reward_last10": float(np.mean(rewards[-10:])),
                       "learned": learned, "exp_golden_ratio": exp_cost, "mix_sigma50": mix_cost,
                       "fpr_gain_vs_exp": exp_cost["fpr"] / learned["fpr"] if learned["fpr"] else None,
-                      "note": "gain > 1 means the learned table gives a lower FPR than cost^EXP"}))
+                      "note": "gain > 1 means the learned table gives a lower FPR than cost^EXP"})
 
 
 def golden_pbar():
@@ -901,8 +953,8 @@ def run_cluster(args):
         row["identical"] = bool(np.array_equal(words["global"], words["cluster"]))
         f.close()
         rows.append(row)
-    print(json.dumps({"workload": "cluster_resident_insert", "rows": rows,
-                      "timing": "CUDA events, median of --steps after --warmup"}))
+    emit({"workload": "cluster_resident_insert", "rows": rows,
+                      "timing": "CUDA events, median of --steps after --warmup"})
 
 
 def run_lanes(args):
@@ -947,8 +999,8 @@ def run_lanes(args):
             rows.append(row)
         del keys
         torch.cuda.empty_cache()
-    print(json.dumps({"workload": "insert_lanes_by_filter_size", "B": 1 << 20, "bits_per_key": 12,
-                      "rows": rows, "timing": "CUDA events, median of --steps after one warm-up"}))
+    emit({"workload": "insert_lanes_by_filter_size", "B": 1 << 20, "bits_per_key": 12,
+                      "rows": rows, "timing": "CUDA events, median of --steps after one warm-up"})
 
 
 def run_variants(args):
@@ -1027,8 +1079,8 @@ def run_variants(args):
         rows.append(row)
         del keys, negatives, bitmap
         torch.cuda.empty_cache()
-    print(json.dumps({"workload": "set_and_bit_selection_variants", "rows": rows,
-                      "timing": "CUDA events, median of --steps after one warm-up"}))
+    emit({"workload": "set_and_bit_selection_variants", "rows": rows,
+                      "timing": "CUDA events, median of --steps after one warm-up"})
 
 
 def run_figures(args):
@@ -1050,7 +1102,7 @@ def run_figures(args):
         if hist is not None:
             r["hist_nonzero"] = {str(L): h for L, h in enumerate(hist) if h}
         keys_done[0] += r["n"] + r["N"]
-        print(json.dumps(r), flush=True)
+        emit(r)
 
     if args.workload == "fig4":
         rows = sweeps.fig4(n=n, ks=ks, log=log)
@@ -1075,14 +1127,26 @@ def run_figures(args):
         cols = ["k", "cost", "param", "c", "load_mean", "load_sd", "log2_fpr"]
         table = [[r["k"], r["cost"], round(r["param"], 4), r["c"], round(r["load_mean"], 2),
                   round(r["load_sd"], 2), l2(r)] for r in rows]
-    print(json.dumps({"workload": args.workload, "points": len(rows), "keys_per_point": n,
+    emit({"workload": args.workload, "points": len(rows), "keys_per_point": n,
                       "device_s": round(dev_s, 3), "wall_s": round(wall, 3),
                       "gkeys_per_s_device": round(keys_done[0] / dev_s / 1e9, 3),
-                      "gpu": torch.cuda.get_device_name(), "columns": cols, "table": table}))
+                      "gpu": torch.cuda.get_device_name(), "columns": cols, "table": table})
 
 
 def main():
+    global _WORKLOAD_CLOCKS
     args = parse()
+    if args.workload != "dna" and args.impl != "reference":
+        _WORKLOAD_CLOCKS = ClockSampler(0)
+        _WORKLOAD_CLOCKS.start()
+    try:
+        run_main(args)
+    finally:
+        if _WORKLOAD_CLOCKS is not None:
+            _WORKLOAD_CLOCKS.stop()
+
+
+def run_main(args):
     if args.workload in ("fig4", "fig8", "fig10"):
         run_figures(args)
         return
@@ -1105,7 +1169,7 @@ def main():
         import torch
         import paper_2501_18977_gb300 as bc
         peak, _ = peaks()
-        print(json.dumps(hbm_resident(bc, torch, peak, 0, reps=args.reps)))
+        emit(hbm_resident(bc, torch, peak, 0, reps=args.reps))
         return
     if args.workload == "many":
         run_many(args)

@@ -230,11 +230,15 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
     // fastest with four lanes per key up to half the L2 size (2 MiB: 0.112 ms
     // against 0.131 with one lane; 64 MiB, three choices: 3.07 ms against 3.21
     // with two), with two lanes up to 1.5 times the L2 size (128 MiB: 6.36 ms
-    // against 6.50 with four; 192 MiB: 11.46 against 11.75) and four beyond
-    // (256 MiB: 15.85 ms against 17.71 with two; 512 MiB: 38.9 against 48.5);
+    // against 6.50 with four; 192 MiB: 11.46 against 11.75) and, with three
+    // choices, four beyond (256 MiB: 16.42 ms against 17.41 with two);
     // queries with one lane while the filter fits in L2 and two beyond
     const uint64_t bytes = params->nblocks * 64ull;
-    f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4 : bytes <= 3ull * (uint64_t)l2 / 2 ? 2 : 4;
+    // Beyond 1.5 L2 with two choices (and the bulk set) two lanes won too:
+    // 256 MiB 12.77 against 14.02 ms, 512 MiB 30.58 against 30.79.
+    f->lanes_choose = bytes <= (uint64_t)l2 / 2 ? 4
+                      : bytes <= 3ull * (uint64_t)l2 / 2 ? 2
+                      : params->choices <= 2 ? 2 : 4;
     f->lanes_query = bytes <= (uint64_t)l2 ? 1 : 2;
     // the bulk set paid at the L2 size and beyond, except with three choices
     // at about the L2 size (one GB300, c = 2, k = 12: 128 MiB 3.26 against
