@@ -999,8 +999,38 @@ def run_lanes(args):
             rows.append(row)
         del keys
         torch.cuda.empty_cache()
+    # around the L2 size the best width also depends on the load: two and
+    # four lanes at 32, 21.5 and 16 bits per key
+    load_rows = []
+    for mib in (96, 128, 192):
+        M = mib * (1 << 20) // 64
+        for bpk in (32, 21.5, 16):
+            n = int(M * 512 / bpk)
+            keys = bc.generate_keys(n, 7)
+            for c, k, cost, par, cname in ((3, 16, bc.COST_LA, 3.5, "LA"), (2, 12, bc.COST_EXP, phi, "EXP")):
+                f = bc.Filter(M, k, c, cost, par, hash_seed=5, batch=1 << 20, stream=s)
+                f.set_tuning(cluster_max=0)
+                row = {"filter_mib": mib, "bits_per_key": bpk, "c": c, "k": k, "cost": cname}
+                for lanes in (2, 4):
+                    f.set_tuning(lanes_choose=lanes)
+                    times = []
+                    for rep in range(1 + max(1, args.steps)):
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        f.clear(s)
+                        a.record(s)
+                        f.insert(keys, s)
+                        b.record(s)
+                        torch.cuda.synchronize()
+                        if rep:
+                            times.append(a.elapsed_time(b))
+                    row["lanes%d_ms" % lanes] = round(statistics.median(times), 4)
+                f.close()
+                load_rows.append(row)
+            del keys
+            torch.cuda.empty_cache()
     emit({"workload": "insert_lanes_by_filter_size", "B": 1 << 20, "bits_per_key": 12,
-                      "rows": rows, "timing": "CUDA events, median of --steps after one warm-up"})
+          "rows": rows, "load_rows": load_rows, "timing": "CUDA events, median of --steps after one warm-up"})
 
 
 def run_variants(args):

@@ -154,8 +154,10 @@ int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
 /*
  * blowchoc_insert_host / blowchoc_query_host -- blowchoc_insert and
  * blowchoc_query on HOST buffers. Keys move to the device in chunks through
- * two device staging slots on the filter's own copy stream, so the copy of
- * one chunk overlaps the kernels of the previous one on `stream`. Insert
+ * a ring of 8 device staging slots on the filter's own copy stream, so the
+ * copies of the next chunks overlap the kernels of earlier ones on `stream`;
+ * the ring continues across calls, so a query's first copies overlap the
+ * kernels of the insert before it. Insert
  * chunks are whole multiples of the batch size B, so the words and counters
  * equal those of one blowchoc_insert over all n keys. Query chunks are
  * multiples of 64 keys, and the bitmap layout is that of blowchoc_query.
@@ -164,8 +166,9 @@ int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *   h_bitmap  host, out, ceil(n/64) uint64 words.
  * Both calls are ordered on `stream` and return once the work is queued. The
  * caller keeps both buffers alive and unchanged until `stream` completes;
- * the bitmap is complete when it does. The staging (two slots of up to 2^22
- * keys, or of one batch if B is larger) is owned by the filter and grows on
+ * the bitmap is complete when it does. The staging (8 slots of up to 2^22
+ * keys, 256 MiB at most, fewer keys per slot for small inputs; two slots of
+ * one batch if B is larger) is owned by the filter and grows on
  * demand. Growing synchronises the device. Host-buffer calls on one filter
  * share that staging: issue them from one host thread at a time (any
  * streams may be used; the staging events order the slots between them).

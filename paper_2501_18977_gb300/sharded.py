@@ -27,6 +27,8 @@ def exchange_keys(part_keys, counts, group):
     segment per source rank in rank order; received count per source)."""
     import torch
     import torch.distributed as dist
+    if len(counts) != dist.get_world_size(group) or sum(int(c) for c in counts) != part_keys.numel():
+        raise ValueError("one count per rank, summing to the number of partitioned keys")
     send = torch.tensor([int(c) for c in counts], dtype=torch.int64, device=part_keys.device)
     recv = torch.empty_like(send)
     dist.all_to_all_single(recv, send, group=group)

@@ -78,3 +78,46 @@ def test_host_calls_reuse_staging_across_calls_and_streams():
     finally:
         f.close()
         g.close()
+
+
+def test_staging_ring_wraps_within_and_across_calls():
+    """More chunks than staging slots in one call (21 chunks of 2^22 keys),
+    then many alternating small insert and query calls whose staging slots
+    wrap around the ring many times: words and every bitmap equal the device
+    calls'."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    M, k, c, B = 1 << 16, 12, 2, 1 << 20
+    big = workloads.uniform_keys(123, 21 << 22)
+    a = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=9, batch=B)
+    b = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=9, batch=B)
+    try:
+        s = torch.cuda.current_stream()
+        hb = _host(big, True)
+        a.insert_host(hb, s)
+        b.insert(to_dev(big))
+        small_bms, alive = [], []   # pinned buffers stay alive until the stream completes
+        for j in range(40):
+            ks = workloads.uniform_keys(1000 + j, 30000 + 17 * j)
+            qs = workloads.uniform_keys(2000 + j, 20000 + 29 * j)
+            hk, hq = _host(ks, True), _host(qs, True)
+            alive += [hk, hq]
+            a.insert_host(hk, s)
+            small_bms.append((a.query_host(hq, stream=s), qs))
+            b.insert(to_dev(ks))
+        s.synchronize()
+        assert np.array_equal(a.words_host(), b.words_host())
+        # the queries saw the filter after their own call's inserts: replay on b's prefix
+        c2 = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=9, batch=B)
+        try:
+            c2.insert(to_dev(big))
+            for j, (bm, qs) in enumerate(small_bms):
+                ks = workloads.uniform_keys(1000 + j, 30000 + 17 * j)
+                c2.insert(to_dev(ks))
+                want = c2.query(to_dev(qs)).cpu().numpy().view(np.uint64)
+                assert np.array_equal(bm[: len(want)], want), j
+        finally:
+            c2.close()
+    finally:
+        a.close()
+        b.close()
