@@ -1319,13 +1319,17 @@ def run_main(args):
         barrier()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         a.record(stream)
-        for _ in range(args.steps):
+        marks[0].record(stream)
+        for i in range(args.steps):
             e2e_step()
+            marks[i + 1].record(stream)
         b.record(stream)
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(a.elapsed_time(b) / args.steps, world, "cuda")
+        per_step = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
         hits = int(np.unpackbits(h_bm.numpy().view(np.uint8), bitorder="little")[:n_q].sum())
         # the copy ceiling of the same step: the pinned host-to-device rate of
         # one plain copy of the step's keys, best of 3, on this machine
@@ -1340,7 +1344,10 @@ def run_main(args):
             h2d_ms = t if h2d_ms is None else min(h2d_ms, t)
         e2e = {"value": round(job_mkeys_per_s(n_ins + n_q, world, ems), 3), "unit": "Mkeys/s",
                "h2d_bytes_per_step": int(8 * (n_ins + n_q)), "d2h_bytes_per_step": int(8 * nwords),
-               "ms_per_step": round(ems, 3), "api": "blowchoc_insert_host + blowchoc_query_host (pinned)",
+               "ms_per_step": round(ems, 3),
+               "ms_per_step_min_median_max": [round(per_step[0], 3), round(statistics.median(per_step), 3),
+                                              round(per_step[-1], 3)],
+               "api": "blowchoc_insert_host + blowchoc_query_host (pinned)",
                "query_hits": hits,
                "h2d_gbs": round(8 * (n_ins + n_q) / (h2d_ms / 1e3) / 1e9, 1),
                "copy_floor_ms": round(h2d_ms, 3),

@@ -3,9 +3,11 @@
 // A scheduler thread owns all GPU work: it releases submitted requests at
 // their arrival times into per-filter FIFOs, admits registered filters in
 // order while their memory fits the HBM budget, and launches waves. A wave
-// takes the head request of every ready filter (one request per filter, so
-// consecutive inserts of a filter stay separate calls with their own batches),
-// up to the wave size and the free staging memory; it copies the keys in,
+// takes, for every ready filter, its head request if that is an insert (one
+// insert per filter, so consecutive inserts stay separate calls with their
+// own batches), or its run of consecutive queries (they see the same filter,
+// so they share one launch item, each padded to whole bitmap words), up to
+// the wave size and the free staging memory; it copies the keys in,
 // runs one insert_many and one query_many over the whole wave, copies the
 // bitmaps out and records an event. Waves rotate over several streams, so
 // copies and kernels of different waves overlap; a filter's next request
@@ -41,6 +43,7 @@ struct Req {
     double done = -1.0;
     uint64_t staging = 0;   // device bytes while in flight
     bool keys_pinned = false, bitmap_pinned = false;
+    bool clear_tail = false;  // a coalesced query followed by padding: bits n..63 of its last word
     size_t key_bounce = SIZE_MAX, bm_bounce = SIZE_MAX;  // offsets in the pinned arenas
 };
 
@@ -158,6 +161,7 @@ namespace {
 
 constexpr int kWavesPerStream = 2;
 constexpr uint64_t kHeavyRounds = 64;  // inserts needing more batches run in a wave of their own
+constexpr size_t kQueryRun = 64;        // queries of one filter sharing one launch item, at most
 
 // Cluster-resident inserts in the server: moderate clusters (4 lanes per key,
 // 512 keys of a batch per CTA) for its filters and many-filter calls. Under
@@ -240,6 +244,11 @@ void collect(blowchoc_server *s) {
                 s->bm_arena.release(r->bm_bounce, (r->n + 63) / 64 * 8);
                 r->bm_bounce = SIZE_MAX;
             }
+            if (r->clear_tail && (r->n & 63)) {
+                // the padding keys after this request answered too: their bits go
+                r->h_bitmap[r->n / 64] &= (1ull << (r->n & 63)) - 1ull;
+                r->clear_tail = false;
+            }
             if (r->key_bounce != SIZE_MAX) {
                 s->keys_arena.release(r->key_bounce, r->n * 8);
                 r->key_bounce = SIZE_MAX;
@@ -278,6 +287,11 @@ bool launch_wave(blowchoc_server *s) {
         if (!s->waves[w].active) { wi = (int)w; break; }
     if (wi < 0) return false;
     Wave &wv = s->waves[wi];
+    // a wave takes, per filter, its next insert, or its next run of queries
+    // (queries with no insert between them see the same filter and share one
+    // launch item: their keys are concatenated, each padded to a multiple of
+    // 64 so that its bitmap starts on a word of the item's bitmap)
+    std::vector<std::vector<Req *>> groups;
     std::vector<Req *> take;
     uint64_t staging = 0;
     const int nf = (int)s->slots.size();
@@ -286,7 +300,20 @@ bool launch_wave(blowchoc_server *s) {
         const uint64_t B = s->slots[r->filter].params.batch;
         return r->kind == BLOWCHOC_REQ_INSERT && (r->n + B - 1) / B > kHeavyRounds;
     };
-    for (int i = 0; i < nf && take.size() < s->cfg.max_wave_requests; ++i) {
+    // host bounce space for a request whose buffers are not pinned
+    auto bounce = [s](Req *r) {
+        if (!r->keys_pinned && r->key_bounce == SIZE_MAX) {
+            r->key_bounce = s->keys_arena.alloc(r->n * 8);
+            if (r->key_bounce == SIZE_MAX) return false;
+        }
+        if (r->kind == BLOWCHOC_REQ_QUERY && !r->bitmap_pinned && r->bm_bounce == SIZE_MAX) {
+            r->bm_bounce = s->bm_arena.alloc((r->n + 63) / 64 * 8);
+            if (r->bm_bounce == SIZE_MAX) return false;
+        }
+        return true;
+    };
+    bool alone = false;
+    for (int i = 0; i < nf && take.size() < s->cfg.max_wave_requests && !alone; ++i) {
         Slot &sl = s->slots[(s->rr + i) % nf];
         if (!sl.admitted || sl.removed || sl.fifo.empty()) continue;
         // a filter with work in flight on another stream waits for it here,
@@ -294,73 +321,102 @@ bool launch_wave(blowchoc_server *s) {
         if (sl.last_wave >= 0 && s->waves[sl.last_wave].stream != st) continue;
         Req *r = sl.fifo.front();
         if (s->staging_used + staging + r->staging > s->cfg.staging_bytes) continue;
-        if (!r->keys_pinned && r->key_bounce == SIZE_MAX) {
-            r->key_bounce = s->keys_arena.alloc(r->n * 8);
-            if (r->key_bounce == SIZE_MAX) continue;
-        }
-        if (r->kind == BLOWCHOC_REQ_QUERY && !r->bitmap_pinned && r->bm_bounce == SIZE_MAX) {
-            r->bm_bounce = s->bm_arena.alloc((r->n + 63) / 64 * 8);
-            if (r->bm_bounce == SIZE_MAX) continue;
-        }
+        if (!bounce(r)) continue;
         if (heavy(r)) {
             if (take.empty()) {
+                groups.push_back({r});
                 take.push_back(r);
                 staging += r->staging;
-                break;
+                alone = true;
             }
             continue;
         }
+        std::vector<Req *> g{r};
         take.push_back(r);
         staging += r->staging;
+        if (r->kind == BLOWCHOC_REQ_QUERY) {
+            for (size_t j = 1; j < sl.fifo.size() && take.size() < s->cfg.max_wave_requests &&
+                               g.size() < kQueryRun; ++j) {
+                Req *q = sl.fifo[j];
+                if (q->kind != BLOWCHOC_REQ_QUERY) break;
+                if (s->staging_used + staging + q->staging > s->cfg.staging_bytes) break;
+                if (!bounce(q)) break;
+                g.push_back(q);
+                take.push_back(q);
+                staging += q->staging;
+            }
+        }
+        groups.push_back(g);
     }
     if (take.empty()) return false;
     s->rr = (s->rr + 1) % std::max(nf, 1);
     s->next_stream = (st + 1) % (int)s->streams.size();
     cudaStream_t stream = s->streams[st];
     std::vector<blowchoc_work> ins, qry;
+    std::vector<std::vector<Req *>> qry_groups;  // the requests behind each query item
     std::vector<void *> bufs;
     const double t = s->now();
     const auto h0 = Clock::now();
-    for (Req *r : take) {
-        Slot &sl = s->slots[r->filter];
-        sl.fifo.pop_front();
+    {
+        const cudaError_t e0 = cudaEventRecord(wv.start, stream);
+        if (e0 != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave event", e0); return false; }
+    }
+    for (const std::vector<Req *> &g : groups) {
+        Slot &sl = s->slots[g.front()->filter];
         // the filter's earlier work, if still in flight, is on this stream
         // (selection above): stream order keeps its requests in FIFO order
-        if (r == take.front()) {
-            const cudaError_t e0 = cudaEventRecord(wv.start, stream);
-            if (e0 != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave event", e0); return false; }
+        uint64_t padded = 0;  // keys of the item, each request but the last padded to 64
+        for (size_t j = 0; j < g.size(); ++j) {
+            sl.fifo.pop_front();
+            padded += j + 1 < g.size() ? (g[j]->n + 63) / 64 * 64 : g[j]->n;
         }
         void *dk = nullptr, *db = nullptr;
-        const void *src = r->h_keys;
-        if (r->key_bounce != SIZE_MAX) {
-            std::memcpy(s->h_keys_arena + r->key_bounce, r->h_keys, r->n * 8);
-            src = s->h_keys_arena + r->key_bounce;
+        cudaError_t e = cudaMallocFromPoolAsync(&dk, ((padded + 63) / 64 * 64) * 8, s->pool, stream);
+        uint64_t off = 0;
+        for (Req *r : g) {
+            if (e != cudaSuccess) break;
+            const void *src = r->h_keys;
+            if (r->key_bounce != SIZE_MAX) {
+                std::memcpy(s->h_keys_arena + r->key_bounce, r->h_keys, r->n * 8);
+                src = s->h_keys_arena + r->key_bounce;
+            }
+            e = cudaMemcpyAsync((uint64_t *)dk + off, src, r->n * 8, cudaMemcpyHostToDevice, stream);
+            off += (r->n + 63) / 64 * 64;
         }
-        cudaError_t e = cudaMallocFromPoolAsync(&dk, r->n * 8, s->pool, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dk, src, r->n * 8, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess && r->kind == BLOWCHOC_REQ_QUERY)
-            e = cudaMallocFromPoolAsync(&db, (r->n + 63) / 64 * 8, s->pool, stream);
+        if (e == cudaSuccess && g.front()->kind == BLOWCHOC_REQ_QUERY)
+            e = cudaMallocFromPoolAsync(&db, (padded + 63) / 64 * 8, s->pool, stream);
         if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "wave staging", e); return false; }
         bufs.push_back(dk);
         if (db) bufs.push_back(db);
-        blowchoc_work w{sl.f, (const uint64_t *)dk, r->n, (uint64_t *)db};
-        (r->kind == BLOWCHOC_REQ_QUERY ? qry : ins).push_back(w);
-        r->launched = t;
-        sl.inflight++;
-        sl.unlaunched--;
+        blowchoc_work w{sl.f, (const uint64_t *)dk, padded, (uint64_t *)db};
+        if (g.front()->kind == BLOWCHOC_REQ_QUERY) {
+            qry.push_back(w);
+            qry_groups.push_back(g);
+        } else {
+            ins.push_back(w);
+        }
+        for (size_t j = 0; j < g.size(); ++j) {
+            Req *r = g[j];
+            r->launched = t;
+            r->clear_tail = j + 1 < g.size();  // padded: not the item's last request
+            sl.inflight++;
+            sl.unlaunched--;
+        }
         sl.last_wave = wi;
     }
     int rc = BLOWCHOC_OK;
     if (!ins.empty()) rc = blowchoc_insert_many(s->batches[st], ins.data(), (uint32_t)ins.size(), stream);
     if (!rc && !qry.empty()) rc = blowchoc_query_many(s->batches[st], qry.data(), (uint32_t)qry.size(), stream);
     if (rc) { fail_locked(s, rc, "wave launch", cudaSuccess); return false; }
-    size_t qi = 0;
-    for (Req *r : take) {
-        if (r->kind != BLOWCHOC_REQ_QUERY) continue;
-        void *dst = r->bm_bounce != SIZE_MAX ? (void *)(s->h_bm_arena + r->bm_bounce) : (void *)r->h_bitmap;
-        const cudaError_t e = cudaMemcpyAsync(dst, qry[qi++].d_bitmap, (r->n + 63) / 64 * 8,
-                                              cudaMemcpyDeviceToHost, stream);
-        if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "bitmap copy", e); return false; }
+    for (size_t qi = 0; qi < qry_groups.size(); ++qi) {
+        uint64_t woff = 0;  // each request's bitmap starts on a word of the item's bitmap
+        for (Req *r : qry_groups[qi]) {
+            void *dst = r->bm_bounce != SIZE_MAX ? (void *)(s->h_bm_arena + r->bm_bounce) : (void *)r->h_bitmap;
+            const cudaError_t e = cudaMemcpyAsync(dst, qry[qi].d_bitmap + woff, (r->n + 63) / 64 * 8,
+                                                  cudaMemcpyDeviceToHost, stream);
+            if (e != cudaSuccess) { fail_locked(s, BLOWCHOC_ECUDA, "bitmap copy", e); return false; }
+            woff += (r->n + 63) / 64;
+        }
     }
     for (void *p : bufs) cudaFreeAsync(p, stream);
     cudaError_t e = cudaEventRecord(wv.ev, stream);

@@ -185,3 +185,34 @@ def test_server_rejects_what_cannot_fit():
             srv.submit(fid, 7, big[:10])
     finally:
         srv.close()
+
+
+def test_runs_of_queries_share_a_launch_and_keep_exact_bitmaps():
+    """All requests arrive at once; a filter's consecutive queries (odd
+    sizes, so each is padded inside the shared launch item) share a launch,
+    every bitmap equals the oracle's, and the bits past each request's last
+    key are zero."""
+    import paper_2501_18977_gb300 as bc
+    M, B = 4096, 2048
+    seed = 3
+    keys_ins = workloads.uniform_keys(31, 50000)
+    reqs, keys = [], {}
+    # filter 0: one insert, then a run of 40 queries of odd sizes; filter 1 the same shape
+    for f in range(2):
+        j = len(reqs)
+        reqs.append(dict(index=j, arrival=0.0, kind=0, filter=f, n=len(keys_ins)))
+        keys[j] = keys_ins
+        for q in range(40):
+            j = len(reqs)
+            n = 1 + 37 * q
+            qk = np.concatenate([keys_ins[q * 100: q * 100 + n // 2], workloads.uniform_keys(700 + j, n - n // 2)])
+            reqs.append(dict(index=j, arrival=0.0, kind=1, filter=f, n=n))
+            keys[j] = qk
+    filters = [dict(index=f, M=M, B=B, key_seed=seed + f) for f in range(2)]
+    served, served_words, st, _ = _serve(bc, filters, reqs, keys, time_scale=0.0, wave=64, streams=2)
+    assert st.completed == len(reqs)
+    assert st.mean_wave_requests > 2.0
+    _check_oracle(filters, reqs, keys, served, served_words)
+    for r in reqs:
+        if r["kind"] == 1 and r["n"] % 64:
+            assert int(served[r["index"]][-1]) >> (r["n"] % 64) == 0, r["index"]
