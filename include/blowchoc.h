@@ -154,24 +154,28 @@ int blowchoc_insert_noalloc(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
 /*
  * blowchoc_insert_host / blowchoc_query_host -- blowchoc_insert and
  * blowchoc_query on HOST buffers. Keys move to the device in chunks through
- * a ring of 8 device staging slots on the filter's own copy stream, so the
- * copies of the next chunks overlap the kernels of earlier ones on `stream`;
- * the ring continues across calls, so a query's first copies overlap the
- * kernels of the insert before it. Insert
- * chunks are whole multiples of the batch size B, so the words and counters
- * equal those of one blowchoc_insert over all n keys. Query chunks are
- * multiples of 64 keys, and the bitmap layout is that of blowchoc_query.
+ * a device staging ring on the filter's own copy stream, so the copies of
+ * the next chunks overlap the kernels of earlier ones on `stream`. Chunks
+ * grow within a call from 2^20 keys to 2^24 (at most a quarter of the ring;
+ * 2^22 for a query call issued while the device is idle, which the copies
+ * bound), one insert or query launch each. The ring position continues across
+ * calls, so a query's first copies overlap the kernels of the insert before
+ * it. Insert chunks are whole multiples of the batch size B, so the words and
+ * counters equal those of one blowchoc_insert over all n keys. Query chunks
+ * are multiples of 64 keys, and the bitmap layout is that of blowchoc_query.
  *   h_keys    host, in, n uint64. Pinned (page-locked) memory lets copies run
  *             asynchronously; pageable memory works but copies synchronously.
  *   h_bitmap  host, out, ceil(n/64) uint64 words.
  * Both calls are ordered on `stream` and return once the work is queued. The
  * caller keeps both buffers alive and unchanged until `stream` completes;
- * the bitmap is complete when it does. The staging (8 slots of up to 2^22
- * keys, 256 MiB at most, fewer keys per slot for small inputs; two slots of
- * one batch if B is larger) is owned by the filter and grows on
- * demand. Growing synchronises the device. Host-buffer calls on one filter
- * share that staging: issue them from one host thread at a time (any
- * streams may be used; the staging events order the slots between them).
+ * the bitmap is complete when it does. The ring is owned by the filter: it
+ * holds up to the tuning's host_ring_keys (default 2^27 keys, 1 GiB, plus
+ * one bitmap word per 64 keys), no more than the largest call needs, and two
+ * chunks at least (two batches if B is larger than a chunk). It grows on
+ * demand and never shrinks; growing synchronises the device. Host-buffer
+ * calls on one filter share that staging: issue them from one host thread at
+ * a time (any streams may be used; per-chunk events order the ring between
+ * them).
  * Errors: EINVAL (NULL filter, NULL buffers with n > 0), ENOMEM, ECUDA.
  */
 int blowchoc_insert_host(blowchoc_filter *f, const uint64_t *h_keys, uint64_t n, void *stream);
@@ -662,6 +666,11 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *   cluster_keys: keys of a batch per CTA that the cluster-resident insert
  *       aims for: a cluster takes more CTAs than the filter needs (up to
  *       cluster_max) while a batch has more keys per CTA (16..2^20).
+ *   host_ring_keys: device staging of blowchoc_insert_host / _query_host,
+ *       in keys at most (0 = 2^27 keys, 1 GiB; else 2^16..2^31 - 1, rounded
+ *       down to a multiple of 64). The ring is sized to the calls (never
+ *       more than they need, never shrinking) and holds at least two chunks,
+ *       so a batch size B above a quarter of it raises it to two batches.
  */
 typedef struct {
     uint32_t lanes_choose;
@@ -676,6 +685,7 @@ typedef struct {
     uint32_t cluster_max;
     uint32_t lanes_cluster;
     uint32_t cluster_keys;
+    uint32_t host_ring_keys;
 } blowchoc_tuning;
 
 /* Read / replace a filter's launch configuration. set_tuning checks every

@@ -48,7 +48,8 @@ class blowchoc_tuning(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
                 ("keys_per_cta", ctypes.c_uint32), ("set_mode", ctypes.c_uint32),
                 ("seq_window", ctypes.c_uint32), ("cluster_max", ctypes.c_uint32),
-                ("lanes_cluster", ctypes.c_uint32), ("cluster_keys", ctypes.c_uint32)]
+                ("lanes_cluster", ctypes.c_uint32), ("cluster_keys", ctypes.c_uint32),
+                ("host_ring_keys", ctypes.c_uint32)]
 
 
 class blowchoc_class_tuning(ctypes.Structure):

@@ -641,6 +641,7 @@ int blowchoc_get_tuning(blowchoc_filter *f, blowchoc_tuning *out) {
     out->cluster_max = (uint32_t)f->cluster_max;
     out->lanes_cluster = (uint32_t)f->lanes_cluster;
     out->cluster_keys = (uint32_t)f->cluster_keys;
+    out->host_ring_keys = f->host_ring_keys;
     return BLOWCHOC_OK;
 }
 
@@ -661,6 +662,8 @@ int bc_check_tuning(const blowchoc_tuning *t) {
     if (t->lanes_cluster != 4 && t->lanes_cluster != 8) return fail(BLOWCHOC_EINVAL, "lanes_cluster must be 4 or 8");
     if (t->cluster_keys < 16 || t->cluster_keys > (1u << 20))
         return fail(BLOWCHOC_EINVAL, "cluster_keys must be in 16..2^20");
+    if (t->host_ring_keys != 0 && (t->host_ring_keys < (1u << 16) || t->host_ring_keys > 0x7FFFFFFFu))
+        return fail(BLOWCHOC_EINVAL, "host_ring_keys must be 0 or in 2^16..2^31-1");
     return BLOWCHOC_OK;
 }
 
@@ -680,6 +683,7 @@ int blowchoc_set_tuning(blowchoc_filter *f, const blowchoc_tuning *t) {
     f->cluster_max = (int)t->cluster_max;
     f->lanes_cluster = (int)t->lanes_cluster;
     f->cluster_keys = (int)t->cluster_keys;
+    f->host_ring_keys = t->host_ring_keys;
     return BLOWCHOC_OK;
 }
 

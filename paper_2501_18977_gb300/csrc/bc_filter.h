@@ -31,6 +31,7 @@ struct blowchoc_filter {
     int cluster_max = 16;          // cluster-resident insert: CTAs per cluster at most (0: off)
     int lanes_cluster = 8;
     int cluster_keys = 128;        // keys of a batch per CTA the cluster size aims for
+    uint32_t host_ring_keys = 0;   // host-buffer staging ring limit in keys (0: the default)
     struct HostStage *host = nullptr;  // host-buffer calls' staging (bc_host.cu), made on first use
 };
 

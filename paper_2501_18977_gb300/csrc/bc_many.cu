@@ -810,6 +810,7 @@ int blowchoc_batch_get_tuning(blowchoc_batch *b, blowchoc_tuning *out) {
     out->cluster_max = (uint32_t)b->cluster_max;
     out->lanes_cluster = (uint32_t)b->lanes_cluster;
     out->cluster_keys = (uint32_t)b->cluster_keys;
+    out->host_ring_keys = 0;
     return BLOWCHOC_OK;
 }
 

@@ -1,6 +1,6 @@
 """Insert and query from host buffers (blowchoc_insert_host /
 blowchoc_query_host) give exactly what the device-buffer calls give: the
-chunked copies through staging slots keep every batch edge, and the bitmap
+chunked copies through the staging ring keep every batch edge, and the bitmap
 layout is the same, for pinned and pageable memory, ragged lengths, batch
 sizes that do not divide the chunk and a batch larger than the chunk. The
 results are also the oracle's."""
@@ -23,9 +23,9 @@ def _host(a, pinned):
 
 @pytest.mark.parametrize("M,k,c,B,n,pinned", [
     (4096, 14, 2, 65536, 1000003, True),      # several chunks of whole batches
-    (3000, 12, 3, 1000, 5000001, True),       # B not dividing 2^22: chunks of 4,194,000 keys
+    (3000, 12, 3, 1000, 5000001, True),       # B not dividing the chunk sizes: 1,048,000 keys first
     (777, 9, 2, 1, 200001, False),            # one key at a time, pageable memory
-    (8192, 16, 3, 5 << 20, 12 << 20, True),   # one batch larger than a chunk
+    (8192, 16, 3, 5 << 20, 12 << 20, True),   # one batch larger than the first chunks
     (100, 7, 1, 64, 63, False),               # fewer keys than a bitmap word
 ])
 def test_host_buffers_equal_device_buffers(M, k, c, B, n, pinned):
@@ -81,17 +81,17 @@ def test_host_calls_reuse_staging_across_calls_and_streams():
 
 
 def test_staging_ring_wraps_within_and_across_calls():
-    """More chunks than staging slots in one call (21 chunks of 2^22 keys),
-    then many alternating small insert and query calls whose staging slots
-    wrap around the ring many times: words and every bitmap equal the device
-    calls'."""
+    """A ring of 2^18 keys (chunks of at most 2^16): one call of 5 M keys
+    wraps it 19 times, then alternating small insert and query calls wrap it
+    again across calls. Words and every bitmap equal the device calls'."""
     import torch
     import paper_2501_18977_gb300 as bc
-    M, k, c, B = 1 << 16, 12, 2, 1 << 20
-    big = workloads.uniform_keys(123, 21 << 22)
+    M, k, c, B = 1 << 16, 12, 2, 1 << 16
+    big = workloads.uniform_keys(123, 5_000_000)
     a = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=9, batch=B)
     b = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=9, batch=B)
     try:
+        a.set_tuning(host_ring_keys=1 << 18)
         s = torch.cuda.current_stream()
         hb = _host(big, True)
         a.insert_host(hb, s)
@@ -121,3 +121,61 @@ def test_staging_ring_wraps_within_and_across_calls():
     finally:
         a.close()
         b.close()
+
+
+def test_more_pending_chunks_than_event_sets():
+    """A ring of 2^16 keys grown by a first call of 60,000 keys, then 300
+    calls of 100 keys (B = 64): about 500 chunks fit in the ring, more than
+    the staging's 64 event sets, so the oldest pending chunks are retired
+    before their space comes round again. Results equal the device calls',
+    on two alternating caller streams."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    M, k, c, B = 1024, 10, 3, 64
+    a = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=4, batch=B)
+    b = bc.Filter(M, k, c, COST_EXP, GOLDEN_RATIO, hash_seed=4, batch=B)
+    try:
+        a.set_tuning(host_ring_keys=1 << 16)
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        first = workloads.uniform_keys(77, 60000)
+        h0 = _host(first, True)
+        a.insert_host(h0, s1)
+        b.insert(to_dev(first))
+        alive, got, want = [h0], [], []
+        for j in range(300):
+            st, other = (s1, s2) if j % 2 == 0 else (s2, s1)
+            st.wait_stream(other)   # the caller orders its streams; the staging orders the ring
+            ks = workloads.uniform_keys(5000 + j, 100)
+            hk = _host(ks, True)
+            alive.append(hk)
+            a.insert_host(hk, st)
+            b.insert(to_dev(ks))
+            if j % 10 == 9:
+                qs = workloads.uniform_keys(9000 + j, 100)
+                hq = _host(qs, True)
+                alive.append(hq)
+                got.append(a.query_host(hq, stream=st))
+                want.append(b.query(to_dev(qs)).cpu().numpy().view(np.uint64))
+        torch.cuda.synchronize()
+        assert np.array_equal(a.words_host(), b.words_host())
+        for g, w in zip(got, want):
+            assert np.array_equal(g[: len(w)], w)
+        sa, sb = a.stats(), b.stats()
+        assert (sa.inserted, sa.skipped) == (sb.inserted, sb.skipped)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_host_ring_keys_is_checked():
+    import paper_2501_18977_gb300 as bc
+    f = bc.Filter(256, 8, 2, COST_EXP, GOLDEN_RATIO, hash_seed=1, batch=64)
+    try:
+        for bad in (1, 1000, (1 << 16) - 1, 1 << 31):
+            with pytest.raises(Exception):
+                f.set_tuning(host_ring_keys=bad)
+        f.set_tuning(host_ring_keys=(1 << 16) + 5)
+        assert f.tuning().host_ring_keys == (1 << 16) + 5
+        f.set_tuning(host_ring_keys=0)
+    finally:
+        f.close()
