@@ -179,6 +179,17 @@ class ClockSampler:
 _WORKLOAD_CLOCKS = None
 
 
+def finite(obj):
+    """obj with every non-finite float replaced by None (strict JSON has no NaN)."""
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: finite(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [finite(v) for v in obj]
+    return obj
+
+
 def emit(record):
     """Print one workload JSON line with the clocks sampled since the last one."""
     global _WORKLOAD_CLOCKS
@@ -186,7 +197,16 @@ def emit(record):
         record = dict(record, clocks=_WORKLOAD_CLOCKS.stop())
         _WORKLOAD_CLOCKS = ClockSampler(_WORKLOAD_CLOCKS.index)
         _WORKLOAD_CLOCKS.start()
-    print(json.dumps(record), flush=True)
+    print(json.dumps(finite(record), allow_nan=False), flush=True)
+
+
+def ratio(a, b, nd=4):
+    """round(a / b, nd), or None where b was not measured."""
+    return None if b is None or not b else round(a / b, nd)
+
+
+def rounded(v, nd):
+    return None if v is None else round(v, nd)
 
 
 def peaks():
@@ -907,7 +927,7 @@ def run_reference(args):
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 4), "unit": "Mkeys/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
+    print(json.dumps(finite(out), allow_nan=False))
 
 
 def run_cluster(args):
@@ -1370,7 +1390,7 @@ def run_main(args):
     dom_gbs = q_gbs if dominant == "query_kernel" else i_gbs
     traffic = ncu_traffic(dominant, f.tuning())
     if args.no_extra_records:
-        ceil_filter, ceil_filter_cfg, ceil_hbm, hbm = float("nan"), (None, None, None), float("nan"), None
+        ceil_filter, ceil_filter_cfg, ceil_hbm, hbm = None, (None, None, None), None, None
     else:
         ceil_filter, ceil_filter_cfg = gather_ceiling(bc, torch, CONFIG["nblocks"])
         ceil_hbm, _ = gather_ceiling(bc, torch, 1 << 26)
@@ -1395,25 +1415,25 @@ def run_main(args):
                      "residency": ("L2-assisted: the 128 MiB filter is about L2's size, so part of "
                                    "its block reads hit L2; see hbm_resident for a filter four "
                                    "times L2"),
-                     "frac_of_gather_ceiling": round(dom_gbs / ceil_filter, 4),
-                     "gather_ceiling_gbs": {"filter_footprint_128MiB": round(ceil_filter, 1),
+                     "frac_of_gather_ceiling": ratio(dom_gbs, ceil_filter),
+                     "gather_ceiling_gbs": {"filter_footprint_128MiB": rounded(ceil_filter, 1),
                                             "filter_footprint_config": {
                                                 "lanes": ceil_filter_cfg[0],
                                                 "ctas_per_sm": ceil_filter_cfg[1],
                                                 "inflight": ceil_filter_cfg[2]},
-                                            "hbm_4GiB": round(ceil_hbm, 1)}},
+                                            "hbm_4GiB": rounded(ceil_hbm, 1)}},
         "hbm_resident": hbm,
         "roofline_other": {"insert_gbs": round(i_gbs, 1), "insert_frac": round(i_gbs / peak, 4),
                            "query_gbs": round(q_gbs, 1), "query_frac": round(q_gbs / peak, 4),
-                           "insert_frac_of_gather_ceiling": round(i_gbs / ceil_filter, 4),
-                           "query_frac_of_gather_ceiling": round(q_gbs / ceil_filter, 4)},
+                           "insert_frac_of_gather_ceiling": ratio(i_gbs, ceil_filter),
+                           "query_frac_of_gather_ceiling": ratio(q_gbs, ceil_filter)},
         "skip_rate": round(skip_rate, 6), "inserted": st.inserted, "skipped": st.skipped,
         "query_hits": hits, "fpr_est": st.fpr_est,
         "gpu_launches": int(launches),
         "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
     }
     f.close()
-    print(json.dumps(out))
+    print(json.dumps(finite(out), allow_nan=False))
     if world > 1:
         dist.destroy_process_group()
 

@@ -75,3 +75,19 @@ def test_committed_record_matches_the_guard():
         assert entry["dram_bytes_per_launch"] > 0
         for field in entry["launch"]:
             assert hasattr(blowchoc_tuning(), field)
+
+
+def test_bench_lines_are_strict_json():
+    """A measurement that was not taken (a gather ceiling skipped by
+    --no-extra-records) is printed as null, never as NaN or Infinity."""
+    import json
+    import bench
+    rec = {"frac_of_gather_ceiling": bench.ratio(3519.4, None),
+           "gather_ceiling_gbs": {"filter_footprint_128MiB": bench.rounded(None, 1), "hbm_4GiB": float("nan")},
+           "list": [1.5, float("inf"), -float("inf")], "ok": 0.52}
+    text = json.dumps(bench.finite(rec), allow_nan=False)
+    back = json.loads(text)
+    assert back["frac_of_gather_ceiling"] is None
+    assert back["gather_ceiling_gbs"] == {"filter_footprint_128MiB": None, "hbm_4GiB": None}
+    assert back["list"] == [1.5, None, None] and back["ok"] == 0.52
+    assert bench.ratio(3519.4, 8300.0) == round(3519.4 / 8300.0, 4)
