@@ -1383,7 +1383,7 @@ def run_main(args):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(keys, queries, 300_000, 600_000)
+        cpu = cpu_baseline(keys, queries, 800_000, 1_600_000)
 
     dominant = "query_kernel" if qry_ms >= ins_ms else "persistent_insert_kernel"
     dom_ms = qry_ms if dominant == "query_kernel" else ins_ms
