@@ -133,7 +133,10 @@ class ClockSampler:
         ClockSampler.count += 1  # unique file per sampler: several may run at once
         self.path = os.path.join("/tmp", "bc_clocks_%d_%d_%d.csv" % (os.getpid(), index, ClockSampler.count))
 
-    def start(self):
+    def start(self, settle_s=0.0):
+        """Starts sampling; with settle_s > 0, waits (up to settle_s) until the
+        first sample is written, so that nvidia-smi's start-up, which takes
+        the driver's locks, is over before the caller's timed work begins."""
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -142,6 +145,13 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while settle_s > 0 and time.perf_counter() - t0 < settle_s and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                time.sleep(0.1)  # a second sample's worth, for the process to settle
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -1281,13 +1291,16 @@ def run_main(args):
             ev.append(e)
         return st
 
+    # the sampler starts before the warm-up and stops after the last timed
+    # region: its start-up and shutdown take the driver's locks and once
+    # stalled a timed step by about 200 ms
+    clocks = ClockSampler(local)
+    clocks.start(settle_s=5.0)
     for _ in range(args.warmup):
         st = step(False)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     launches0 = bc.blowchoc_launch_count()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -1298,7 +1311,6 @@ def run_main(args):
     torch.cuda.synchronize()
     barrier()
     launches = bc.blowchoc_launch_count() - launches0
-    clk = clocks.stop()
     ms = max_over_ranks(t_start.elapsed_time(t_end) / args.steps, world, "cuda")
     value = job_mkeys_per_s(n_ins + n_q, world, ms)
 
@@ -1374,6 +1386,7 @@ def run_main(args):
                "frac_of_copy_floor": round(h2d_ms / ems, 4),
                "copy_floor_note": "pinned host-to-device copy of the step's 1.2 GB of keys alone (best of 3); "
                                   "the step cannot end before it"}
+    clk = clocks.stop()
 
     if rank != 0:
         f.close()

@@ -170,14 +170,23 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
 // whole launch (zeroed before it); the barrier completes when it reaches
 // `target`. A wait past kBarrierCycles, or an error word already set by
 // another CTA, sets *err and returns false; the caller then leaves.
+//
+// Each CTA's first thread arrives with one release reduction (no value
+// returned, so it starts polling at once) after a CTA barrier, which makes
+// every write of the CTA part of that release; the acquiring load that sees
+// the count complete then synchronises with every CTA's arrival, and the
+// closing CTA barrier passes that on to the CTA's other threads. On the DNA
+// insert (96 barriers) this took 3.679 ms against 3.716 ms for a full fence
+// before a returning atomic add and after the wait; a last-arriver flag on a
+// line of its own (3.772 ms) and a two-level arrival tree (3.831 ms) were
+// slower, each adding a hop to the release.
 __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int target,
                                              unsigned long long *err, long long limit = kBarrierCycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        atomicAdd(bar, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         const long long t0 = clock64();
         while (ld_acquire(bar) < target) {
             if (*reinterpret_cast<volatile unsigned long long *>(err) != 0ull ||
@@ -188,7 +197,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int tar
             }
             __nanosleep(100);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
