@@ -1273,6 +1273,12 @@ def run_main(args):
                   hash_seed=CONFIG["hash_seed"], batch=CONFIG["batch"], stream=stream)
 
     ev = []
+    # Each step's statistics are queued into a pinned buffer (two, alternating)
+    # with no host wait, so the host queues the timed steps ahead of the GPU:
+    # the machine's host side pauses now and then for tens of milliseconds (seen
+    # about every 0.5 s), which a per-step host wait turned into idle GPU time.
+    raws = [torch.zeros(bc.STATS_RAW_WORDS, dtype=torch.int64).pin_memory() for _ in range(2)]
+    nstep = [0]
 
     def step(record):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
@@ -1285,11 +1291,12 @@ def run_main(args):
         f.query(dq, bitmap, stream)
         if record:
             e[2].record(stream)
-        st = f.stats()
+        raw = f.stats_async(raws[nstep[0] % 2], stream)
+        nstep[0] += 1
         if record:
             e[3].record(stream)
             ev.append(e)
-        return st
+        return raw
 
     # the sampler starts before the warm-up and stops after the last timed
     # region: its start-up and shutdown take the driver's locks and once
@@ -1297,7 +1304,7 @@ def run_main(args):
     clocks = ClockSampler(local)
     clocks.start(settle_s=5.0)
     for _ in range(args.warmup):
-        st = step(False)
+        step(False)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -1306,9 +1313,10 @@ def run_main(args):
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for _ in range(args.steps):
-        st = step(True)
+        raw = step(True)
     t_end.record(stream)
     torch.cuda.synchronize()
+    st = f.stats_decode(raw)
     barrier()
     launches = bc.blowchoc_launch_count() - launches0
     ms = max_over_ranks(t_start.elapsed_time(t_end) / args.steps, world, "cuda")
@@ -1339,11 +1347,14 @@ def run_main(args):
 
         def e2e_step():
             # the library's host-buffer calls: keys copied in chunks that
-            # overlap the previous chunk's kernels, bitmap copied back
+            # overlap the previous chunk's kernels, bitmap and statistics
+            # copied back; the host waits once, after the last timed step
             f.clear(stream)
             f.insert_host(h_keys, stream)
             f.query_host(h_q, h_bm_np, stream)
-            f.stats()
+            raw = f.stats_async(raws[nstep[0] % 2], stream)
+            nstep[0] += 1
+            return raw
 
         for _ in range(max(1, args.warmup)):
             e2e_step()
@@ -1355,10 +1366,11 @@ def run_main(args):
         a.record(stream)
         marks[0].record(stream)
         for i in range(args.steps):
-            e2e_step()
+            raw_e = e2e_step()
             marks[i + 1].record(stream)
         b.record(stream)
         torch.cuda.synchronize()
+        st_e = f.stats_decode(raw_e)
         barrier()
         ems = max_over_ranks(a.elapsed_time(b) / args.steps, world, "cuda")
         per_step = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
@@ -1375,12 +1387,12 @@ def run_main(args):
             t = a.elapsed_time(b)
             h2d_ms = t if h2d_ms is None else min(h2d_ms, t)
         e2e = {"value": round(job_mkeys_per_s(n_ins + n_q, world, ems), 3), "unit": "Mkeys/s",
-               "h2d_bytes_per_step": int(8 * (n_ins + n_q)), "d2h_bytes_per_step": int(8 * nwords),
+               "h2d_bytes_per_step": int(8 * (n_ins + n_q)), "d2h_bytes_per_step": int(8 * nwords + 8 * bc.STATS_RAW_WORDS),
                "ms_per_step": round(ems, 3),
                "ms_per_step_min_median_max": [round(per_step[0], 3), round(statistics.median(per_step), 3),
                                               round(per_step[-1], 3)],
-               "api": "blowchoc_insert_host + blowchoc_query_host (pinned)",
-               "query_hits": hits,
+               "api": "blowchoc_insert_host + blowchoc_query_host (pinned) + blowchoc_stats_async",
+               "query_hits": hits, "inserted": st_e.inserted, "skipped": st_e.skipped,
                "h2d_gbs": round(8 * (n_ins + n_q) / (h2d_ms / 1e3) / 1e9, 1),
                "copy_floor_ms": round(h2d_ms, 3),
                "frac_of_copy_floor": round(h2d_ms / ems, 4),

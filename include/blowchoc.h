@@ -21,8 +21,9 @@
  *    needs one fails with BLOWCHOC_ECUDA. The host-only calls
  *    (blowchoc_cost_ranks, blowchoc_fpr_estimate,
  *    blowchoc_derive_multipliers, blowchoc_shard_layout,
- *    blowchoc_shard_partition_scratch) compute host-side preparation and
- *    statistics only; no insert or query runs without a device.
+ *    blowchoc_shard_partition_scratch, and blowchoc_stats_decode of an
+ *    existing filter) compute host-side preparation and statistics only; no
+ *    insert or query runs without a device.
  */
 #ifndef BLOWCHOC_H
 #define BLOWCHOC_H
@@ -205,6 +206,24 @@ int blowchoc_query(blowchoc_filter *f, const uint64_t *d_keys, uint64_t n,
  * device wait of this filter gave up; its result is not trustworthy).
  */
 int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out);
+
+/*
+ * blowchoc_stats_async / blowchoc_stats_decode -- the same statistics without
+ * a host wait, for pipelined callers. stats_async recomputes the histogram
+ * on `stream` and copies the filter's raw counters to h_raw
+ * (BLOWCHOC_STATS_RAW_WORDS uint64: [0] inserted, [1] skipped, [2] error
+ * word, [3 + L] blocks of load L for L = 0..512) on the same stream; it
+ * returns once the work is queued. With pinned h_raw the copy is
+ * asynchronous; the caller keeps h_raw alive until `stream` completes. The
+ * histogram scratch belongs to the filter: order its stats calls (one stream,
+ * or streams the caller orders). stats_decode is host-only: it fills `out`
+ * from a completed h_raw exactly as blowchoc_stats does.
+ * Errors: EINVAL (NULL pointers), ECUDA; decode: ETIMEOUT when the error
+ * word is set (an earlier bounded device wait of this filter gave up).
+ */
+#define BLOWCHOC_STATS_RAW_WORDS 516
+int blowchoc_stats_async(blowchoc_filter *f, uint64_t *h_raw, void *stream);
+int blowchoc_stats_decode(const blowchoc_filter *f, const uint64_t *h_raw, blowchoc_filter_stats *out);
 
 /*
  * blowchoc_destroy -- synchronise the home stream and free the filter's

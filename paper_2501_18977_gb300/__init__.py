@@ -9,7 +9,8 @@ from .binding import (  # noqa: F401
     BLOWCHOC_EBUDGET, COST_MIX, COST_LA, COST_EXP, BlowChocError, Filter,
     blowchoc_params, blowchoc_filter_stats, blowchoc_create, blowchoc_insert,
     blowchoc_insert_noalloc, blowchoc_query,
-    blowchoc_stats, blowchoc_destroy, blowchoc_words, blowchoc_multipliers,
+    blowchoc_stats, blowchoc_stats_async, blowchoc_stats_decode, STATS_RAW_WORDS,
+    blowchoc_destroy, blowchoc_words, blowchoc_multipliers,
     blowchoc_read_words, blowchoc_write_words, blowchoc_clear, blowchoc_set_cost_table, blowchoc_cost_ranks,
     blowchoc_fpr_estimate, blowchoc_derive_multipliers,
     blowchoc_cluster_ctas,

