@@ -123,7 +123,7 @@ class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     count = 0
 
@@ -162,7 +162,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], None, set()
+        sm, busy, smax, reasons = [], [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
             for line in fh:
@@ -174,14 +174,22 @@ class ClockSampler:
                     smax = float(parts[2])
                 except ValueError:
                     continue
+                try:  # samples with the GPU busy (utilization over the last interval)
+                    if len(parts) > 9 and float(parts[9]) >= 50.0:
+                        busy.append(sm[-1])
+                except ValueError:
+                    pass
                 for nm, v in zip(names, parts[5:9]):
                     if v.lower() == "active":
                         reasons.add(nm)
         os.unlink(self.path)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        # the median under load: over the samples with the GPU busy, when there
+        # are any (a short workload leaves most samples idle, at idle clocks)
+        return {"sm_mhz": statistics.median(busy) if busy else statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_busy": len(busy),
+                "sm_mhz_all_samples": statistics.median(sm)}
 
 
 # Clock record of a --workload run: every JSON line a workload prints carries
@@ -409,6 +417,18 @@ def run_many(args):
         classes[["cache", "l2", "spill", "hbm"][key[0]]] = dict(
             t, tuned=bool(is_set), filters=len(members), keys=int(sum(it["n"] for it in members)))
     st = [f.stats() for f in filters]
+    # algorithmic bytes of the job (c = 2): insert 8 + 128 + 64 (1 - skip
+    # rate) per key; queries half members (at least one block, 8 + 64 + 1/8)
+    # and half random (8 + 128 + 1/8); against random whole blocks over the
+    # filters' combined footprint (the gather probe)
+    ins_done = sum(x.inserted for x in st)
+    skip_rate = sum(x.skipped for x in st) / max(1, ins_done + sum(x.skipped for x in st))
+    alg_bytes = n_ins * (8 + 128 + 64 * (1 - skip_rate)) + (n_q / 2) * (8 + 64 + 0.125) + (n_q / 2) * (8 + 128 + 0.125)
+    total_blocks = int(sum(it["M"] for it in cfg))
+    ceil, ceil_cfg = gather_ceiling(bc, torch, total_blocks)
+    for r in results.values():
+        r["gbs_lower_bound"] = round(alg_bytes / (r["ms"] / 1e3) / 1e9, 1)
+        r["frac_of_gather_ceiling"] = ratio(alg_bytes / (r["ms"] / 1e3) / 1e9, ceil)
     out = {"workload": "many_filters_256", "metric": "insert+query throughput, 256 filters",
            "unit": "Mkeys/s", "n_insert": n_ins, "n_query": n_q,
            "filters": len(cfg), "filter_mib": round(sum(it["M"] for it in cfg) * 64 / 2**20, 1),
@@ -422,6 +442,9 @@ def run_many(args):
                          "query_early": best.query_early, "ctas_per_sm": best.ctas_per_sm,
                          "classes": classes},
            "repeats": reps, "clocks": clk,
+           "gather_ceiling_gbs": round(ceil, 1),
+           "gather_ceiling_config": {"lanes": ceil_cfg[0], "ctas_per_sm": ceil_cfg[1], "inflight": ceil_cfg[2]},
+           "bytes_note": "algorithmic bytes with members' queries at one block each (a lower bound)",
            "timing": "CUDA events per repetition (median, min, max), filters cleared before each"}
     default_batch.close()
     batch.close()
@@ -665,6 +688,10 @@ def run_small(args):
     dq = torch.from_numpy(np.concatenate([keys, neg]).view(np.int64)).cuda()
     bm = torch.empty((dq.numel() + 63) // 64, dtype=torch.int64, device="cuda")
     s = torch.cuda.current_stream()
+    # the ceiling beside the peak for this L2-resident filter: random whole
+    # 64-byte blocks over the same 2 MiB footprint (the gather probe)
+    ceil, ceil_cfg = gather_ceiling(bc, torch, 32768)
+    peak, peak_src = peaks()
     rows = []
     for B in (65536, 1):
         f = bc.Filter(32768, 14, 2, bc.COST_MIX, 50.0, hash_seed=1, batch=B)
@@ -685,7 +712,14 @@ def run_small(args):
         h = bm.cpu().numpy().view(np.uint8)
         bits = np.unpackbits(h, bitorder="little")[: dq.numel()]
         st = f.stats()
+        skip = st.skipped / max(1, st.inserted + st.skipped)
+        # algorithmic bytes: insert 8 + 64 c + 64 (1 - skip rate) per key; query
+        # negatives 8 + 64 c + 1/8, members at least 8 + 64 + 1/8 (first block)
+        i_gbs = 1e6 * (8 + 128 + 64 * (1 - skip)) / (statistics.median(ti) / 1e3) / 1e9
+        q_gbs = (1e6 * (8 + 128 + 0.125) + 1e6 * (8 + 64 + 0.125)) / (statistics.median(tq) / 1e3) / 1e9
         rows.append({"B": B, "insert_ms": round(statistics.median(ti), 4),
+                     "insert_gbs": round(i_gbs, 1), "insert_frac_of_l2_gather_ceiling": ratio(i_gbs, ceil),
+                     "query_gbs_lower_bound": round(q_gbs, 1), "query_frac_of_l2_gather_ceiling": ratio(q_gbs, ceil),
                      "insert_mkeys_s": round(1e6 / (statistics.median(ti) / 1e3) / 1e6, 1),
                      "query_ms": round(statistics.median(tq), 4),
                      "query_mkeys_s": round(2e6 / (statistics.median(tq) / 1e3) / 1e6, 1),
@@ -694,7 +728,13 @@ def run_small(args):
                      "inserted": st.inserted, "skipped": st.skipped})
         f.close()
     emit({"workload": "small_uniform", "M": 32768, "k": 14, "c": 2, "cost": "MIX 50",
-          "timing": "CUDA events, median of at least 5 repeats after one warm-up", "rows": rows})
+          "timing": "CUDA events, median of at least 5 repeats after one warm-up",
+          "l2_gather_ceiling_gbs": round(ceil, 1),
+          "l2_gather_ceiling_config": {"lanes": ceil_cfg[0], "ctas_per_sm": ceil_cfg[1], "inflight": ceil_cfg[2]},
+          "hbm_copy_peak_gbs": peak, "peak_source": peak_src,
+          "bytes_note": "members' query bytes counted at one block each (a lower bound: the first "
+                        "candidate that holds a member is not counted here)",
+          "rows": rows})
 
 
 def run_learn(args):

@@ -91,3 +91,28 @@ def test_bench_lines_are_strict_json():
     assert back["gather_ceiling_gbs"] == {"filter_footprint_128MiB": None, "hbm_4GiB": None}
     assert back["list"] == [1.5, None, None] and back["ok"] == 0.52
     assert bench.ratio(3519.4, 8300.0) == round(3519.4 / 8300.0, 4)
+
+
+def test_clock_record_is_the_median_under_load():
+    """The clock record's sm_mhz is the median over samples with the GPU busy
+    (utilization >= 50%); idle samples at idle clocks do not pull it down.
+    Throttle reasons are collected from every sample."""
+    import bench
+
+    class Done:  # a finished sampler process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.ClockSampler(0)
+    with open(c.path, "w") as fh:
+        fh.write("0, 120, 2070, 150.1, 0x0, Not Active, Not Active, Not Active, Not Active, 0\n" * 5)
+        fh.write("0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Active, 97\n" * 3)
+        fh.write("garbage line\n")
+    c.proc, c.fh = Done(), open(os.devnull, "w")
+    rec = c.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_mhz_all_samples"] == 120.0
+    assert (rec["samples"], rec["samples_busy"]) == (8, 3)
+    assert rec["reasons"] == ["sw_power_cap"] and rec["sm_max_mhz"] == 2070.0
