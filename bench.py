@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["dna", "gather", "many", "serve", "sweep", "batching", "small",
                                            "learn", "fig4", "fig8", "fig10", "cluster", "lanes", "variants",
-                                           "hbm"],
+                                           "hbm", "shard"],
                     default="dna")
     ap.add_argument("--keys", type=float, default=2e9, help="fig4/fig8/fig10: keys inserted and negatives")
     ap.add_argument("--ks", type=str, default="4,7,10,14,17,20", help="fig4/fig10: k values")
@@ -324,6 +324,102 @@ def run_gather(args):
                     "inflight": inf})
     emit({"workload": "gather_ceiling", "unit": "GB/s of whole 64-byte blocks",
                       "reads": 100_000_000, "results": out})
+
+
+def run_shard(args):
+    """Sub-arrays (Sec. 3.4) on one GPU: the DNA 31-mer filter split into T
+    sub-arrays of M / T blocks. Per T: the partition of the 49,999,970 insert
+    keys by h_0 and the unpermute of the 99,999,940 query answers, each as
+    GB/s of algorithmic bytes against the copy peak (partition: one read of
+    each key, one write of the key and of its index, 24 B; unpermute: the
+    index, 8 B, plus a bit read and a bit written); and the whole split insert
+    and query (partition, T sub-array calls, unpermute) against the unsplit
+    filter. At T = 1 the split filter's words must equal the unsplit one's."""
+    import torch
+    import paper_2501_18977_gb300 as bc
+    from paper_2501_18977_gb300.sharded import ShardedFilter
+    keys, queries = make_workload()
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dq = torch.from_numpy(queries.view(np.int64)).cuda()
+    n, nq = dk.numel(), dq.numel()
+    s = torch.cuda.current_stream()
+    peak, peak_src = peaks()
+    reps = max(5, args.steps)
+
+    def timed(fn):
+        ts = []
+        for r in range(reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    plain = bc.Filter(CONFIG["nblocks"], CONFIG["k"], CONFIG["choices"], bc.COST_LA, CONFIG["mu"],
+                      hash_seed=CONFIG["hash_seed"], batch=CONFIG["batch"])
+    bm = torch.empty((nq + 63) // 64, dtype=torch.int64, device="cuda")
+
+    def plain_insert():
+        plain.clear(s)
+        plain.insert(dk, s)
+
+    t_plain_ins = timed(plain_insert)
+    t_plain_q = timed(lambda: plain.query(dq, bm, s))
+    plain_words = plain.words_host()
+    plain_bits = bm.cpu().numpy().copy()
+    plain.close()
+    rows = []
+    for T in (1, 2, 4, 8):
+        sf = ShardedFilter(CONFIG["nblocks"], T, CONFIG["k"], CONFIG["choices"], bc.COST_LA, CONFIG["mu"],
+                           hash_seed=CONFIG["hash_seed"], batch=CONFIG["batch"])
+        out_k = torch.empty_like(dk)
+        out_i = torch.empty(n, dtype=torch.int64, device="cuda")
+        offs = torch.empty(T + 1, dtype=torch.int64, device="cuda")
+        sw = bc.blowchoc_shard_partition_scratch(n, T)
+        scratch = torch.empty(max(sw, 1), dtype=torch.int64, device="cuda")
+        t_part = timed(lambda: bc.blowchoc_shard_partition(dk, n, T, sf.a0, out_k, out_i, offs, scratch, sw, s))
+
+        def split_insert():
+            for f in sf.subs.values():
+                f.clear(s)
+            sf.insert(dk, s)
+
+        t_ins = timed(split_insert)
+        t_q = timed(lambda: sf.query(dq, bm, s))
+        # the unpermute alone, on the last query's partition of the queries
+        part, index, offsets, off = sf.partition(dq, s)
+        wc = [(off[t + 1] - off[t] + 63) // 64 for t in range(T)]
+        seg = torch.zeros(max(sum(wc), 1), dtype=torch.int64, device="cuda")
+        t_unp = timed(lambda: bc.blowchoc_shard_unpermute(seg, offsets, index, nq, T, bm, s))
+        sf.query(dq, bm, s)
+        torch.cuda.synchronize()
+        bits = bm.cpu().numpy()
+        st = [f.stats() for f in sf.subs.values()]
+        row = {"T": T, "sub_blocks": sf.Ms,
+               "partition_ms": round(t_part, 4), "partition_gbs": round(24 * n / (t_part / 1e3) / 1e9, 1),
+               "partition_frac_of_peak": ratio(24 * n / (t_part / 1e3) / 1e9, peak),
+               "unpermute_ms": round(t_unp, 4), "unpermute_gbs": round((8 + 0.25) * nq / (t_unp / 1e3) / 1e9, 1),
+               "unpermute_frac_of_peak": ratio((8 + 0.25) * nq / (t_unp / 1e3) / 1e9, peak),
+               "insert_ms": round(t_ins, 4), "query_ms": round(t_q, 4),
+               "insert_vs_unsplit": round(t_plain_ins / t_ins, 3), "query_vs_unsplit": round(t_plain_q / t_q, 3),
+               "inserted": int(sum(x.inserted for x in st)), "skipped": int(sum(x.skipped for x in st)),
+               "hits": int(np.unpackbits(bits.view(np.uint8), bitorder="little")[:nq].sum())}
+        if T == 1:
+            row["equal_to_unsplit"] = bool(np.array_equal(sf.words_host(), plain_words) and
+                                           np.array_equal(bits, plain_bits))
+        rows.append(row)
+        sf.close()
+        del out_k, out_i, scratch, seg
+        torch.cuda.empty_cache()
+    emit({"workload": "sub_arrays_one_gpu", "filter": "DNA 31-mer (M = 2^21, k = 16, c = 3, cost^LA, B = 2^20)",
+          "n_insert": n, "n_query": nq, "unsplit_insert_ms": round(t_plain_ins, 4),
+          "unsplit_query_ms": round(t_plain_q, 4), "peak_gbs": peak, "peak_source": peak_src,
+          "timing": "CUDA events, median of %d after one warm-up; split calls include the host reading "
+                    "the partition's offsets" % reps, "rows": rows})
 
 
 def run_many(args):
@@ -1273,6 +1369,9 @@ def run_main(args):
         return
     if args.workload == "many":
         run_many(args)
+        return
+    if args.workload == "shard":
+        run_shard(args)
         return
     if args.workload == "serve":
         run_serve(args)
