@@ -116,3 +116,40 @@ def test_clock_record_is_the_median_under_load():
     assert rec["sm_mhz"] == 2070.0 and rec["sm_mhz_all_samples"] == 120.0
     assert (rec["samples"], rec["samples_busy"]) == (8, 3)
     assert rec["reasons"] == ["sw_power_cap"] and rec["sm_max_mhz"] == 2070.0
+
+
+def _run_bench(args, env_extra=None, timeout=300):
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, cwd=root, env=env,
+                          capture_output=True, text=True, timeout=timeout)
+
+
+def test_reference_arm_prints_one_strict_json_line():
+    """The reference arm (the oracle on the host, a bounded sample per step)
+    prints exactly one JSON line with the benchmark's metric and unit, its
+    own cpu_baseline and e2e blocks, and no NaN."""
+    r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0], parse_constant=lambda c: (_ for _ in ()).throw(ValueError(c)))
+    assert d["impl"] == "reference" and d["unit"] == "Mkeys/s" and d["higher_is_better"] is True
+    assert d["metric"] == "insert+query throughput (DNA 31-mers, c=3, k=16, cost^LA)"
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": "Mkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "dna_kmer_31_c3_la"
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm; another rank exits
+    0 at once and prints nothing."""
+    r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1", "--gpus", "2"],
+                   env_extra={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
