@@ -202,16 +202,20 @@ __host__ __device__ inline size_t bulk_ring_offset(int C, uint32_t k) {
     return ((C > 1 ? 513u * (k + 1) * 2u : 0u) + 127u) & ~(size_t)127;
 }
 
-// BITSEL: the filter uses distinct bit selection. Random-selection filters
-// take the false instance, where the distinct code is compiled out: inlined
-// into the same kernel it cost registers (the DNA insert spilled 72 bytes
-// against none) and the random-bit insert measured 2% faster without it.
-template <int C, int LANES, bool BULK, bool BITSEL>
+// BITSEL: the filter uses distinct bit selection; POW2: its block count is a
+// power of two (block addresses are the top bits of a x). Each false instance
+// compiles the other paths out: inlined as runtime branches they cost
+// registers (the DNA insert spilled 72 bytes with the distinct path, none
+// without) and time (DNA insert 3.70 -> 3.67 ms without the distinct path,
+// -> 3.63 ms with the power-of-two addressing alone).
+template <int C, int LANES, bool BULK, bool BITSEL, bool POW2>
 __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ctas<LANES>()) persistent_insert_kernel(
     DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
     const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters,
     unsigned int *bar) {
-    if constexpr (!BITSEL) f.bitsel = 0;  // a constant from here on: the distinct paths fold away
+    // constants from here on: the paths this instance does not take fold away
+    if constexpr (!BITSEL) f.bitsel = 0;
+    if constexpr (POW2) f.range_kind = kRangePow2;
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
     extern __shared__ __align__(16) uint8_t s_dyn[];  // rank table | bulk slot ring (16-byte aligned slots)
@@ -730,15 +734,15 @@ cudaError_t small_dispatch(const Launch &L, const DevFilter &f, const uint64_t *
     }
 }
 
-template <int C, int LANES, bool BULK, bool BITSEL>
+template <int C, int LANES, bool BULK, bool BITSEL, bool POW2>
 cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                               uint64_t B, const uint16_t *rank, uint8_t *sel,
                               unsigned long long *counters, unsigned int *bar, int sms) {
     const size_t sm = BULK ? bulk_ring_offset(C, f.k) + bulk_ring_bytes<LANES>() : rank_bytes(C, f.k);
-    cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES, BULK, BITSEL>, sm);
+    cudaError_t e = allow_smem(persistent_insert_kernel<C, LANES, BULK, BITSEL, POW2>, sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES, BULK, BITSEL>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_insert_kernel<C, LANES, BULK, BITSEL, POW2>,
                                                       persistent_threads<LANES>(), sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -748,24 +752,31 @@ cudaError_t persistent_launch(const Launch &L, const DevFilter &f, const uint64_
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&f, (void *)&keys, (void *)&n, (void *)&B, (void *)&rank,
                     (void *)&sel, (void *)&counters, (void *)&bar};
-    return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES, BULK, BITSEL>, dim3(grid),
+    return cudaLaunchCooperativeKernel((const void *)persistent_insert_kernel<C, LANES, BULK, BITSEL, POW2>, dim3(grid),
                                        dim3(persistent_threads<LANES>()), args, sm, L.stream);
+}
+
+// The instance for the filter's bit selection and block range (distinct
+// selection always takes the general addressing).
+template <int C, int LANES, bool BULK>
+cudaError_t persistent_variant(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
+                               uint64_t B, const uint16_t *rank, uint8_t *sel,
+                               unsigned long long *counters, unsigned int *bar, int sms) {
+    if (f.bitsel) return persistent_launch<C, LANES, BULK, true, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+    if (f.range_kind == kRangePow2)
+        return persistent_launch<C, LANES, BULK, false, true>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+    return persistent_launch<C, LANES, BULK, false, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
 }
 
 template <int C, bool BULK>
 cudaError_t persistent_dispatch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n,
                                 uint64_t B, const uint16_t *rank, uint8_t *sel,
                                 unsigned long long *counters, unsigned int *bar, int sms) {
-    const bool d = f.bitsel != 0;
     switch (L.lanes) {
-        case 1: return d ? persistent_launch<C, 1, BULK, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
-                         : persistent_launch<C, 1, BULK, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 2: return d ? persistent_launch<C, 2, BULK, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
-                         : persistent_launch<C, 2, BULK, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 4: return d ? persistent_launch<C, 4, BULK, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
-                         : persistent_launch<C, 4, BULK, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
-        case 8: return d ? persistent_launch<C, 8, BULK, true>(L, f, keys, n, B, rank, sel, counters, bar, sms)
-                         : persistent_launch<C, 8, BULK, false>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 1: return persistent_variant<C, 1, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 2: return persistent_variant<C, 2, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 4: return persistent_variant<C, 4, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
+        case 8: return persistent_variant<C, 8, BULK>(L, f, keys, n, B, rank, sel, counters, bar, sms);
         default: return cudaErrorInvalidValue;
     }
 }
