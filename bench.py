@@ -185,9 +185,10 @@ class ClockSampler:
         os.unlink(self.path)
         if not sm:
             return None
-        # the median under load: over the samples with the GPU busy, when there
-        # are any (a short workload leaves most samples idle, at idle clocks)
-        return {"sm_mhz": statistics.median(busy) if busy else statistics.median(sm), "sm_max_mhz": smax,
+        # the median under load: over the samples with the GPU busy; a workload
+        # too short for any sample to see it busy reports the highest clock seen
+        return {"sm_mhz": statistics.median(busy) if busy else max(sm), "sm_max_mhz": smax,
+                "sm_mhz_basis": "median of busy samples" if busy else "highest sample (no busy sample)",
                 "reasons": sorted(reasons), "samples": len(sm), "samples_busy": len(busy),
                 "sm_mhz_all_samples": statistics.median(sm)}
 

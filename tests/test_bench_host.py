@@ -116,6 +116,16 @@ def test_clock_record_is_the_median_under_load():
     assert rec["sm_mhz"] == 2070.0 and rec["sm_mhz_all_samples"] == 120.0
     assert (rec["samples"], rec["samples_busy"]) == (8, 3)
     assert rec["reasons"] == ["sw_power_cap"] and rec["sm_max_mhz"] == 2070.0
+    assert rec["sm_mhz_basis"] == "median of busy samples"
+    # no busy sample at all: the highest clock seen, and the record says so
+    c = bench.ClockSampler(0)
+    with open(c.path, "w") as fh:
+        fh.write("0, 120, 2070, 150.1, 0x0, Not Active, Not Active, Not Active, Not Active, 0\n" * 4)
+        fh.write("0, 1980, 2070, 400.0, 0x0, Not Active, Not Active, Not Active, Not Active, 12\n")
+    c.proc, c.fh = Done(), open(os.devnull, "w")
+    rec = c.stop()
+    assert rec["sm_mhz"] == 1980.0 and rec["samples_busy"] == 0
+    assert rec["sm_mhz_basis"] == "highest sample (no busy sample)"
 
 
 def _run_bench(args, env_extra=None, timeout=300):
