@@ -83,7 +83,6 @@ template <int C, int LANES>
 __global__ void __launch_bounds__(kClThreads, 1)
     cluster_insert_kernel(const ManyItem *__restrict__ items, const ManyItem one, uint32_t slice_max,
                           uint32_t rank_u16, uint32_t kpc) {
-    constexpr int G = 32 / LANES;             // groups per warp
     constexpr int W = kBlockWords / LANES;    // words per lane
     constexpr int TC = kClThreads / LANES;    // groups per CTA
     __shared__ uint64_t s_amul[32];

@@ -96,11 +96,13 @@ struct ManyItem {
 // Many-filter execution (bc_many.cu): one cooperative insert launch over the
 // rounds of a work list, and one query launch over its bitmap words.
 uint64_t many_tile();
-cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
-                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, uint32_t tile,
-                               unsigned int *bar, unsigned long long *err, int sms);
-cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
-                              uint32_t nitems, const uint32_t *prefix);
+// bitsel: some item uses distinct bit selection; pow2: every item's block
+// count is a power of two (each picks a kernel instance, never a result).
+cudaError_t launch_insert_many(int C, int lanes, bool bitsel, bool pow2, int grid, cudaStream_t s,
+                               const ManyItem *items, uint32_t nitems, const uint32_t *prefix, uint32_t nrounds,
+                               uint32_t tile, unsigned int *bar, unsigned long long *err, int sms);
+cudaError_t launch_query_many(int C, int lanes, bool early, bool bitsel, bool pow2, int grid, cudaStream_t s,
+                              const ManyItem *items, uint32_t nitems, const uint32_t *prefix);
 
 // Cluster-resident insert (bc_cluster.cu): one thread-block cluster holds a
 // whole filter in the distributed shared memory of its CTAs and runs every

@@ -60,7 +60,11 @@ __device__ __forceinline__ void load_item(const ManyItem *it, DevFilter &f, uint
     __syncwarp();
 }
 
-template <int C, int LANES>
+// BITSEL: some item of the launch uses distinct bit selection; POW2: every
+// item's block count is a power of two. The instances without a path compile
+// it out (as in the single-filter kernels: inlined runtime branches cost the
+// hot path registers).
+template <int C, int LANES, bool BITSEL, bool POW2>
 __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *__restrict__ items, uint32_t nitems,
                                                                const uint32_t *__restrict__ prefix,
                                                                uint32_t nrounds, uint32_t tile,
@@ -84,6 +88,8 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
                 const ManyItem *it = items + fi;
                 DevFilter f;
                 load_item(it, f, s_amul[wib], lane);
+                if constexpr (!BITSEL) f.bitsel = 0;
+                if constexpr (POW2) f.range_kind = kRangePow2;
                 const uint64_t B = it->B, n = it->n;
                 const uint64_t bstart = (uint64_t)r * B;
                 const uint64_t bend = bstart + B < n ? bstart + B : n;
@@ -128,10 +134,9 @@ __global__ void __launch_bounds__(kThreads) insert_many_kernel(const ManyItem *_
     }
 }
 
-template <int C, int LANES, int MODE>
+template <int C, int LANES, int MODE, bool BITSEL, bool POW2>
 __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__restrict__ items, uint32_t nitems,
                                                               const uint32_t *__restrict__ prefix) {
-    constexpr int G = 32 / LANES;
     __shared__ uint64_t s_amul[kWarps][32];
     __shared__ __align__(16) uint32_t s_mask[kWarps * mask_u32_per_warp<LANES>()];
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
@@ -148,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__
         if (fi != cur) {
             it = items + fi;
             load_item(it, f, s_amul[wib], lane);
+            if constexpr (!BITSEL) f.bitsel = 0;
+            if constexpr (POW2) f.range_kind = kRangePow2;
             cur = fi;
         }
         const uint64_t wd = t - __ldg(prefix + fi);
@@ -156,12 +163,12 @@ __global__ void __launch_bounds__(kThreads) query_many_kernel(const ManyItem *__
     }
 }
 
-template <int C, int LANES>
+template <int C, int LANES, bool BITSEL, bool POW2>
 cudaError_t insert_many_launch(int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
                                const uint32_t *prefix, uint32_t nrounds, uint32_t tile, unsigned int *bar,
                                unsigned long long *err, int sms) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_many_kernel<C, LANES>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, insert_many_kernel<C, LANES, BITSEL, POW2>,
                                                                   kThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -170,57 +177,76 @@ cudaError_t insert_many_launch(int grid, cudaStream_t s, const ManyItem *items, 
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&items, (void *)&nitems, (void *)&prefix, (void *)&nrounds, (void *)&tile,
                     (void *)&bar, (void *)&err};
-    return cudaLaunchCooperativeKernel((const void *)insert_many_kernel<C, LANES>, dim3(g), dim3(kThreads),
+    return cudaLaunchCooperativeKernel((const void *)insert_many_kernel<C, LANES, BITSEL, POW2>, dim3(g), dim3(kThreads),
                                        args, 0, s);
 }
 
-template <int C>
-cudaError_t insert_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
-                                 const uint32_t *prefix, uint32_t nrounds, uint32_t tile, unsigned int *bar,
-                                 unsigned long long *err, int sms) {
+template <int C, bool BITSEL, bool POW2>
+cudaError_t insert_many_lanes(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
+                              const uint32_t *prefix, uint32_t nrounds, uint32_t tile, unsigned int *bar,
+                              unsigned long long *err, int sms) {
     switch (lanes) {
-        case 1: return insert_many_launch<C, 1>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
-        case 2: return insert_many_launch<C, 2>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
-        case 4: return insert_many_launch<C, 4>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
-        case 8: return insert_many_launch<C, 8>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 1: return insert_many_launch<C, 1, BITSEL, POW2>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 2: return insert_many_launch<C, 2, BITSEL, POW2>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 4: return insert_many_launch<C, 4, BITSEL, POW2>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 8: return insert_many_launch<C, 8, BITSEL, POW2>(grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int C, int MODE>
-cudaError_t query_many_dispatch(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
-                                const uint32_t *prefix) {
+// The instance for the launch's items (distinct selection always takes the
+// general addressing).
+template <int C>
+cudaError_t insert_many_dispatch(int lanes, bool bitsel, bool pow2, int grid, cudaStream_t s, const ManyItem *items,
+                                 uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, uint32_t tile,
+                                 unsigned int *bar, unsigned long long *err, int sms) {
+    if (bitsel) return insert_many_lanes<C, true, false>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+    if (pow2) return insert_many_lanes<C, false, true>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+    return insert_many_lanes<C, false, false>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+}
+
+template <int C, int MODE, bool BITSEL, bool POW2>
+cudaError_t query_many_lanes(int lanes, int grid, cudaStream_t s, const ManyItem *items, uint32_t nitems,
+                             const uint32_t *prefix) {
     switch (lanes) {
-        case 1: query_many_kernel<C, 1, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
-        case 2: query_many_kernel<C, 2, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
-        case 4: query_many_kernel<C, 4, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
-        case 8: query_many_kernel<C, 8, MODE><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 1: query_many_kernel<C, 1, MODE, BITSEL, POW2><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 2: query_many_kernel<C, 2, MODE, BITSEL, POW2><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 4: query_many_kernel<C, 4, MODE, BITSEL, POW2><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
+        case 8: query_many_kernel<C, 8, MODE, BITSEL, POW2><<<grid, kThreads, 0, s>>>(items, nitems, prefix); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+template <int C, int MODE>
+cudaError_t query_many_dispatch(int lanes, bool bitsel, bool pow2, int grid, cudaStream_t s, const ManyItem *items,
+                                uint32_t nitems, const uint32_t *prefix) {
+    if (bitsel) return query_many_lanes<C, MODE, true, false>(lanes, grid, s, items, nitems, prefix);
+    if (pow2) return query_many_lanes<C, MODE, false, true>(lanes, grid, s, items, nitems, prefix);
+    return query_many_lanes<C, MODE, false, false>(lanes, grid, s, items, nitems, prefix);
+}
+
 }  // namespace
 
-cudaError_t launch_insert_many(int C, int lanes, int grid, cudaStream_t s, const ManyItem *items,
-                               uint32_t nitems, const uint32_t *prefix, uint32_t nrounds, uint32_t tile,
-                               unsigned int *bar, unsigned long long *err, int sms) {
+cudaError_t launch_insert_many(int C, int lanes, bool bitsel, bool pow2, int grid, cudaStream_t s,
+                               const ManyItem *items, uint32_t nitems, const uint32_t *prefix, uint32_t nrounds,
+                               uint32_t tile, unsigned int *bar, unsigned long long *err, int sms) {
     switch (C) {
-        case 1: return insert_many_dispatch<1>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
-        case 2: return insert_many_dispatch<2>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
-        case 3: return insert_many_dispatch<3>(lanes, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 1: return insert_many_dispatch<1>(lanes, bitsel, pow2, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 2: return insert_many_dispatch<2>(lanes, bitsel, pow2, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
+        case 3: return insert_many_dispatch<3>(lanes, bitsel, pow2, grid, s, items, nitems, prefix, nrounds, tile, bar, err, sms);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_query_many(int C, int lanes, bool early, int grid, cudaStream_t s, const ManyItem *items,
-                              uint32_t nitems, const uint32_t *prefix) {
+cudaError_t launch_query_many(int C, int lanes, bool early, bool bitsel, bool pow2, int grid, cudaStream_t s,
+                              const ManyItem *items, uint32_t nitems, const uint32_t *prefix) {
     switch (C) {
-        case 1: return query_many_dispatch<1, 0>(lanes, grid, s, items, nitems, prefix);
-        case 2: return early ? query_many_dispatch<2, 1>(lanes, grid, s, items, nitems, prefix)
-                             : query_many_dispatch<2, 0>(lanes, grid, s, items, nitems, prefix);
-        case 3: return early ? query_many_dispatch<3, 1>(lanes, grid, s, items, nitems, prefix)
-                             : query_many_dispatch<3, 0>(lanes, grid, s, items, nitems, prefix);
+        case 1: return query_many_dispatch<1, 0>(lanes, bitsel, pow2, grid, s, items, nitems, prefix);
+        case 2: return early ? query_many_dispatch<2, 1>(lanes, bitsel, pow2, grid, s, items, nitems, prefix)
+                             : query_many_dispatch<2, 0>(lanes, bitsel, pow2, grid, s, items, nitems, prefix);
+        case 3: return early ? query_many_dispatch<3, 1>(lanes, bitsel, pow2, grid, s, items, nitems, prefix)
+                             : query_many_dispatch<3, 0>(lanes, bitsel, pow2, grid, s, items, nitems, prefix);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -251,6 +277,8 @@ struct ManyPlan {
         int lanes;                // lanes per key of the group's launch
         uint32_t tile;            // insert: keys per tile
         int early;                // query: stop at the first candidate holding the key
+        bool bitsel = false;      // some item uses distinct bit selection
+        bool pow2 = true;         // every item's block count is a power of two
     };
     struct Slot {
         ManyItem *d_items = nullptr, *h_items = nullptr;
@@ -530,7 +558,11 @@ int prepare(const blowchoc_batch *b, ManyPlan &p, const blowchoc_work *items, ui
             std::vector<ManyItem> &mine = kv.second;
             ManyPlan::Group g{C, (uint32_t)list.size(), (uint32_t)mine.size(), prefix.size(), 0, 0,
                               kv.first.first, query ? 0u : kv.first.second, query ? (int)kv.first.second : 0};
-            for (const ManyItem &it : mine) g.keys += it.n;
+            for (const ManyItem &it : mine) {
+                g.keys += it.n;
+                g.bitsel = g.bitsel || it.f.bitsel != 0;
+                g.pow2 = g.pow2 && it.f.range_kind == bc::kRangePow2;
+            }
             if (query) {
                 prefix.push_back(0);
                 for (const ManyItem &it : mine) {
@@ -634,9 +666,10 @@ int launch(blowchoc_batch *b, const ManyPlan &p, bool query, cudaStream_t s, boo
         }
         cudaError_t e;
         if (query)
-            e = bc::launch_query_many(g.C, g.lanes, g.early != 0, grid, s, items, g.nitems, prefix);
+            e = bc::launch_query_many(g.C, g.lanes, g.early != 0, g.bitsel, g.pow2, grid, s, items, g.nitems, prefix);
         else
-            e = bc::launch_insert_many(g.C, g.lanes, grid, s, items, g.nitems, prefix, g.nrounds, g.tile, bar, err,
+            e = bc::launch_insert_many(g.C, g.lanes, g.bitsel, g.pow2, grid, s, items, g.nitems, prefix, g.nrounds, g.tile,
+                                       bar, err,
                                        b->sms);
         if (e != cudaSuccess) return cuda_err(e, query ? "query_many launch" : "insert_many launch");
         bc_note_launch();
