@@ -121,11 +121,16 @@ constexpr int kSmallThreads = 1024;
 template <int LANES>
 constexpr size_t small_mask_bytes() { return (kSmallThreads / 32) * mask_u32_per_warp<LANES>() * 4; }
 
-template <int C, int LANES>
-__global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f, const uint64_t *__restrict__ keys,
+// BITSEL and POW2 as in the persistent kernel.
+template <int C, int LANES, bool BITSEL, bool POW2>
+__global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(const DevFilter fp,
+                                                                    const uint64_t *__restrict__ keys,
                                                                     uint64_t n, uint64_t B,
                                                                     const uint16_t *__restrict__ rank_g,
                                                                     unsigned long long *counters) {
+    DevFilter f = fp;
+    if constexpr (!BITSEL) f.bitsel = 0;
+    if constexpr (POW2) f.range_kind = kRangePow2;
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
     extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(DevFilter f,
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_dyn);
     uint8_t *sel = s_dyn + small_mask_bytes<LANES>();
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(sel + kSmallBatchMax);
-    stage_bit_mults(f, s_amul);
+    stage_bit_mults(fp, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
@@ -210,10 +215,14 @@ __host__ __device__ inline size_t bulk_ring_offset(int C, uint32_t k) {
 // -> 3.63 ms with the power-of-two addressing alone).
 template <int C, int LANES, bool BULK, bool BITSEL, bool POW2>
 __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ctas<LANES>()) persistent_insert_kernel(
-    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
+    const DevFilter fp, const uint64_t *__restrict__ keys, uint64_t n, uint64_t B,
     const uint16_t *__restrict__ rank_g, uint8_t *sel, unsigned long long *counters,
     unsigned int *bar) {
-    // constants from here on: the paths this instance does not take fold away
+    // constants from here on: the paths this instance does not take fold away.
+    // The bit multipliers are staged from the parameter itself: read with a
+    // thread-dependent index through the modified copy, they made the compiler
+    // keep the whole copy (328 bytes) in local memory and read every field there.
+    DevFilter f = fp;
     if constexpr (!BITSEL) f.bitsel = 0;
     if constexpr (POW2) f.range_kind = kRangePow2;
     constexpr int G = 32 / LANES;
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(persistent_threads<LANES>(), persistent_min_ct
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_dyn);
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(persistent_threads<LANES>() / 32) * mask_u32_per_warp<LANES>()];
-    stage_bit_mults(f, s_amul);
+    stage_bit_mults(fp, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
@@ -509,10 +518,16 @@ __global__ void __launch_bounds__(kThreads) sorted_insert_kernel(
 
 constexpr int kSeqThreads = 1024;
 
-template <int C, int LANES>
+// BITSEL and POW2 as in the persistent kernel: the instance for a filter
+// without distinct selection, or with a power-of-two block count, has the
+// other paths compiled out.
+template <int C, int LANES, bool BITSEL, bool POW2>
 __global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
-    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint32_t window,
+    const DevFilter fp, const uint64_t *__restrict__ keys, uint64_t n, uint32_t window,
     const uint16_t *__restrict__ rank_g, unsigned long long *counters, unsigned long long *resv) {
+    DevFilter f = fp;
+    if constexpr (!BITSEL) f.bitsel = 0;
+    if constexpr (POW2) f.range_kind = kRangePow2;
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
     extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -522,7 +537,7 @@ __global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * mask_u32_per_warp<LANES>()];
     __shared__ int s_left;
-    stage_bit_mults(f, s_amul);
+    stage_bit_mults(fp, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
@@ -588,10 +603,13 @@ __global__ void __launch_bounds__(kSeqThreads) exact_sequential_kernel(
 // filter, and only after all of them decided do they set their bits. Batches
 // that commit in the same round touch disjoint blocks. The outcome is that of
 // inserting the batches one after another. The window holds whole batches.
-template <int C, int LANES>
+template <int C, int LANES, bool BITSEL, bool POW2>
 __global__ void __launch_bounds__(kSeqThreads) exact_batched_kernel(
-    DevFilter f, const uint64_t *__restrict__ keys, uint64_t n, uint32_t B, uint32_t window,
+    const DevFilter fp, const uint64_t *__restrict__ keys, uint64_t n, uint32_t B, uint32_t window,
     const uint16_t *__restrict__ rank_g, unsigned long long *counters, unsigned long long *resv) {
+    DevFilter f = fp;
+    if constexpr (!BITSEL) f.bitsel = 0;
+    if constexpr (POW2) f.range_kind = kRangePow2;
     constexpr int G = 32 / LANES;
     constexpr int W = kBlockWords / LANES;
     extern __shared__ __align__(16) uint8_t s_dyn[];
@@ -604,7 +622,7 @@ __global__ void __launch_bounds__(kSeqThreads) exact_batched_kernel(
     __shared__ uint64_t s_amul[32];
     __shared__ __align__(16) uint32_t s_mask[(kSeqThreads / 32) * mask_u32_per_warp<LANES>()];
     __shared__ int s_left;
-    stage_bit_mults(f, s_amul);
+    stage_bit_mults(fp, s_amul);
     const uint16_t *rank = stage_rank<C>(rank_g, s_rank, f.k + 1);
     if constexpr (C == 1) __syncthreads();
     const int lane = threadIdx.x & 31, q = lane % LANES, g = lane / LANES;
@@ -711,15 +729,25 @@ cudaError_t choose_dispatch(const Launch &L, const DevFilter &f, const uint64_t 
     }
 }
 
-template <int C, int LANES>
+template <int C, int LANES, bool BITSEL, bool POW2>
 cudaError_t small_launch(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n, uint64_t B,
                          const uint16_t *rank, unsigned long long *counters) {
     const size_t sm = small_mask_bytes<LANES>() + kSmallBatchMax + rank_bytes(C, f.k);
-    cudaError_t e = cudaFuncSetAttribute(small_batch_kernel<C, LANES>,
+    cudaError_t e = cudaFuncSetAttribute(small_batch_kernel<C, LANES, BITSEL, POW2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    small_batch_kernel<C, LANES><<<1, kSmallThreads, sm, L.stream>>>(f, keys, n, B, rank, counters);
+    small_batch_kernel<C, LANES, BITSEL, POW2><<<1, kSmallThreads, sm, L.stream>>>(f, keys, n, B, rank, counters);
     return cudaGetLastError();
+}
+
+// The instance for the filter's bit selection and block range (distinct
+// selection always takes the general addressing).
+template <int C, int LANES>
+cudaError_t small_variant(const Launch &L, const DevFilter &f, const uint64_t *keys, uint64_t n, uint64_t B,
+                          const uint16_t *rank, unsigned long long *counters) {
+    if (f.bitsel) return small_launch<C, LANES, true, false>(L, f, keys, n, B, rank, counters);
+    if (f.range_kind == kRangePow2) return small_launch<C, LANES, false, true>(L, f, keys, n, B, rank, counters);
+    return small_launch<C, LANES, false, false>(L, f, keys, n, B, rank, counters);
 }
 
 template <int C>
@@ -727,9 +755,9 @@ cudaError_t small_dispatch(const Launch &L, const DevFilter &f, const uint64_t *
                            uint64_t B, const uint16_t *rank, unsigned long long *counters) {
     switch (L.lanes) {
         case 1:  // one lane per key needs more registers than a 1024-thread CTA allows
-        case 2: return small_launch<C, 2>(L, f, keys, n, B, rank, counters);
-        case 4: return small_launch<C, 4>(L, f, keys, n, B, rank, counters);
-        case 8: return small_launch<C, 8>(L, f, keys, n, B, rank, counters);
+        case 2: return small_variant<C, 2>(L, f, keys, n, B, rank, counters);
+        case 4: return small_variant<C, 4>(L, f, keys, n, B, rank, counters);
+        case 8: return small_variant<C, 8>(L, f, keys, n, B, rank, counters);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -819,31 +847,54 @@ cudaError_t sorted_dispatch(const Launch &L, const DevFilter &f, const uint64_t 
     }
 }
 
-template <int C, int LANES>
+template <int C, int LANES, bool BITSEL, bool POW2>
 cudaError_t exact_seq_launch(cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n, uint32_t window,
                              const uint16_t *rank, unsigned long long *counters, unsigned long long *resv) {
     const size_t sm = (size_t)window * 8 + ((window + 15) & ~15u) + rank_bytes(C, f.k);
-    cudaError_t e = cudaFuncSetAttribute(exact_sequential_kernel<C, LANES>,
+    cudaError_t e = cudaFuncSetAttribute(exact_sequential_kernel<C, LANES, BITSEL, POW2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(resv, 0, f.M * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    exact_sequential_kernel<C, LANES><<<1, kSeqThreads, sm, s>>>(f, keys, n, window, rank, counters, resv);
+    exact_sequential_kernel<C, LANES, BITSEL, POW2><<<1, kSeqThreads, sm, s>>>(f, keys, n, window, rank, counters,
+                                                                               resv);
     return cudaGetLastError();
 }
 
+// The instance for the filter's bit selection and block range (distinct
+// selection always takes the general addressing).
 template <int C, int LANES>
+cudaError_t exact_seq_variant(cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n, uint32_t window,
+                              const uint16_t *rank, unsigned long long *counters, unsigned long long *resv) {
+    if (f.bitsel) return exact_seq_launch<C, LANES, true, false>(s, f, keys, n, window, rank, counters, resv);
+    if (f.range_kind == kRangePow2)
+        return exact_seq_launch<C, LANES, false, true>(s, f, keys, n, window, rank, counters, resv);
+    return exact_seq_launch<C, LANES, false, false>(s, f, keys, n, window, rank, counters, resv);
+}
+
+template <int C, int LANES, bool BITSEL, bool POW2>
 cudaError_t exact_batched_launch(cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n, uint32_t B,
                                  uint32_t window, const uint16_t *rank, unsigned long long *counters,
                                  unsigned long long *resv) {
     const size_t wpad = (window + 15) & ~15u;
     const size_t sm = (size_t)window * 8 + 3 * wpad + rank_bytes(C, f.k);
-    cudaError_t e = allow_smem(exact_batched_kernel<C, LANES>, sm);
+    cudaError_t e = allow_smem(exact_batched_kernel<C, LANES, BITSEL, POW2>, sm);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(resv, 0, f.M * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    exact_batched_kernel<C, LANES><<<1, kSeqThreads, sm, s>>>(f, keys, n, B, window, rank, counters, resv);
+    exact_batched_kernel<C, LANES, BITSEL, POW2><<<1, kSeqThreads, sm, s>>>(f, keys, n, B, window, rank, counters,
+                                                                            resv);
     return cudaGetLastError();
+}
+
+template <int C, int LANES>
+cudaError_t exact_batched_variant(cudaStream_t s, const DevFilter &f, const uint64_t *keys, uint64_t n, uint32_t B,
+                                  uint32_t window, const uint16_t *rank, unsigned long long *counters,
+                                  unsigned long long *resv) {
+    if (f.bitsel) return exact_batched_launch<C, LANES, true, false>(s, f, keys, n, B, window, rank, counters, resv);
+    if (f.range_kind == kRangePow2)
+        return exact_batched_launch<C, LANES, false, true>(s, f, keys, n, B, window, rank, counters, resv);
+    return exact_batched_launch<C, LANES, false, false>(s, f, keys, n, B, window, rank, counters, resv);
 }
 
 }  // namespace
@@ -853,9 +904,9 @@ cudaError_t launch_exact_batched(int C, cudaStream_t s, const DevFilter &f, cons
                                  unsigned long long *resv) {
     if (B < 2 || B > kSeqMaxBatch || window < B || window > kSeqMaxWindow || window % B) return cudaErrorInvalidValue;
     switch (C) {
-        case 1: return exact_batched_launch<1, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
-        case 2: return exact_batched_launch<2, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
-        case 3: return exact_batched_launch<3, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
+        case 1: return exact_batched_variant<1, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
+        case 2: return exact_batched_variant<2, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
+        case 3: return exact_batched_variant<3, 2>(s, f, keys, n, (uint32_t)B, window, rank, counters, resv);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -865,9 +916,9 @@ cudaError_t launch_exact_sequential(int C, cudaStream_t s, const DevFilter &f, c
                                     unsigned long long *resv) {
     if (window < 32 || window > kSeqMaxWindow) return cudaErrorInvalidValue;
     switch (C) {
-        case 1: return exact_seq_launch<1, 2>(s, f, keys, n, window, rank, counters, resv);
-        case 2: return exact_seq_launch<2, 2>(s, f, keys, n, window, rank, counters, resv);
-        case 3: return exact_seq_launch<3, 2>(s, f, keys, n, window, rank, counters, resv);
+        case 1: return exact_seq_variant<1, 2>(s, f, keys, n, window, rank, counters, resv);
+        case 2: return exact_seq_variant<2, 2>(s, f, keys, n, window, rank, counters, resv);
+        case 3: return exact_seq_variant<3, 2>(s, f, keys, n, window, rank, counters, resv);
         default: return cudaErrorInvalidValue;
     }
 }
