@@ -674,6 +674,9 @@ int blowchoc_insert_sampled(blowchoc_filter *f, const uint64_t *d_keys, uint64_t
  *       cluster-resident) use the same rounds with whole batches in place
  *       of keys, over windows of seq_window keys rounded to whole batches
  *       (at least four); 0 = one CTA running the batches one after another.
+ *       Default 512, or 256 for batches of B = 2..16 keys when
+ *       64 (B c)^2 >= M (their candidate blocks meet often); the window
+ *       never changes the result.
  *   cluster_max: an insert of at least 4 batches (B >= 2; B <= 2048 while
  *       persistent is 1) into a filter that fits in the shared memory of one
  *       thread-block cluster runs cluster-resident: the cluster's CTAs hold the filter's words (a

@@ -246,6 +246,20 @@ int blowchoc_create(const blowchoc_params *params, void *stream, blowchoc_filter
     // 512 MiB 21.0-21.8 against 23.2-23.4; 16 MiB and below 3-18% slower;
     // the 128 MiB DNA shape, c = 3, k = 16: 2.83 against 2.59)
     f->set_mode = (bytes > (uint64_t)l2 && (params->choices <= 2 || bytes > 3ull * (uint64_t)l2 / 2)) ? 2 : 0;
+    // reservation window of the exact inserts of B <= 16 (one GB300, 2^15 to
+    // 2^21 blocks, 2.8 M keys or 12 bits per key): 512 keys, one commit pass
+    // of the 1024-thread CTA at two lanes per key, was the fastest window or
+    // within 5% of it for B = 1 (2^16 blocks, c = 2: 47.5 ms against 54.2
+    // with 2048 and 72.2 with 128). Windows of batches whose candidate blocks
+    // often meet, 64 (B c)^2 >= M, did best at 256 (2^16 blocks, B = 16,
+    // c = 3: 145.8 ms against 164.9 with 512 and 326.6 with 2048); larger
+    // filters at 512 (2^21 blocks, B = 16, c = 2: 53.7 against 61.7 with 256).
+    {
+        const uint64_t bcw = params->batch * params->choices;
+        f->seq_window = (params->batch > 1 && params->batch <= bc::kSeqMaxBatch && 64 * bcw * bcw >= params->nblocks)
+                            ? 256
+                            : 512;
+    }
     bc::DevFilter &d = f->dev;
     std::memset(&d, 0, sizeof d);
     d.M = params->nblocks;

@@ -26,7 +26,7 @@ struct blowchoc_filter {
     int set_mode = 0;              // 0: atomic OR at L2; 1: sort by block range
     uint32_t *d_sorted = nullptr;  // sort-by-block scratch (3 R + 1 + batch u32)
     uint64_t sorted_cap = 0;
-    int seq_window = 2048;         // B = 1: keys per reservation window (0: one-warp kernel)
+    int seq_window = 512;          // B <= 16: keys per reservation window, set at creation (0: one-warp kernel)
     unsigned long long *d_resv = nullptr;  // B = 1 reservations, M words
     int cluster_max = 16;          // cluster-resident insert: CTAs per cluster at most (0: off)
     int lanes_cluster = 8;
