@@ -179,8 +179,8 @@ class OracleFilter:
         return hist, int(total)
 
     def block_terms(self, block, x):
-        _load().orc_set_bitsel(self.bitsel)
         """(|F'|, |F(x) minus F'|) of block `block` for key x (Section 3.2)."""
+        _load().orc_set_bitsel(self.bitsel)
         L, a = ctypes.c_uint32(0), ctypes.c_uint32(0)
         _load().orc_block_terms(_ptr(self.words), block, _ptr(self.a_bit), self.k, x,
                                 ctypes.byref(L), ctypes.byref(a))

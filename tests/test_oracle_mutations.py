@@ -1,0 +1,218 @@
+"""Planted mistakes in the oracle must make one of its pins fail.
+
+The pins in tests/test_oracle_pins.py vouch for the oracle only if a
+plausible mistake in it would break one of them. Each case below copies one
+oracle source (the C file or a Python module), plants one such mistake (a
+dropped term, a wrong sign, index, bound or constant, a transposed operand),
+and runs the pin tests against the copy in a child process. The case passes
+when a pin fails there (pytest exit status 1). A mistake that crashes or
+hangs the child would not count, so the mistakes are chosen to keep every
+array access in bounds, and a child is given a time limit.
+
+Two controls run the same way with nothing planted: the unchanged C source
+compiled by this harness, and an unchanged Python module re-executed by it.
+They must pass every pin, which shows that a failing case fails because of
+its mistake and not because of the harness.
+
+CPU only; the children run in parallel, stopping at their first failing pin.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+PINS = os.path.join("tests", "test_oracle_pins.py")
+CHILD_TIMEOUT_S = 240
+
+# The child: point the oracle at the planted copy, then run the pins.
+#   kind "c":    the C library the oracle loads is the compiled copy;
+#   kind "none": nothing planted;
+#   otherwise:   the named oracle module is re-executed from the copy
+#                before the pins import anything from it.
+CHILD = r"""
+import importlib, sys
+kind, path = sys.argv[1], sys.argv[2]
+if kind == "c":
+    import oracle.build as ob
+    ob.build = lambda force=False: path
+elif kind != "none":
+    mod = importlib.import_module("oracle." + kind)
+    with open(path) as fh:
+        src = fh.read()
+    exec(compile(src, mod.__file__, "exec"), mod.__dict__)
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", sys.argv[3]]))
+"""
+
+# (name, file under oracle/, [(text, replacement), ...]); every text must
+# occur exactly once in its file.
+C_MUTANTS = [
+    # generator (splitmix64) and multipliers (Section 3.4)
+    ("splitmix_shift", [("z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;",
+                         "z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;")]),
+    ("splitmix_increment", [("(*state += 0x9e3779b97f4a7c15ULL)", "(*state += 0x9e3779b97f4a7c13ULL)")]),
+    ("block_multiplier_even", [("a = orc_splitmix64_next(&state) | 1u;\n        } while (orc_gcd(a, M) != 1);",
+                                "a = orc_splitmix64_next(&state);\n        } while (orc_gcd(a, M) != 1);")]),
+    ("block_multiplier_not_coprime", [("} while (orc_gcd(a, M) != 1);", "} while (0);")]),
+    ("distinct_multiplier_range", [("uint64_t range = orc_bitsel ? ORC_BLOCK_BITS - i : ORC_BLOCK_BITS;",
+                                    "uint64_t range = ORC_BLOCK_BITS;")]),
+    # linear hash (Section 3.4)
+    ("hash_pow2_low_bits", [("return (y >> (64u - lg)) % b;", "return y % b;")]),
+    ("hash_pow2_shift_off_by_one", [("return (y >> (64u - lg)) % b;", "return (y >> (63u - lg)) % b;")]),
+    ("hash_even_fold_dropped", [("    if ((b & 1u) == 0)\n        y = y ^ (y >> 32);\n", "")]),
+    # costs (Eq. 4-6)
+    ("mix_new_bits_dropped", [("pow((double)j / 256.0, dk) + (double)a;", "pow((double)j / 256.0, dk);")]),
+    ("mix_wrong_scale", [("pow((double)j / 256.0, dk)", "pow((double)j / 512.0, dk)")]),
+    ("la_wrong_sign", [("((double)j + param * dk)", "((double)j - param * dk)")]),
+    ("la_factor_k_dropped", [("return dk * pow(((double)j + param * dk)", "return pow(((double)j + param * dk)")]),
+    ("exp_operands_transposed", [("pow(param, (double)j / 128.0)", "pow((double)j / 128.0, param)")]),
+    ("exp_divisor_dropped", [("+ (double)a / dk;", "+ (double)a;")]),
+    # bits of a block
+    ("get_bit_reversed_in_word", [("(words[8u * b + p / 64u] >> (p % 64u)) & 1u",
+                                   "(words[8u * b + p / 64u] >> (63u - p % 64u)) & 1u")]),
+    ("set_bit_wrong_word", [("words[8u * b + p / 64u] |= ", "words[8u * b + (p / 64u + 1u) % 8u] |= ")]),
+    ("load_misses_last_bit", [("for (uint32_t p = 0; p < ORC_BLOCK_BITS; p++)\n        L += ",
+                               "for (uint32_t p = 0; p + 1 < ORC_BLOCK_BITS; p++)\n        L += ")]),
+    ("new_bits_negated", [("if (inF[p] && !orc_get_bit(words, b, p))\n            a++;",
+                           "if (inF[p] && orc_get_bit(words, b, p))\n            a++;")]),
+    # the choice (Section 3.2)
+    ("skip_rule_dropped", [("        if (a[i] == 0)\n            return -1;\n", "")]),
+    ("ties_to_last", [("cost < best_cost", "cost <= best_cost")]),
+    ("argmax_instead_of_argmin", [("cost < best_cost", "cost > best_cost")]),
+    ("cost_of_load_before_insert", [("orc_cost(kind, param, k, L + a[i], a[i])", "orc_cost(kind, param, k, L, a[i])")]),
+    # batch-synchronous insertion (Section 3.1)
+    ("keys_one_by_one", [("uint64_t e = (n - s) < B ? n : s + B;", "uint64_t e = s + 1;"),
+                         ("for (uint64_t s = 0; s < n; s += B) {", "for (uint64_t s = 0; s < n; s += 1) {")]),
+    ("last_key_dropped", [("uint64_t e = (n - s) < B ? n : s + B;", "uint64_t e = (n - s) <= B ? n - 1 : s + B;")]),
+    ("set_in_first_candidate", [("uint64_t b = orc_hash(a_block[(int)ch[t - s]], keys[t], M);",
+                                 "uint64_t b = orc_hash(a_block[0], keys[t], M);")]),
+    # query (Section 3.1)
+    ("query_first_candidate_only", [("for (uint32_t i = 0; i < c && !hit; i++) {",
+                                     "for (uint32_t i = 0; i < 1 && !hit; i++) {")]),
+    ("query_bitmap_msb_first", [("bitmap[t / 64] |= (uint64_t)1 << (t % 64);",
+                                 "bitmap[t / 64] |= (uint64_t)1 << (63 - t % 64);")]),
+    # load histogram (Appendix C)
+    ("histogram_off_by_one", [("hist[L]++;", "hist[L > 0 ? L - 1 : 0]++;")]),
+    ("histogram_total_counts_blocks", [("total += L;", "total += 1;")]),
+    # distinct bit selection (Appendix B)
+    ("distinct_shift_strict", [("uint32_t f = (uint32_t)orc_hash(a_bit[i], x, ORC_BLOCK_BITS - i);\n"
+                                "        uint32_t pos = 0;\n        while (pos < nsorted && sorted[pos] <= f) {",
+                                "uint32_t f = (uint32_t)orc_hash(a_bit[i], x, ORC_BLOCK_BITS - i);\n"
+                                "        uint32_t pos = 0;\n        while (pos < nsorted && sorted[pos] < f) {")]),
+    ("distinct_raw_shift_strict", [("uint32_t f = raw[i];\n        uint32_t pos = 0;\n"
+                                    "        while (pos < nsorted && sorted[pos] <= f) {",
+                                    "uint32_t f = raw[i];\n        uint32_t pos = 0;\n"
+                                    "        while (pos < nsorted && sorted[pos] < f) {")]),
+]
+
+PY_MUTANTS = [
+    # closed forms (Eq. 1, Eq. 2, Fig. 3, Appendix C)
+    ("closed_forms", "bloom_fpr_k_dropped", [("math.exp(-n * k / m)", "math.exp(-n / m)")]),
+    ("closed_forms", "overload_sign", [("2.0 ** (-gamma)", "2.0 ** (gamma)")]),
+    ("closed_forms", "bloom_bits_times_ln2", [("n * k / math.log(2.0)", "n * k * math.log(2.0)")]),
+    ("closed_forms", "load_bound_sign", [("256.0 * c ** (-1.0 / k)", "256.0 * c ** (1.0 / k)")]),
+    ("closed_forms", "birthday_off_by_one", [("p *= 1.0 - i / s", "p *= 1.0 - (i + 1) / s")]),
+    ("closed_forms", "blocked_bloom_bit_exponent", [("(1.0 - 1.0 / BLOCK_BITS) ** (i * k)",
+                                                     "(1.0 - 1.0 / BLOCK_BITS) ** i")]),
+    ("closed_forms", "state_fpr_exponent", [("(L / BLOCK_BITS) ** k", "(L / BLOCK_BITS) ** (k - 1)")]),
+    # learned cost: network, gradient, sampler, Adam
+    ("learned", "grid_load_without_new_bits", [("(L + a) / 512.0", "L / 512.0")]),
+    ("learned", "forward_bias_sign", [("return h2 @ w3 + b3", "return h2 @ w3 - b3")]),
+    ("learned", "tanh_derivative_wrong", [("d1 = (d2 @ W2) * (1.0 - h1 ** 2)", "d1 = (d2 @ W2) * (1.0 - h1)")]),
+    ("learned", "output_bias_gradient_dropped", [("g[5 * H + H * H] = w.sum()", "g[5 * H + H * H] = 0.0")]),
+    ("learned", "second_layer_transposed", [("g[3 * H:3 * H + H * H] = (d2.T @ h1).reshape(-1)",
+                                             "g[3 * H:3 * H + H * H] = (h1.T @ d2).reshape(-1)")]),
+    ("learned", "uniform_bits", [("return (z >> 11) / float(1 << 53)", "return (z >> 12) / float(1 << 53)")]),
+    ("learned", "policy_sign", [("e = np.exp(-(g - g.min()) / tau)", "e = np.exp((g - g.min()) / tau)")]),
+    ("learned", "score_weight_tau_dropped", [("w[p] += (e[i] / z - (1.0 if i == s else 0.0)) / tau",
+                                              "w[p] += (e[i] / z - (1.0 if i == s else 0.0))")]),
+    ("learned", "adam_bias_correction_dropped", [("vh = m2 / (1 - b2 ** step)", "vh = m2")]),
+    ("learned", "adam_betas_swapped", [("mh = m1 / (1 - b1 ** step)", "mh = m1 / (1 - b2 ** step)")]),
+    # sub-arrays (Section 3.4)
+    ("sharded", "h0_multiplier_even", [("a0 = out | 1", "a0 = out")]),
+    ("sharded", "query_wrong_subarray", [("idx = np.flatnonzero(sh == t)",
+                                          "idx = np.flatnonzero(sh == (t + 1) % self.T)")]),
+    ("sharded", "layout_reversed", [("np.concatenate([s.words for s in self.subs])",
+                                     "np.concatenate([s.words for s in reversed(self.subs)])")]),
+    # the wrapper
+    ("oracle", "bitmap_unpacked_msb_first", [('np.unpackbits(b, bitorder="little")[:n]',
+                                              'np.unpackbits(b, bitorder="big")[:n]')]),
+    ("oracle", "batch_argument_ignored", [("B = self.batch if batch is None else int(batch)", "B = self.batch")]),
+]
+
+
+def _plant(src, edits):
+    for old, new in edits:
+        assert src.count(old) == 1, "planted text must occur exactly once: %r" % old
+        src = src.replace(old, new)
+    return src
+
+
+def _compile_c(src, out_dir, name):
+    c = os.path.join(out_dir, name + ".c")
+    lib = os.path.join(out_dir, "lib" + name + ".so")
+    with open(c, "w") as fh:
+        fh.write(src)
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", lib, c, "-lm"],
+                   check=True, capture_output=True)
+    return lib
+
+
+def _run_pins(kind, path):
+    """(exit status of the pin run against the planted copy, output tail)."""
+    try:
+        r = subprocess.run([sys.executable, "-c", CHILD, kind, path, PINS], cwd=ROOT,
+                           capture_output=True, text=True, timeout=CHILD_TIMEOUT_S)
+    except subprocess.TimeoutExpired:
+        return "timeout", ""
+    return r.returncode, (r.stdout + r.stderr)[-1500:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Exit status of the pins for every planted copy and both controls."""
+    out_dir = str(tmp_path_factory.mktemp("planted"))
+    with open(os.path.join(ORACLE, "blowchoc_oracle.c")) as fh:
+        c_src = fh.read()
+    jobs = {"control_c": ("c", _compile_c(c_src, out_dir, "control_c"))}
+    for name, edits in C_MUTANTS:
+        jobs[name] = ("c", _compile_c(_plant(c_src, edits), out_dir, name))
+    py_src = {}
+    for module in {m for m, _, _ in PY_MUTANTS}:
+        with open(os.path.join(ORACLE, module + ".py")) as fh:
+            py_src[module] = fh.read()
+    path = os.path.join(out_dir, "control_py.py")
+    with open(path, "w") as fh:
+        fh.write(py_src["closed_forms"])
+    jobs["control_py"] = ("closed_forms", path)
+    for module, name, edits in PY_MUTANTS:
+        path = os.path.join(out_dir, name + ".py")
+        with open(path, "w") as fh:
+            fh.write(_plant(py_src[module], edits))
+        jobs[name] = (module, path)
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {name: ex.submit(_run_pins, kind, path) for name, (kind, path) in jobs.items()}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("control", ["control_c", "control_py"])
+def test_unplanted_copies_pass_every_pin(outcomes, control):
+    rc, tail = outcomes[control]
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("name", [n for n, _ in C_MUTANTS])
+def test_planted_mistake_in_the_c_oracle_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
+
+
+@pytest.mark.parametrize("name", [n for _, n, _ in PY_MUTANTS])
+def test_planted_mistake_in_a_python_oracle_module_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)

@@ -352,6 +352,27 @@ def test_load_histograms_ordered_by_choices():
     assert stats[2][1] < stats[1][1] < stats[0][1]
 
 
+def test_histogram_is_blocks_per_popcount():
+    """hist[L] counts the blocks that hold exactly L set bits and the total is
+    every set bit (Appendix C, Fig. 8). Hand cases: an empty filter is M blocks
+    of load 0, and one key put into it makes one block of load |F(x)|. A built
+    filter's histogram equals numpy's count of the bits of its words."""
+    M, k = 257, 9
+    f = _filter(M, k, 2, COST_MIX, 50.0, seed=4)
+    hist, total = f.histogram()
+    assert int(hist[0]) == M and int(hist[1:].sum()) == 0 and total == 0
+    x = 0x243F6A8885A308D3
+    f.insert(np.array([x], dtype=np.uint64))
+    nF = len(oracle.bit_positions(f.a_bit[:k], x))
+    hist, total = f.histogram()
+    assert int(hist[0]) == M - 1 and int(hist[nF]) == 1 and total == nF
+    f.insert(workloads.uniform_keys(5, 3000))
+    hist, total = f.histogram()
+    pop = np.unpackbits(f.words.view(np.uint8)).reshape(M, 512).sum(axis=1)
+    assert np.array_equal(hist.astype(np.int64), np.bincount(pop, minlength=513))
+    assert total == int(pop.sum())
+
+
 def test_duplicates_and_skip_counts():
     f = _filter(32, 10, 2, COST_MIX, 50.0, B=1)
     keys = workloads.uniform_keys(91, 100)
@@ -395,6 +416,27 @@ def test_learned_forward_hand_value():
     g = lr.forward(p, 7)
     assert g.shape == (513 * 8,)
     assert np.allclose(g, 1.25, rtol=0, atol=1e-15)
+
+
+def test_learned_forward_reads_the_cost_arguments():
+    """The network reads the cost arguments of Section 3.2: j = L + a (set bits
+    after the insertion) over 512 and a over k. With W1[0] = (1, 0),
+    W1[1] = (0, 1), W2[0][0] = W2[1][1] = 1, w3 = (1, 1, 0, ...) and every other
+    parameter 0, the output at grid point L (k + 1) + a is
+    tanh(tanh((L + a) / 512)) + tanh(tanh(a / k))."""
+    from oracle import learned as lr
+    H, k = lr.H, 7
+    p = np.zeros(lr.NPARAMS)
+    p[0] = 1.0                                   # W1[0][0]
+    p[3] = 1.0                                   # W1[1][1]
+    p[3 * H] = 1.0                               # W2[0][0]
+    p[3 * H + H + 1] = 1.0                       # W2[1][1]
+    p[4 * H + H * H] = 1.0                       # w3[0]
+    p[4 * H + H * H + 1] = 1.0                   # w3[1]
+    g = lr.forward(p, k)
+    for L, a in [(0, 0), (10, 3), (200, 1), (505, 7)]:
+        want = math.tanh(math.tanh((L + a) / 512.0)) + math.tanh(math.tanh(a / k))
+        assert g[L * (k + 1) + a] == pytest.approx(want, rel=1e-14), (L, a)
 
 
 def test_learned_backward_matches_finite_differences():
@@ -672,6 +714,26 @@ def test_sharded_one_choice_is_a_textbook_blocked_bloom(M, T):
     w = s.words
     got = [sum(int(w[8 * b + j]) << (64 * j) for j in range(8)) for b in range(T * Ms)]
     assert got == want
+
+
+def test_sharded_h0_multiplier_is_drawn_first_odd_and_coprime():
+    """h_0's multiplier a_0 is drawn before the block and bit multipliers: the
+    first output of the seed's splitmix64 stream that is coprime to T, made
+    odd. Against the published check vector of seed 1234567 (outputs 1 and 2
+    are 0 and 1 mod 3): a_0 is output 1 for T = 2 and output 2 for T = 3, and
+    the sub-arrays' multipliers start from the state after it. Over many seeds
+    a_0 is odd and coprime to T."""
+    from oracle.sharded import shard_layout
+    want = [int(r[0]) for r in _rows("splitmix64_seed1234567.txt")]
+    gamma = 0x9E3779B97F4A7C15
+    a0, Ms, state = shard_layout(100, 2, 1234567)
+    assert (a0, Ms, state) == (want[0] | 1, 50, (1234567 + gamma) % (1 << 64))
+    a0, Ms, state = shard_layout(100, 3, 1234567)
+    assert (a0, Ms, state) == (want[1] | 1, 34, (1234567 + 2 * gamma) % (1 << 64))
+    for T in (3, 5, 6, 7):
+        for seed in range(64):
+            a0, _, _ = shard_layout(1000, T, seed)
+            assert a0 % 2 == 1 and math.gcd(a0, T) == 1, (T, seed, a0)
 
 
 @pytest.mark.parametrize("T", [2, 3, 4, 6])
