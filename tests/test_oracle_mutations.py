@@ -60,7 +60,10 @@ C_MUTANTS = [
     ("block_multiplier_not_coprime", [("} while (orc_gcd(a, M) != 1);", "} while (0);")]),
     ("distinct_multiplier_range", [("uint64_t range = orc_bitsel ? ORC_BLOCK_BITS - i : ORC_BLOCK_BITS;",
                                     "uint64_t range = ORC_BLOCK_BITS;")]),
+    ("random_bit_multiplier_range", [("uint64_t range = orc_bitsel ? ORC_BLOCK_BITS - i : ORC_BLOCK_BITS;",
+                                      "uint64_t range = orc_bitsel ? ORC_BLOCK_BITS - i : ORC_BLOCK_BITS - 1;")]),
     # linear hash (Section 3.4)
+    ("hash_odd_range", [("    return y % b;\n}", "    return y % (b - 1 > 0 ? b - 1 : 1);\n}")]),
     ("hash_pow2_low_bits", [("return (y >> (64u - lg)) % b;", "return y % b;")]),
     ("hash_pow2_shift_off_by_one", [("return (y >> (64u - lg)) % b;", "return (y >> (63u - lg)) % b;")]),
     ("hash_even_fold_dropped", [("    if ((b & 1u) == 0)\n        y = y ^ (y >> 32);\n", "")]),
@@ -71,7 +74,9 @@ C_MUTANTS = [
     ("la_factor_k_dropped", [("return dk * pow(((double)j + param * dk)", "return pow(((double)j + param * dk)")]),
     ("exp_operands_transposed", [("pow(param, (double)j / 128.0)", "pow((double)j / 128.0, param)")]),
     ("exp_divisor_dropped", [("+ (double)a / dk;", "+ (double)a;")]),
+    ("table_cost_indexed_by_j", [("orc_table[(j - a) * (k + 1) + a]", "orc_table[j * (k + 1) + a]")]),
     # bits of a block
+    ("bit_selection_mode_ignored", [("if (!orc_bitsel) {", "if (1) {")]),
     ("get_bit_reversed_in_word", [("(words[8u * b + p / 64u] >> (p % 64u)) & 1u",
                                    "(words[8u * b + p / 64u] >> (63u - p % 64u)) & 1u")]),
     ("set_bit_wrong_word", [("words[8u * b + p / 64u] |= ", "words[8u * b + (p / 64u + 1u) % 8u] |= ")]),
@@ -88,11 +93,13 @@ C_MUTANTS = [
     ("keys_one_by_one", [("uint64_t e = (n - s) < B ? n : s + B;", "uint64_t e = s + 1;"),
                          ("for (uint64_t s = 0; s < n; s += B) {", "for (uint64_t s = 0; s < n; s += 1) {")]),
     ("last_key_dropped", [("uint64_t e = (n - s) < B ? n : s + B;", "uint64_t e = (n - s) <= B ? n - 1 : s + B;")]),
+    ("skips_counted_as_inserts", [("n_skip++;", "n_ins++;")]),
     ("set_in_first_candidate", [("uint64_t b = orc_hash(a_block[(int)ch[t - s]], keys[t], M);",
                                  "uint64_t b = orc_hash(a_block[0], keys[t], M);")]),
     # query (Section 3.1)
     ("query_first_candidate_only", [("for (uint32_t i = 0; i < c && !hit; i++) {",
                                      "for (uint32_t i = 0; i < 1 && !hit; i++) {")]),
+    ("query_first_hit_index", [("hit = (int)i + 1;", "hit = (int)i;")]),
     ("query_bitmap_msb_first", [("bitmap[t / 64] |= (uint64_t)1 << (t % 64);",
                                  "bitmap[t / 64] |= (uint64_t)1 << (63 - t % 64);")]),
     # load histogram (Appendix C)
