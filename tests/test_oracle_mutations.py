@@ -9,10 +9,14 @@ when a pin fails there (pytest exit status 1). A mistake that crashes or
 hangs the child would not count, so the mistakes are chosen to keep every
 array access in bounds, and a child is given a time limit.
 
-Two controls run the same way with nothing planted: the unchanged C source
-compiled by this harness, and an unchanged Python module re-executed by it.
-They must pass every pin, which shows that a failing case fails because of
-its mistake and not because of the harness.
+The seeded input generators (workloads/) get the same treatment against
+tests/test_workloads_host.py: both sides of every parity test draw their
+keys from them, so only their own pins can catch a mistake there.
+
+Three controls run the same way with nothing planted: the unchanged C source
+compiled by this harness, and an unchanged oracle module and generator
+module re-executed by it. They must pass every pin, which shows that a
+failing case fails because of its mistake and not because of the harness.
 
 CPU only; the children run in parallel, stopping at their first failing pin.
 """
@@ -26,13 +30,14 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join("tests", "test_oracle_pins.py")
+WORKLOAD_PINS = os.path.join("tests", "test_workloads_host.py")
 CHILD_TIMEOUT_S = 240
 
 # The child: point the oracle at the planted copy, then run the pins.
 #   kind "c":    the C library the oracle loads is the compiled copy;
 #   kind "none": nothing planted;
-#   otherwise:   the named oracle module is re-executed from the copy
-#                before the pins import anything from it.
+#   otherwise:   the named module is re-executed from the copy before the
+#                pins import anything from it.
 CHILD = r"""
 import importlib, sys
 kind, path = sys.argv[1], sys.argv[2]
@@ -40,7 +45,7 @@ if kind == "c":
     import oracle.build as ob
     ob.build = lambda force=False: path
 elif kind != "none":
-    mod = importlib.import_module("oracle." + kind)
+    mod = importlib.import_module(kind)
     with open(path) as fh:
         src = fh.read()
     exec(compile(src, mod.__file__, "exec"), mod.__dict__)
@@ -118,37 +123,65 @@ C_MUTANTS = [
 
 PY_MUTANTS = [
     # closed forms (Eq. 1, Eq. 2, Fig. 3, Appendix C)
-    ("closed_forms", "bloom_fpr_k_dropped", [("math.exp(-n * k / m)", "math.exp(-n / m)")]),
-    ("closed_forms", "overload_sign", [("2.0 ** (-gamma)", "2.0 ** (gamma)")]),
-    ("closed_forms", "bloom_bits_times_ln2", [("n * k / math.log(2.0)", "n * k * math.log(2.0)")]),
-    ("closed_forms", "load_bound_sign", [("256.0 * c ** (-1.0 / k)", "256.0 * c ** (1.0 / k)")]),
-    ("closed_forms", "birthday_off_by_one", [("p *= 1.0 - i / s", "p *= 1.0 - (i + 1) / s")]),
-    ("closed_forms", "blocked_bloom_bit_exponent", [("(1.0 - 1.0 / BLOCK_BITS) ** (i * k)",
+    ("oracle.closed_forms", "bloom_fpr_k_dropped", [("math.exp(-n * k / m)", "math.exp(-n / m)")]),
+    ("oracle.closed_forms", "overload_sign", [("2.0 ** (-gamma)", "2.0 ** (gamma)")]),
+    ("oracle.closed_forms", "bloom_bits_times_ln2", [("n * k / math.log(2.0)", "n * k * math.log(2.0)")]),
+    ("oracle.closed_forms", "load_bound_sign", [("256.0 * c ** (-1.0 / k)", "256.0 * c ** (1.0 / k)")]),
+    ("oracle.closed_forms", "birthday_off_by_one", [("p *= 1.0 - i / s", "p *= 1.0 - (i + 1) / s")]),
+    ("oracle.closed_forms", "blocked_bloom_bit_exponent", [("(1.0 - 1.0 / BLOCK_BITS) ** (i * k)",
                                                      "(1.0 - 1.0 / BLOCK_BITS) ** i")]),
-    ("closed_forms", "state_fpr_exponent", [("(L / BLOCK_BITS) ** k", "(L / BLOCK_BITS) ** (k - 1)")]),
+    ("oracle.closed_forms", "state_fpr_exponent", [("(L / BLOCK_BITS) ** k", "(L / BLOCK_BITS) ** (k - 1)")]),
     # learned cost: network, gradient, sampler, Adam
-    ("learned", "grid_load_without_new_bits", [("(L + a) / 512.0", "L / 512.0")]),
-    ("learned", "forward_bias_sign", [("return h2 @ w3 + b3", "return h2 @ w3 - b3")]),
-    ("learned", "tanh_derivative_wrong", [("d1 = (d2 @ W2) * (1.0 - h1 ** 2)", "d1 = (d2 @ W2) * (1.0 - h1)")]),
-    ("learned", "output_bias_gradient_dropped", [("g[5 * H + H * H] = w.sum()", "g[5 * H + H * H] = 0.0")]),
-    ("learned", "second_layer_transposed", [("g[3 * H:3 * H + H * H] = (d2.T @ h1).reshape(-1)",
+    ("oracle.learned", "grid_load_without_new_bits", [("(L + a) / 512.0", "L / 512.0")]),
+    ("oracle.learned", "forward_bias_sign", [("return h2 @ w3 + b3", "return h2 @ w3 - b3")]),
+    ("oracle.learned", "tanh_derivative_wrong", [("d1 = (d2 @ W2) * (1.0 - h1 ** 2)", "d1 = (d2 @ W2) * (1.0 - h1)")]),
+    ("oracle.learned", "output_bias_gradient_dropped", [("g[5 * H + H * H] = w.sum()", "g[5 * H + H * H] = 0.0")]),
+    ("oracle.learned", "second_layer_transposed", [("g[3 * H:3 * H + H * H] = (d2.T @ h1).reshape(-1)",
                                              "g[3 * H:3 * H + H * H] = (h1.T @ d2).reshape(-1)")]),
-    ("learned", "uniform_bits", [("return (z >> 11) / float(1 << 53)", "return (z >> 12) / float(1 << 53)")]),
-    ("learned", "policy_sign", [("e = np.exp(-(g - g.min()) / tau)", "e = np.exp((g - g.min()) / tau)")]),
-    ("learned", "score_weight_tau_dropped", [("w[p] += (e[i] / z - (1.0 if i == s else 0.0)) / tau",
+    ("oracle.learned", "uniform_bits", [("return (z >> 11) / float(1 << 53)", "return (z >> 12) / float(1 << 53)")]),
+    ("oracle.learned", "policy_sign", [("e = np.exp(-(g - g.min()) / tau)", "e = np.exp((g - g.min()) / tau)")]),
+    ("oracle.learned", "score_weight_tau_dropped", [("w[p] += (e[i] / z - (1.0 if i == s else 0.0)) / tau",
                                               "w[p] += (e[i] / z - (1.0 if i == s else 0.0))")]),
-    ("learned", "adam_bias_correction_dropped", [("vh = m2 / (1 - b2 ** step)", "vh = m2")]),
-    ("learned", "adam_betas_swapped", [("mh = m1 / (1 - b1 ** step)", "mh = m1 / (1 - b2 ** step)")]),
+    ("oracle.learned", "adam_bias_correction_dropped", [("vh = m2 / (1 - b2 ** step)", "vh = m2")]),
+    ("oracle.learned", "adam_betas_swapped", [("mh = m1 / (1 - b1 ** step)", "mh = m1 / (1 - b2 ** step)")]),
     # sub-arrays (Section 3.4)
-    ("sharded", "h0_multiplier_even", [("a0 = out | 1", "a0 = out")]),
-    ("sharded", "query_wrong_subarray", [("idx = np.flatnonzero(sh == t)",
+    ("oracle.sharded", "h0_multiplier_even", [("a0 = out | 1", "a0 = out")]),
+    ("oracle.sharded", "query_wrong_subarray", [("idx = np.flatnonzero(sh == t)",
                                           "idx = np.flatnonzero(sh == (t + 1) % self.T)")]),
-    ("sharded", "layout_reversed", [("np.concatenate([s.words for s in self.subs])",
+    ("oracle.sharded", "layout_reversed", [("np.concatenate([s.words for s in self.subs])",
                                      "np.concatenate([s.words for s in reversed(self.subs)])")]),
     # the wrapper
-    ("oracle", "bitmap_unpacked_msb_first", [('np.unpackbits(b, bitorder="little")[:n]',
+    ("oracle.oracle", "bitmap_unpacked_msb_first", [('np.unpackbits(b, bitorder="little")[:n]',
                                               'np.unpackbits(b, bitorder="big")[:n]')]),
-    ("oracle", "batch_argument_ignored", [("B = self.batch if batch is None else int(batch)", "B = self.batch")]),
+    ("oracle.oracle", "batch_argument_ignored", [("B = self.batch if batch is None else int(batch)", "B = self.batch")]),
+]
+
+
+# The seeded input generators feed the oracle and the GPU path alike, so a
+# mistake there survives every parity test; their own pins must catch it.
+WORKLOAD_MUTANTS = [
+    ("splitmix_constant", [("_M1 = np.uint64(0xBF58476D1CE4E5B9)", "_M1 = np.uint64(0xBF58476D1CE4E5B8)")]),
+    ("splitmix_first_index", [("idx = np.arange(start + 1, start + n + 1, dtype=np.uint64)",
+                               "idx = np.arange(start, start + n, dtype=np.uint64)")]),
+    ("splitmix_at_first_index", [("idx = np.asarray(positions, dtype=np.uint64) + np.uint64(1)",
+                                  "idx = np.asarray(positions, dtype=np.uint64)")]),
+    ("genome_high_bits_first", [("shifts = (2 * np.arange(32, dtype=np.uint64))",
+                                 "shifts = (np.uint64(62) - 2 * np.arange(32, dtype=np.uint64))")]),
+    ("window_doubling_shift", [("pieces[2 * L] = (a[:m] << np.uint64(2 * L)) | a[L:L + m]",
+                                "pieces[2 * L] = (a[:m] << np.uint64(L)) | a[L:L + m]")]),
+    ("canonical_max", [("return np.minimum(fwd, rc)", "return np.maximum(fwd, rc)")]),
+    ("complement_wrong", [("rc = _windows((3 - bases).astype(np.uint8), q, first_high=False)",
+                           "rc = _windows((bases ^ 1).astype(np.uint8), q, first_high=False)")]),
+    ("reverse_missing", [("rc = _windows((3 - bases).astype(np.uint8), q, first_high=False)",
+                          "rc = _windows((3 - bases).astype(np.uint8), q, first_high=True)")]),
+    ("disjoint_not_excluding", [("cand = cand[ex[pos] != cand]", "cand = cand")]),
+    ("box_muller_sin", [("np.cos(2.0 * math.pi * u2)", "np.sin(2.0 * math.pi * u2)")]),
+    ("many_filter_blocks_rounded_down", [("M = -(-bits_per_key * n // 512)", "M = bits_per_key * n // 512")]),
+    ("many_filter_queries_all_members", [("return keys, np.concatenate([keys[:half], other])",
+                                          "return keys, np.concatenate([keys, other])")]),
+    ("serving_query_fraction", [("kind = 1 if r[j, 1] < query_frac else 0",
+                                 "kind = 1 if r[j, 1] > query_frac else 0")]),
+    ("serving_members_not_yet_inserted", [("n_mem) % np.uint64(have)", "n_mem) % np.uint64(have + 1)")]),
 ]
 
 
@@ -169,10 +202,16 @@ def _compile_c(src, out_dir, name):
     return lib
 
 
-def _run_pins(kind, path):
-    """(exit status of the pin run against the planted copy, output tail)."""
+def _module_file(module):
+    parts = module.split(".")
+    base = os.path.join(ROOT, *parts)
+    return os.path.join(base, "__init__.py") if os.path.isdir(base) else base + ".py"
+
+
+def _run_pins(kind, path, pins):
+    """(exit status of the pins run against the planted copy, output tail)."""
     try:
-        r = subprocess.run([sys.executable, "-c", CHILD, kind, path, PINS], cwd=ROOT,
+        r = subprocess.run([sys.executable, "-c", CHILD, kind, path, pins], cwd=ROOT,
                            capture_output=True, text=True, timeout=CHILD_TIMEOUT_S)
     except subprocess.TimeoutExpired:
         return "timeout", ""
@@ -185,29 +224,26 @@ def outcomes(tmp_path_factory):
     out_dir = str(tmp_path_factory.mktemp("planted"))
     with open(os.path.join(ORACLE, "blowchoc_oracle.c")) as fh:
         c_src = fh.read()
-    jobs = {"control_c": ("c", _compile_c(c_src, out_dir, "control_c"))}
+    jobs = {"control_c": ("c", _compile_c(c_src, out_dir, "control_c"), PINS)}
     for name, edits in C_MUTANTS:
-        jobs[name] = ("c", _compile_c(_plant(c_src, edits), out_dir, name))
-    py_src = {}
-    for module in {m for m, _, _ in PY_MUTANTS}:
-        with open(os.path.join(ORACLE, module + ".py")) as fh:
-            py_src[module] = fh.read()
-    path = os.path.join(out_dir, "control_py.py")
-    with open(path, "w") as fh:
-        fh.write(py_src["closed_forms"])
-    jobs["control_py"] = ("closed_forms", path)
-    for module, name, edits in PY_MUTANTS:
+        jobs[name] = ("c", _compile_c(_plant(c_src, edits), out_dir, name), PINS)
+    py = [(module, name, edits, PINS) for module, name, edits in PY_MUTANTS]
+    py += [("workloads", name, edits, WORKLOAD_PINS) for name, edits in WORKLOAD_MUTANTS]
+    py += [("oracle.closed_forms", "control_py", [], PINS), ("workloads", "control_workloads", [], WORKLOAD_PINS)]
+    for module, name, edits, pins in py:
+        with open(_module_file(module)) as fh:
+            src = fh.read()
         path = os.path.join(out_dir, name + ".py")
         with open(path, "w") as fh:
-            fh.write(_plant(py_src[module], edits))
-        jobs[name] = (module, path)
+            fh.write(_plant(src, edits))
+        jobs[name] = (module, path, pins)
     workers = max(1, min(8, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = {name: ex.submit(_run_pins, kind, path) for name, (kind, path) in jobs.items()}
+        futs = {name: ex.submit(_run_pins, *job) for name, job in jobs.items()}
         return {name: f.result() for name, f in futs.items()}
 
 
-@pytest.mark.parametrize("control", ["control_c", "control_py"])
+@pytest.mark.parametrize("control", ["control_c", "control_py", "control_workloads"])
 def test_unplanted_copies_pass_every_pin(outcomes, control):
     rc, tail = outcomes[control]
     assert rc == 0, tail
@@ -221,5 +257,11 @@ def test_planted_mistake_in_the_c_oracle_fails_a_pin(outcomes, name):
 
 @pytest.mark.parametrize("name", [n for _, n, _ in PY_MUTANTS])
 def test_planted_mistake_in_a_python_oracle_module_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
+
+
+@pytest.mark.parametrize("name", [n for n, _ in WORKLOAD_MUTANTS])
+def test_planted_mistake_in_the_input_generators_fails_a_pin(outcomes, name):
     rc, tail = outcomes[name]
     assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)

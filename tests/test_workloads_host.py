@@ -98,6 +98,20 @@ def test_many_filter_recipe():
         assert it["B"] <= max(1, it["M"] // 2) or it["M"] == 1
 
 
+def test_many_filter_keys_recipe():
+    """A filter's queries are its first ceil(n / 2) keys followed by
+    floor(n / 2) keys of its query stream, which it does not hold."""
+    cfg = sorted(workloads.many_filter_config(), key=lambda it: it["n"])[:8]
+    for it in cfg:
+        keys, queries = workloads.many_filter_keys(it)
+        n, half = it["n"], (it["n"] + 1) // 2
+        assert len(keys) == n and len(queries) == n
+        assert np.array_equal(keys, workloads.splitmix64(it["key_seed"], n))
+        assert np.array_equal(queries[:half], keys[:half])
+        assert np.array_equal(queries[half:], workloads.splitmix64(it["query_seed"], n // 2))
+        assert not np.isin(queries[half:], keys).any()
+
+
 def test_serving_recipe():
     filters, reqs = workloads.serving_config(n_requests=4000)
     assert len(filters) == 64
