@@ -13,15 +13,26 @@ The seeded input generators (workloads/) get the same treatment against
 tests/test_workloads_host.py: both sides of every parity test draw their
 keys from them, so only their own pins can catch a mistake there.
 
-Three controls run the same way with nothing planted: the unchanged C source
-compiled by this harness, and an unchanged oracle module and generator
-module re-executed by it. They must pass every pin, which shows that a
-failing case fails because of its mistake and not because of the harness.
+The library's multi-rank exchange of sub-arrays (paper_2501_18977_gb300/
+sharded.py) is checked the same way against tests/test_sharded_host.py, whose
+gloo ranks compare it with the oracle's split filter. Its ranks are spawned
+processes that import the package from disk, so each such case runs in a
+shadow tree: links to the repository's directories and a package directory
+whose sharded.py is the planted copy. Only mistakes that let every rank run
+to its end are planted (a rank that raised would leave its peers waiting in
+a collective).
+
+Four controls run the same way with nothing planted: the unchanged C source
+compiled by this harness, an unchanged oracle module and generator module
+re-executed by it, and the unchanged exchange in a shadow tree. They must
+pass every pin, which shows that a failing case fails because of its mistake
+and not because of the harness.
 
 CPU only; the children run in parallel, stopping at their first failing pin.
 """
 import concurrent.futures as cf
 import os
+import signal
 import subprocess
 import sys
 
@@ -31,6 +42,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join("tests", "test_oracle_pins.py")
 WORKLOAD_PINS = os.path.join("tests", "test_workloads_host.py")
+EXCHANGE_PINS = os.path.join("tests", "test_sharded_host.py")
+PACKAGE = "paper_2501_18977_gb300"
 CHILD_TIMEOUT_S = 240
 
 # The child: point the oracle at the planted copy, then run the pins.
@@ -185,6 +198,19 @@ WORKLOAD_MUTANTS = [
 ]
 
 
+# The multi-rank exchange (the library's sharded.py); every rank still
+# reaches its end, with wrong words or answers.
+EXCHANGE_MUTANTS = [
+    ("exchange_drops_first_received_key", [("    if recv.numel():\n        local_insert(recv)",
+                                            "    if recv.numel() > 1:\n        local_insert(recv[1:])")]),
+    ("exchange_reverses_arrival_order", [("        local_insert(recv)", "        local_insert(recv.flip(0))")]),
+    ("answers_written_to_the_start", [("local_query(recv[kpos:kpos + c], answers[wpos:wpos + w])",
+                                       "local_query(recv[kpos:kpos + c], answers[:w])")]),
+    ("answers_of_sources_reversed", [("    for c, w in zip(rc, rw):",
+                                      "    for c, w in zip(reversed(rc), reversed(rw)):")]),
+]
+
+
 def _plant(src, edits):
     for old, new in edits:
         assert src.count(old) == 1, "planted text must occur exactly once: %r" % old
@@ -208,14 +234,45 @@ def _module_file(module):
     return os.path.join(base, "__init__.py") if os.path.isdir(base) else base + ".py"
 
 
+def _run(cmd, cwd):
+    """(exit status, output tail) of a child in a session of its own; on
+    timeout the whole session (the child and any rank it spawned) is killed."""
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    p = subprocess.Popen(cmd, cwd=cwd, env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                         text=True, start_new_session=True)
+    try:
+        out, _ = p.communicate(timeout=CHILD_TIMEOUT_S)
+    except subprocess.TimeoutExpired:
+        os.killpg(p.pid, signal.SIGKILL)
+        p.communicate()
+        return "timeout", ""
+    return p.returncode, out[-1500:]
+
+
 def _run_pins(kind, path, pins):
     """(exit status of the pins run against the planted copy, output tail)."""
-    try:
-        r = subprocess.run([sys.executable, "-c", CHILD, kind, path, pins], cwd=ROOT,
-                           capture_output=True, text=True, timeout=CHILD_TIMEOUT_S)
-    except subprocess.TimeoutExpired:
-        return "timeout", ""
-    return r.returncode, (r.stdout + r.stderr)[-1500:]
+    return _run([sys.executable, "-c", CHILD, kind, path, pins], ROOT)
+
+
+def _shadow_tree(out_dir, name, sharded_src):
+    """A tree that links the repository's directories and files, except the
+    package, which is a directory of links with sharded.py replaced."""
+    top = os.path.join(out_dir, "shadow_" + name)
+    os.makedirs(os.path.join(top, PACKAGE))
+    for entry in os.listdir(ROOT):
+        if entry not in (PACKAGE, ".git") and not entry.startswith("."):
+            os.symlink(os.path.join(ROOT, entry), os.path.join(top, entry))
+    src_pkg = os.path.join(ROOT, PACKAGE)
+    for entry in os.listdir(src_pkg):
+        if entry not in ("sharded.py", "__pycache__"):
+            os.symlink(os.path.join(src_pkg, entry), os.path.join(top, PACKAGE, entry))
+    with open(os.path.join(top, PACKAGE, "sharded.py"), "w") as fh:
+        fh.write(sharded_src)
+    return top
+
+
+def _run_exchange_pins(top):
+    return _run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", EXCHANGE_PINS], top)
 
 
 @pytest.fixture(scope="module")
@@ -237,13 +294,19 @@ def outcomes(tmp_path_factory):
         with open(path, "w") as fh:
             fh.write(_plant(src, edits))
         jobs[name] = (module, path, pins)
+    with open(os.path.join(ROOT, PACKAGE, "sharded.py")) as fh:
+        sharded_src = fh.read()
+    trees = {"control_exchange": _shadow_tree(out_dir, "control_exchange", sharded_src)}
+    for name, edits in EXCHANGE_MUTANTS:
+        trees[name] = _shadow_tree(out_dir, name, _plant(sharded_src, edits))
     workers = max(1, min(8, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = {name: ex.submit(_run_pins, *job) for name, job in jobs.items()}
+        futs = {name: ex.submit(_run_exchange_pins, top) for name, top in trees.items()}
+        futs.update({name: ex.submit(_run_pins, *job) for name, job in jobs.items()})
         return {name: f.result() for name, f in futs.items()}
 
 
-@pytest.mark.parametrize("control", ["control_c", "control_py", "control_workloads"])
+@pytest.mark.parametrize("control", ["control_c", "control_py", "control_workloads", "control_exchange"])
 def test_unplanted_copies_pass_every_pin(outcomes, control):
     rc, tail = outcomes[control]
     assert rc == 0, tail
@@ -263,5 +326,11 @@ def test_planted_mistake_in_a_python_oracle_module_fails_a_pin(outcomes, name):
 
 @pytest.mark.parametrize("name", [n for n, _ in WORKLOAD_MUTANTS])
 def test_planted_mistake_in_the_input_generators_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
+
+
+@pytest.mark.parametrize("name", [n for n, _ in EXCHANGE_MUTANTS])
+def test_planted_mistake_in_the_multi_rank_exchange_fails_a_pin(outcomes, name):
     rc, tail = outcomes[name]
     assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
