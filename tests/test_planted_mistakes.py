@@ -22,11 +22,15 @@ whose sharded.py is the planted copy. Only mistakes that let every rank run
 to its end are planted (a rank that raised would leave its peers waiting in
 a collective).
 
-Four controls run the same way with nothing planted: the unchanged C source
+The bench's host arithmetic (bench.py: max over ranks, whole-job throughput,
+ratios, the traffic record's tie, the clock record, strict JSON) runs the
+same way against tests/test_bench_host.py and tests/test_multirank_host.py.
+
+Five controls run the same way with nothing planted: the unchanged C source
 compiled by this harness, an unchanged oracle module and generator module
-re-executed by it, and the unchanged exchange in a shadow tree. They must
-pass every pin, which shows that a failing case fails because of its mistake
-and not because of the harness.
+re-executed by it, and the unchanged exchange and bench in shadow trees. They
+must pass every pin, which shows that a failing case fails because of its
+mistake and not because of the harness.
 
 CPU only; the children run in parallel, stopping at their first failing pin.
 """
@@ -42,8 +46,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join("tests", "test_oracle_pins.py")
 WORKLOAD_PINS = os.path.join("tests", "test_workloads_host.py")
-EXCHANGE_PINS = os.path.join("tests", "test_sharded_host.py")
-PACKAGE = "paper_2501_18977_gb300"
+EXCHANGE_PINS = [os.path.join("tests", "test_sharded_host.py")]
+BENCH_PINS = [os.path.join("tests", "test_bench_host.py"), os.path.join("tests", "test_multirank_host.py")]
 CHILD_TIMEOUT_S = 240
 
 # The child: point the oracle at the planted copy, then run the pins.
@@ -211,6 +215,26 @@ EXCHANGE_MUTANTS = [
 ]
 
 
+# The measurement contract's host arithmetic (bench.py): max over ranks,
+# whole-job throughput, ratios, the traffic record's tie, the clock record
+# and strict JSON.
+BENCH_MUTANTS = [
+    ("slowest_rank_is_the_fastest", [("op=dist.ReduceOp.MAX", "op=dist.ReduceOp.MIN")]),
+    ("throughput_per_rank", [("return world * keys_per_rank / (ms_per_step / 1e3) / 1e6",
+                              "return keys_per_rank / (ms_per_step / 1e3) / 1e6")]),
+    ("ratio_inverted", [("else round(a / b, nd)", "else round(b / a, nd)")]),
+    ("traffic_launch_not_checked", [("    if d[kernel].get(\"launch\") != launch_config(tuning, kernel):\n"
+                                     "        return None\n", "")]),
+    ("traffic_sources_not_checked", [("    if d[kernel].get(\"sources_sha256\") != sources_sha256(KERNEL_SOURCES[kernel]):\n"
+                                      "        return None\n", "")]),
+    ("clock_median_over_all_samples", [("\"sm_mhz\": statistics.median(busy) if busy else max(sm)",
+                                        "\"sm_mhz\": statistics.median(sm)")]),
+    ("idle_samples_counted_busy", [("float(parts[9]) >= 50.0", "float(parts[9]) >= 0.0")]),
+    ("nan_left_in_json", [("return obj if math.isfinite(obj) else None", "return obj")]),
+    ("throttle_reasons_shifted", [("zip(names, parts[5:9])", "zip(names, parts[4:8])")]),
+]
+
+
 def _plant(src, edits):
     for old, new in edits:
         assert src.count(old) == 1, "planted text must occur exactly once: %r" % old
@@ -254,25 +278,30 @@ def _run_pins(kind, path, pins):
     return _run([sys.executable, "-c", CHILD, kind, path, pins], ROOT)
 
 
-def _shadow_tree(out_dir, name, sharded_src):
-    """A tree that links the repository's directories and files, except the
-    package, which is a directory of links with sharded.py replaced."""
+def _shadow_tree(out_dir, name, relpath, src):
+    """A tree of links to the repository in which the file at `relpath` is
+    `src`: the directories on its path are real, everything else is a link."""
     top = os.path.join(out_dir, "shadow_" + name)
-    os.makedirs(os.path.join(top, PACKAGE))
-    for entry in os.listdir(ROOT):
-        if entry not in (PACKAGE, ".git") and not entry.startswith("."):
-            os.symlink(os.path.join(ROOT, entry), os.path.join(top, entry))
-    src_pkg = os.path.join(ROOT, PACKAGE)
-    for entry in os.listdir(src_pkg):
-        if entry not in ("sharded.py", "__pycache__"):
-            os.symlink(os.path.join(src_pkg, entry), os.path.join(top, PACKAGE, entry))
-    with open(os.path.join(top, PACKAGE, "sharded.py"), "w") as fh:
-        fh.write(sharded_src)
+
+    def mirror(src_dir, dst_dir, rest):
+        os.makedirs(dst_dir)
+        for entry in os.listdir(src_dir):
+            if entry.startswith(".") or entry == "__pycache__":
+                continue
+            if entry != rest[0]:
+                os.symlink(os.path.join(src_dir, entry), os.path.join(dst_dir, entry))
+            elif len(rest) == 1:
+                with open(os.path.join(dst_dir, entry), "w") as fh:
+                    fh.write(src)
+            else:
+                mirror(os.path.join(src_dir, entry), os.path.join(dst_dir, entry), rest[1:])
+
+    mirror(ROOT, top, relpath.split("/"))
     return top
 
 
-def _run_exchange_pins(top):
-    return _run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", EXCHANGE_PINS], top)
+def _run_shadow_pins(top, pins):
+    return _run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + list(pins), top)
 
 
 @pytest.fixture(scope="module")
@@ -294,19 +323,23 @@ def outcomes(tmp_path_factory):
         with open(path, "w") as fh:
             fh.write(_plant(src, edits))
         jobs[name] = (module, path, pins)
-    with open(os.path.join(ROOT, PACKAGE, "sharded.py")) as fh:
-        sharded_src = fh.read()
-    trees = {"control_exchange": _shadow_tree(out_dir, "control_exchange", sharded_src)}
-    for name, edits in EXCHANGE_MUTANTS:
-        trees[name] = _shadow_tree(out_dir, name, _plant(sharded_src, edits))
+    shadow = [("paper_2501_18977_gb300/sharded.py", EXCHANGE_PINS, "control_exchange", [])]
+    shadow += [("paper_2501_18977_gb300/sharded.py", EXCHANGE_PINS, n, e) for n, e in EXCHANGE_MUTANTS]
+    shadow += [("bench.py", BENCH_PINS, "control_bench", [])]
+    shadow += [("bench.py", BENCH_PINS, n, e) for n, e in BENCH_MUTANTS]
+    trees = {}
+    for relpath, pins, name, edits in shadow:
+        with open(os.path.join(ROOT, relpath)) as fh:
+            trees[name] = (_shadow_tree(out_dir, name, relpath, _plant(fh.read(), edits)), pins)
     workers = max(1, min(8, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = {name: ex.submit(_run_exchange_pins, top) for name, top in trees.items()}
+        futs = {name: ex.submit(_run_shadow_pins, *tree) for name, tree in trees.items()}
         futs.update({name: ex.submit(_run_pins, *job) for name, job in jobs.items()})
         return {name: f.result() for name, f in futs.items()}
 
 
-@pytest.mark.parametrize("control", ["control_c", "control_py", "control_workloads", "control_exchange"])
+@pytest.mark.parametrize("control", ["control_c", "control_py", "control_workloads", "control_exchange",
+                                     "control_bench"])
 def test_unplanted_copies_pass_every_pin(outcomes, control):
     rc, tail = outcomes[control]
     assert rc == 0, tail
@@ -332,5 +365,11 @@ def test_planted_mistake_in_the_input_generators_fails_a_pin(outcomes, name):
 
 @pytest.mark.parametrize("name", [n for n, _ in EXCHANGE_MUTANTS])
 def test_planted_mistake_in_the_multi_rank_exchange_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
+
+
+@pytest.mark.parametrize("name", [n for n, _ in BENCH_MUTANTS])
+def test_planted_mistake_in_the_bench_arithmetic_fails_a_pin(outcomes, name):
     rc, tail = outcomes[name]
     assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
