@@ -24,7 +24,9 @@ a collective).
 
 The bench's host arithmetic (bench.py: max over ranks, whole-job throughput,
 ratios, the traffic record's tie, the clock record, strict JSON) runs the
-same way against tests/test_bench_host.py and tests/test_multirank_host.py.
+same way against tests/test_bench_host.py and tests/test_multirank_host.py,
+and the paper-scale sweep driver (the stream-disjointness proof, the sizes,
+the batch rule) against tests/test_sweeps_host.py.
 
 Five controls run the same way with nothing planted: the unchanged C source
 compiled by this harness, an unchanged oracle module and generator module
@@ -47,6 +49,7 @@ ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join("tests", "test_oracle_pins.py")
 WORKLOAD_PINS = os.path.join("tests", "test_workloads_host.py")
 EXCHANGE_PINS = [os.path.join("tests", "test_sharded_host.py")]
+SWEEP_PINS = os.path.join("tests", "test_sweeps_host.py")
 BENCH_PINS = [os.path.join("tests", "test_bench_host.py"), os.path.join("tests", "test_multirank_host.py")]
 CHILD_TIMEOUT_S = 240
 
@@ -202,6 +205,22 @@ WORKLOAD_MUTANTS = [
 ]
 
 
+# The paper-scale sweep driver: the proof that inserted and negative key
+# streams are disjoint, the sizes of Appendix C and the batch rule.
+SWEEP_MUTANTS = [
+    ("overlap_lower_bound", [("return not (d < n or d > (1 << 64) - n_neg)",
+                              "return not (d < n - 1 or d > (1 << 64) - n_neg)")]),
+    ("overlap_upper_bound", [("return not (d < n or d > (1 << 64) - n_neg)",
+                              "return not (d < n or d >= (1 << 64) - n_neg)")]),
+    ("gamma_not_inverted", [("pow(GAMMA, -1, 1 << 64)", "GAMMA")]),
+    ("blocks_rounded_down", [("math.ceil(bloom_bits(n, k, rho) / 512.0)", "math.floor(bloom_bits(n, k, rho) / 512.0)")]),
+    ("batch_fraction", [("max(M / 64.0, 1.0)", "max(M / 32.0, 1.0)")]),
+    ("batch_cap", [("max(0, min(20, ", "max(0, min(21, ")]),
+    ("bloom_exponent_dropped", [("return (1.0 - math.exp(-k * n / m)) ** k", "return (1.0 - math.exp(-k * n / m))")]),
+    ("poisson_mean_inverted", [("    lam = n / M\n", "    lam = M / n\n")]),
+    ("bloom_bits_rho_dropped", [("return rho * n * k / LN2", "return n * k / LN2")]),
+]
+
 # The multi-rank exchange (the library's sharded.py); every rank still
 # reaches its end, with wrong words or answers.
 EXCHANGE_MUTANTS = [
@@ -315,6 +334,7 @@ def outcomes(tmp_path_factory):
         jobs[name] = ("c", _compile_c(_plant(c_src, edits), out_dir, name), PINS)
     py = [(module, name, edits, PINS) for module, name, edits in PY_MUTANTS]
     py += [("workloads", name, edits, WORKLOAD_PINS) for name, edits in WORKLOAD_MUTANTS]
+    py += [("paper_2501_18977_gb300.sweeps", name, edits, SWEEP_PINS) for name, edits in SWEEP_MUTANTS]
     py += [("oracle.closed_forms", "control_py", [], PINS), ("workloads", "control_workloads", [], WORKLOAD_PINS)]
     for module, name, edits, pins in py:
         with open(_module_file(module)) as fh:
@@ -371,5 +391,11 @@ def test_planted_mistake_in_the_multi_rank_exchange_fails_a_pin(outcomes, name):
 
 @pytest.mark.parametrize("name", [n for n, _ in BENCH_MUTANTS])
 def test_planted_mistake_in_the_bench_arithmetic_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
+
+
+@pytest.mark.parametrize("name", [n for n, _ in SWEEP_MUTANTS])
+def test_planted_mistake_in_the_sweep_driver_fails_a_pin(outcomes, name):
     rc, tail = outcomes[name]
     assert rc == 1, "planted mistake %s was not caught (exit %s):\n%s" % (name, rc, tail)
