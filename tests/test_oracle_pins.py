@@ -158,6 +158,23 @@ def test_load_bound_printed(c, k, want):
     assert (j / 512.0) ** k == pytest.approx(2.0 ** -k / c, rel=1e-12)
 
 
+def test_choices_fpr_printed():
+    """Querying c candidate blocks turns a per-block FPR eps into
+    1 - (1 - eps)^c: eps + eps - eps^2 for two choices and almost three times
+    eps for three (Section 3.1). The histogram estimate combines its c blocks
+    so; a filter whose blocks all hold L bits has eps = (L/512)^k."""
+    assert _printed()[("choices_fpr", "c=2")][2].startswith("eps + eps - eps^2")
+    for L, k in ((256, 10), (300, 7), (200, 14)):
+        hist = np.zeros(513)
+        hist[L] = 1000
+        eps = (L / 512.0) ** k
+        assert cf.fpr_given_state(hist, k, 1) == pytest.approx(eps, rel=1e-12)
+        assert cf.fpr_given_state(hist, k, 2) == pytest.approx(eps + eps - eps ** 2, rel=1e-12)
+        three = cf.fpr_given_state(hist, k, 3)
+        assert three == pytest.approx(3 * eps - 3 * eps ** 2 + eps ** 3, rel=1e-12)
+        assert 2.9 * eps < three < 3 * eps
+
+
 def test_birthday_printed():
     p = cf.birthday_collision(10)
     assert 0.08 < p < 0.10  # "almost 10%"

@@ -151,6 +151,7 @@ PY_MUTANTS = [
     ("oracle.closed_forms", "blocked_bloom_bit_exponent", [("(1.0 - 1.0 / BLOCK_BITS) ** (i * k)",
                                                      "(1.0 - 1.0 / BLOCK_BITS) ** i")]),
     ("oracle.closed_forms", "state_fpr_exponent", [("(L / BLOCK_BITS) ** k", "(L / BLOCK_BITS) ** (k - 1)")]),
+    ("oracle.closed_forms", "choices_fpr_linearised", [("return 1.0 - (1.0 - q) ** c", "return c * q")]),
     # learned cost: network, gradient, sampler, Adam
     ("oracle.learned", "grid_load_without_new_bits", [("(L + a) / 512.0", "L / 512.0")]),
     ("oracle.learned", "forward_bias_sign", [("return h2 @ w3 + b3", "return h2 @ w3 - b3")]),
