@@ -1,4 +1,5 @@
-"""Planted mistakes in the oracle must make one of its pins fail.
+"""Planted mistakes must make a pin fail: in the oracle, the seeded input
+generators, the library's multi-rank exchange, the sweep driver and the bench.
 
 The pins in tests/test_oracle_pins.py vouch for the oracle only if a
 plausible mistake in it would break one of them. Each case below copies one
@@ -54,17 +55,16 @@ BENCH_PINS = [os.path.join("tests", "test_bench_host.py"), os.path.join("tests",
 CHILD_TIMEOUT_S = 240
 
 # The child: point the oracle at the planted copy, then run the pins.
-#   kind "c":    the C library the oracle loads is the compiled copy;
-#   kind "none": nothing planted;
-#   otherwise:   the named module is re-executed from the copy before the
-#                pins import anything from it.
+#   kind "c":  the C library the oracle loads is the compiled copy;
+#   otherwise: the named module is re-executed from the copy before the
+#              pins import anything from it.
 CHILD = r"""
 import importlib, sys
 kind, path = sys.argv[1], sys.argv[2]
 if kind == "c":
     import oracle.build as ob
     ob.build = lambda force=False: path
-elif kind != "none":
+else:
     mod = importlib.import_module(kind)
     with open(path) as fh:
         src = fh.read()
@@ -326,7 +326,7 @@ def _run_shadow_pins(top, pins):
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
-    """Exit status of the pins for every planted copy and both controls."""
+    """Exit status of the pins for every planted copy and every control."""
     out_dir = str(tmp_path_factory.mktemp("planted"))
     with open(os.path.join(ORACLE, "blowchoc_oracle.c")) as fh:
         c_src = fh.read()
