@@ -31,7 +31,8 @@ from oracle.oracle import OracleFilter, bits_of_bitmap, COST_MIX, COST_LA, COST_
 import workloads  # noqa: E402
 
 SETTINGS = settings(max_examples=300, deadline=None, derandomize=True, database=None)
-COSTS = st.sampled_from([(COST_MIX, 2.5), (COST_MIX, 50.0), (COST_LA, 3.5), (COST_EXP, GOLDEN_RATIO), (COST_EXP, 1.2)])
+COSTS = st.sampled_from([(COST_MIX, 2.5), (COST_MIX, 50.0), (COST_LA, 3.5), (COST_EXP, GOLDEN_RATIO),
+                         (COST_EXP, 1.2)])
 BLOCKS = st.one_of(st.integers(1, 8), st.sampled_from([63, 64, 100, 127, 128, 257, 1000, 4096]))
 SEEDS = st.integers(0, (1 << 64) - 1)
 
