@@ -174,7 +174,8 @@ PY_MUTANTS = [
     # the wrapper
     ("oracle.oracle", "bitmap_unpacked_msb_first", [('np.unpackbits(b, bitorder="little")[:n]',
                                               'np.unpackbits(b, bitorder="big")[:n]')]),
-    ("oracle.oracle", "batch_argument_ignored", [("B = self.batch if batch is None else int(batch)", "B = self.batch")]),
+    ("oracle.oracle", "batch_argument_ignored", [("B = self.batch if batch is None else int(batch)",
+                                                  "B = self.batch")]),
 ]
 
 
@@ -214,7 +215,8 @@ SWEEP_MUTANTS = [
     ("overlap_upper_bound", [("return not (d < n or d > (1 << 64) - n_neg)",
                               "return not (d < n or d >= (1 << 64) - n_neg)")]),
     ("gamma_not_inverted", [("pow(GAMMA, -1, 1 << 64)", "GAMMA")]),
-    ("blocks_rounded_down", [("math.ceil(bloom_bits(n, k, rho) / 512.0)", "math.floor(bloom_bits(n, k, rho) / 512.0)")]),
+    ("blocks_rounded_down", [("math.ceil(bloom_bits(n, k, rho) / 512.0)",
+                              "math.floor(bloom_bits(n, k, rho) / 512.0)")]),
     ("batch_fraction", [("max(M / 64.0, 1.0)", "max(M / 32.0, 1.0)")]),
     ("batch_cap", [("max(0, min(20, ", "max(0, min(21, ")]),
     ("bloom_exponent_dropped", [("return (1.0 - math.exp(-k * n / m)) ** k", "return (1.0 - math.exp(-k * n / m))")]),
@@ -245,7 +247,8 @@ BENCH_MUTANTS = [
     ("ratio_inverted", [("else round(a / b, nd)", "else round(b / a, nd)")]),
     ("traffic_launch_not_checked", [("    if d[kernel].get(\"launch\") != launch_config(tuning, kernel):\n"
                                      "        return None\n", "")]),
-    ("traffic_sources_not_checked", [("    if d[kernel].get(\"sources_sha256\") != sources_sha256(KERNEL_SOURCES[kernel]):\n"
+    ("traffic_sources_not_checked", [("    if d[kernel].get(\"sources_sha256\") != "
+                                      "sources_sha256(KERNEL_SOURCES[kernel]):\n"
                                       "        return None\n", "")]),
     ("clock_median_over_all_samples", [("\"sm_mhz\": statistics.median(busy) if busy else max(sm)",
                                         "\"sm_mhz\": statistics.median(sm)")]),
